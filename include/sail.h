@@ -1,0 +1,201 @@
+/*
+ * sail.h - C ABI of the GB300 library for SAIL, the simulated-annealing
+ * inversion of the Laplace transform (Lutsyshyn & Astrakharchik,
+ * arXiv:1609.07936).
+ *
+ * One handle holds one inversion: the data F(tau_i) with noise sigma_i on a
+ * tau grid, a histogram spectral model on n_omega equal bins of [0, w_max]
+ * (Sec. 2.1, Eq. spectral-model), and a population of n_walkers Markov
+ * walkers annealed by sum-rule-preserving Metropolis moves (Sec. 2.2), with
+ * a periodic full recomputation of the residual and imprinted branching of
+ * the population after every block of sweeps (Sec. 2.5).
+ *
+ * Memory: the library never allocates device memory.  The caller passes one
+ * device buffer ("workspace", at least sail_workspace_size() bytes, 256-byte
+ * aligned) and a CUDA stream; every kernel of the handle runs on that stream
+ * and all device state lives in the workspace until sail_destroy().  Host
+ * arrays passed in are read during the call only; host arrays passed out are
+ * written before the call returns.  Calls on one handle must not overlap.
+ *
+ * Errors: functions return SAIL_OK (0), a positive status (SAIL_NOT_CONVERGED)
+ * or a negative error code; sail_last_error() gives a message for the calling
+ * thread.  No function aborts or exits the process.
+ */
+#ifndef SAIL_H
+#define SAIL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SAIL_OK 0
+#define SAIL_NOT_CONVERGED 1   /* target chi2 not reached; results are still valid */
+#define SAIL_EINVAL (-1)       /* invalid argument (grid, data, parameters, handle) */
+#define SAIL_ENOMEM (-2)       /* workspace smaller than sail_workspace_size() */
+#define SAIL_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define SAIL_ESTATE (-4)       /* call not valid in the handle's current state */
+
+/* Arithmetic of the Metropolis moves. */
+#define SAIL_PREC_FP64 0   /* validation path: FP64 state, explicit rescale of every bin, sums in the
+                              oracle's order, no fused multiply-add */
+#define SAIL_PREC_FP32 1   /* production path: FP32 state and residual, lazy common scale,
+                              FP64 residual recomputation and chi2 */
+
+typedef struct sail_ctx *sail_t;
+
+/* Run parameters.  sail_default_params() fills the paper's choices (Sec. 3):
+ * T_start = 10 in units of the start residue, k = 100 sweeps per block,
+ * branching of a quarter of the walkers with imprint strength 0.1, amplitude
+ * heuristic p = 1, m = 2. */
+typedef struct sail_params {
+    int n_walkers;          /* population size N_w (>= 1) */
+    int precision;          /* SAIL_PREC_FP64 or SAIL_PREC_FP32 */
+    int n_sweeps;           /* length of the temperature schedule, in sweeps of n_omega moves */
+    int sweeps_per_block;   /* k: branching after every k sweeps (Sec. 3) */
+    int resync_every;       /* full residual recomputation period, in sweeps */
+    int branching;          /* 1: imprinted branching at every block end (Sec. 2.5) */
+    double T_start, T_end;  /* geometric schedule, in units of the start residue chi2_0 (Sec. 3) */
+    double branch_fraction; /* fraction of walkers given a zero multiplier (1/4) */
+    double imprint_t;       /* imprint strength t (0.1) */
+    double move_scale;      /* d: 1 - r is uniform on (-y d, y d); <= 0 selects 1 / n_omega */
+    double y_p, y_m, y_min; /* Eq. (amplitude-acceptance-adjustment) p, m, and a floor for y */
+    double A, B;            /* sum constants of Sec. 2.2; A = NaN takes F(0) / c_0 (needs tau_0 = 0) */
+    double avg_chi2_factor; /* average walkers with chi2 <= factor * min chi2 (1.5) */
+    double target_chi2;     /* > 0: sail_anneal stops once chi2 of the averaged spectrum <= target */
+    uint64_t seed;          /* key of the Philox4x32-10 stream */
+    int trace;              /* 1: record every walker's accepted-move count per sweep and the
+                               branching multipliers (validation; enlarges the workspace) */
+    int timing;             /* 1: time every kernel with CUDA events on the handle's stream;
+                               totals appear in sail_info */
+    int reserved[6];
+} sail_params;
+
+/* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */
+typedef struct sail_block_stats {
+    int block;              /* block index */
+    int sweep_end;          /* sweeps completed after this block */
+    double T;               /* absolute temperature of the block's last sweep */
+    double chi2_min, chi2_mean;
+    double acceptance;      /* accepted / proposed moves in the block */
+    double positivity_rejected; /* proposals rejected because a bin would go negative / proposed */
+    double branch_delta;    /* Delta of the branching solve (0 without branching) */
+    int branch_zeros;       /* walkers imprinted */
+    int reserved;
+} sail_block_stats;
+
+typedef struct sail_info {
+    int n_tau, n_omega, n_walkers, n_tau_pad, precision;
+    int sweeps_done, blocks_done, n_sweeps;
+    double chi2_0;          /* residue of the start spectrum (unit of T) */
+    double d_omega, A, B;
+    double lambda0;         /* tilt of the start spectrum a_j ~ exp(-lambda0 x_j) */
+    long long kernel_launches; /* kernels this handle has launched so far */
+    size_t workspace_bytes;
+    /* with timing = 1: device time in ms and launch counts of the sweep kernel, the
+     * residual recomputation and the branching kernels */
+    double sweep_ms, resync_ms, branch_ms;
+    long long sweep_launches, resync_launches, branch_launches;
+    long long moves;           /* walker-moves proposed so far */
+} sail_info;
+
+/* Fills *p with the defaults listed above (n_walkers 1024, FP32, 20000 sweeps,
+ * resync every 50 sweeps, T 10 -> 1e-9, seed 0). */
+void sail_default_params(sail_params *p);
+
+/* Bytes of device workspace a handle with these sizes needs (Sec. 2.1-2.5 state:
+ * kernel tables, per-walker spectra, residuals, chi2, counters, branching scratch). */
+int sail_workspace_size(int n_tau, int n_omega, const sail_params *p, size_t *bytes);
+
+/*
+ * Creates a handle (Sec. 2.1-2.2).
+ *   tau[n_tau]      >= 0, any order; F[n_tau] data; sigma[n_tau] > 0 noise (chi2 is
+ *                   sum_i ((F_i - model_i) / sigma_i)^2, Eq. residue weighted by sigma)
+ *   omega[n_omega]  bin centres x_j = (j + 1/2) dw of equal bins starting at 0
+ *   p               parameters (copied); p->B must be finite and x_0 < B/A < x_{n-1}
+ *   d_workspace     device buffer of ws_bytes >= sail_workspace_size(), 256-byte aligned
+ *   stream          cudaStream_t (NULL = legacy default stream)
+ * Builds the weighted bin-integrated kernel table K_ij / sigma_i (Eq. correlation-model),
+ * the maximum-entropy start spectrum with the two sum rules, its residue chi2_0 and
+ * the temperature table, copies them to the workspace and starts every walker there.
+ * Synchronises the stream before returning.
+ */
+int sail_create(sail_t *out, const double *tau, const double *F, const double *sigma, int n_tau,
+                const double *omega, int n_omega, const sail_params *p, void *d_workspace,
+                size_t ws_bytes, void *stream);
+
+/*
+ * Runs up to max_blocks blocks of the schedule (Sec. 3): each block is
+ * sweeps_per_block sweeps of n_omega Metropolis moves per walker (Sec. 2.2, Eq.
+ * probability-density), with the residual recomputed every resync_every sweeps and
+ * at the block end, then imprinted branching (Sec. 2.5).  stats[max_blocks] (may be
+ * NULL) receives one record per block run; *n_done (may be NULL) the number run.
+ * Returns SAIL_OK, or SAIL_NOT_CONVERGED when target_chi2 > 0 and the schedule ended
+ * without reaching it.  One stream synchronisation per block.
+ */
+int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done);
+
+/*
+ * Stochastic average (Sec. 1): mean and standard error (sample std / sqrt(n)) per bin
+ * over the walkers with chi2 <= avg_chi2_factor * min chi2, and the chi2 of the mean
+ * spectrum.  S_mean, S_err: host arrays of n_omega (S_err may be NULL).  Branching
+ * correlates walkers, so the error is a lower bound.
+ */
+int sail_average(sail_t h, double *S_mean, double *S_err, int *n_used, double *chi2_of_mean);
+
+int sail_get_info(sail_t h, sail_info *info);
+
+/*
+ * Copies walker state to host arrays (any may be NULL): a[n_walkers * n_omega] spectra
+ * (the common scale folded in), R[n_walkers * n_tau] residuals F/sigma - K a / sigma,
+ * chi2[n_walkers], acc_prev[n_walkers] (accepted moves in the last sweep),
+ * hash[n_walkers] (FNV-1a of every move's outcome: 0 rejected, 1 accepted, 2 negative).
+ */
+int sail_get_state(sail_t h, double *a, double *R, double *chi2, int *acc_prev, uint64_t *hash);
+
+/*
+ * Replaces the spectra (a[n_walkers * n_omega], required) and optionally acc_prev;
+ * the residuals and chi2 are recomputed from them.  Sum rules are not enforced.
+ */
+int sail_set_state(sail_t h, const double *a, const int *acc_prev);
+
+/*
+ * Trace of a handle created with trace = 1: acc[sweeps_done * n_walkers] accepted
+ * moves per sweep and walker; m[n_events * n_walkers] branching multipliers and
+ * delta[n_events] (each may be NULL; n_events = number of branchings so far).
+ */
+int sail_get_trace(sail_t h, int *acc, int *m, double *delta, int *n_events);
+
+/*
+ * Evaluates n proposals on the current walker states with the handle's move
+ * arithmetic (Sec. 2.2) without changing them: walker[q], bins p[q] != s[q],
+ * eps[q] = 1 - r.  Writes ok[q] (0: a bin would go negative, 1: valid) and, for
+ * valid moves, delta[q] = the change of chi2.  Host arrays; 0 <= n <= 65536.
+ */
+int sail_delta_probe(sail_t h, int n, const int *walker, const int *p, const int *s,
+                     const double *eps, double *delta, int *ok);
+
+/* Device Philox4x32-10 (Salmon et al., SC'11) over n counters: d_ctr[4n] -> d_out[4n]
+ * (device pointers), key = seed.  The generator every kernel draws from. */
+int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, void *stream);
+
+/* Measurement utility for the roofline (no counterpart in the paper): every SM reads
+ * d_buf[0 .. bytes) reps times with 16-byte loads and writes a checksum to d_sink[0..7]
+ * (device pointers; d_buf 16-byte aligned, bytes a multiple of 16).  Timed by the caller
+ * on its stream, it gives the read bandwidth of L2 (a buffer far smaller than L2) or of
+ * HBM (a buffer far larger). */
+int sail_probe_read_bandwidth(const void *d_buf, size_t bytes, int reps, void *d_sink, void *stream);
+
+/* Frees the host side of the handle; the workspace stays the caller's. */
+int sail_destroy(sail_t h);
+
+/* Message of the last error on this thread ("" if none). */
+const char *sail_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAIL_H */

@@ -1,0 +1,8 @@
+"""GB300 library for SAIL, annealing inversion of the Laplace transform (arXiv:1609.07936).
+
+The computation lives in libsail.so (CUDA C++ for sm_103a, C ABI in
+include/sail.h); this package is its ctypes binding.  There is no CPU path:
+using the binding without a CUDA device or without the built library raises.
+"""
+from ._capi import (PREC_FP32, PREC_FP64, Params, Sail, SailError, load, philox,  # noqa: F401
+                    workspace_size)

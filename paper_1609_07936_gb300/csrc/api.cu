@@ -1,0 +1,678 @@
+// Host side of libsail: argument checks, the FP64 tables of Sec. 2.1-2.2, the start spectrum,
+// the workspace layout and the block loop of Sec. 3 (sweeps -> residual recomputation ->
+// imprinted branching -> statistics).  Compiled with -ffp-contract=off: host arithmetic
+// rounds every product and sum on its own.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sail.h"
+#include "sail_internal.cuh"
+
+using namespace sail;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(SAIL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SAIL_CUDA(call, what)                      \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+
+size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
+
+struct Layout {
+    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, Tsweep, a0, R0;
+    size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos;
+    size_t acc_trace, m_trace, delta_trace;
+    size_t m, zero_l, donor_l, n_pairs, delta, counters;
+    size_t mean, err, R_mean, chi2_mean, n_used, cut;
+    size_t pr_walker, pr_p, pr_s, pr_eps, pr_delta, pr_ok;
+    size_t total;
+    int max_events;
+};
+
+Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
+    Layout L{};
+    const size_t W = (size_t)p.n_walkers, NO = (size_t)n_omega;
+    const size_t PAD = (size_t)((n_tau + 31) / 32 * 32);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t at = off; off = align_up(off + (bytes ? bytes : 1)); return at; };
+    L.Khat64 = take(NO * PAD * 8);
+    L.Khat32 = take(NO * PAD * 4);
+    L.Fhat64 = take(PAD * 8);
+    L.Fhat32 = take(PAD * 4);
+    L.x64 = take(NO * 8);
+    L.beta32 = take(NO * 4);
+    L.Tsweep = take((size_t)p.n_sweeps * 8);
+    L.a0 = take(NO * 8);
+    L.R0 = take(PAD * 8);
+    if (p.precision == SAIL_PREC_FP64) {
+        L.a64 = take(W * NO * 8);
+        L.R64 = take(W * PAD * 8);
+    } else {
+        L.b32 = take(W * NO * 4);
+        L.g2 = take(W * 2 * 4);
+        L.R32 = take(W * PAD * 4);
+    }
+    L.chi2 = take(W * 8);
+    L.acc_prev = take(W * 4);
+    L.hash = take(W * 8);
+    L.n_acc = take(W * 8);
+    L.n_pos = take(W * 8);
+    L.max_events = p.n_sweeps / (p.sweeps_per_block > 0 ? p.sweeps_per_block : 1) + 1;
+    if (p.trace) {
+        L.acc_trace = take((size_t)p.n_sweeps * W * 4);
+        L.m_trace = take((size_t)L.max_events * W * 4);
+        L.delta_trace = take((size_t)L.max_events * 8);
+    }
+    L.m = take(W * 4);
+    L.zero_l = take(W * 4);
+    L.donor_l = take(W * 4);
+    L.n_pairs = take(4);
+    L.delta = take(8);
+    L.counters = take(sizeof(BlockCounters));
+    L.mean = take(NO * 8);
+    L.err = take(NO * 8);
+    L.R_mean = take(PAD * 8);
+    L.chi2_mean = take(8);
+    L.n_used = take(4);
+    L.cut = take(8);
+    L.pr_walker = take((size_t)kProbeMax * 4);
+    L.pr_p = take((size_t)kProbeMax * 4);
+    L.pr_s = take((size_t)kProbeMax * 4);
+    L.pr_eps = take((size_t)kProbeMax * 8);
+    L.pr_delta = take((size_t)kProbeMax * 8);
+    L.pr_ok = take((size_t)kProbeMax * 4);
+    L.total = off;
+    return L;
+}
+
+int check_params(int n_tau, int n_omega, const sail_params *p) {
+    if (!p) return fail(SAIL_EINVAL, "params is NULL");
+    if (n_tau < 1 || n_tau > kMaxTau) return fail(SAIL_EINVAL, "n_tau must be in [1, %d]", kMaxTau);
+    if (n_omega < 2 || n_omega > (1 << 20)) return fail(SAIL_EINVAL, "n_omega must be in [2, 2^20]");
+    if (p->n_walkers < 1 || p->n_walkers > kMaxWalkers)
+        return fail(SAIL_EINVAL, "n_walkers must be in [1, %d]", kMaxWalkers);
+    if (p->precision != SAIL_PREC_FP64 && p->precision != SAIL_PREC_FP32)
+        return fail(SAIL_EINVAL, "unknown precision %d", p->precision);
+    if (p->n_sweeps < 1 || p->sweeps_per_block < 1 || p->resync_every < 1)
+        return fail(SAIL_EINVAL, "n_sweeps, sweeps_per_block and resync_every must be >= 1");
+    if (!(p->T_start > 0) || !(p->T_end > 0) || !std::isfinite(p->T_start) || !std::isfinite(p->T_end))
+        return fail(SAIL_EINVAL, "temperatures must be finite and > 0");
+    if (!(p->branch_fraction >= 0 && p->branch_fraction < 1)) return fail(SAIL_EINVAL, "branch_fraction must be in [0, 1)");
+    if (!(p->imprint_t >= 0 && p->imprint_t <= 1)) return fail(SAIL_EINVAL, "imprint_t must be in [0, 1]");
+    if (!(p->y_p > 0 && p->y_p <= 1) || !(p->y_m >= 1) || !(p->y_min > 0 && p->y_min <= 1))
+        return fail(SAIL_EINVAL, "amplitude heuristic needs 0 < p <= 1, m >= 1, 0 < y_min <= 1");
+    if (!(p->move_scale < 1) || std::isnan(p->move_scale)) return fail(SAIL_EINVAL, "move_scale must be < 1");
+    if (!std::isfinite(p->B)) return fail(SAIL_EINVAL, "B must be given (Sec. 2.2)");
+    if (!(p->avg_chi2_factor >= 1)) return fail(SAIL_EINVAL, "avg_chi2_factor must be >= 1");
+    if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
+        return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
+    return SAIL_OK;
+}
+
+}  // namespace
+
+struct sail_ctx {
+    sail_params prm;
+    int n_tau, n_omega, pad;
+    double dw, A, B, lambda0, chi2_0;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    Layout L;
+    DevProblem P;
+    DevState S;
+    BranchScratch Bs;
+    std::vector<double> T;   // temperature table (host copy)
+    int sweeps_done, blocks_done, events;
+    long long launches, moves;
+    unsigned long long acc_seen, pos_seen;
+    // optional per-kernel timing: event pairs recorded around launches, read at block ends
+    struct Timed { cudaEvent_t a, b; int kind; };
+    std::vector<Timed> timed;
+    int n_timed;
+    double ms[3];
+    long long n_kind[3];
+};
+
+namespace {
+
+enum { kSweep = 0, kResync = 1, kBranch = 2 };
+
+int timed_begin(sail_ctx *h) {
+    if (!h->prm.timing) return -1;
+    if (h->n_timed == (int)h->timed.size()) {
+        sail_ctx::Timed t{};
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) return -1;
+        h->timed.push_back(t);
+    }
+    const int k = h->n_timed++;
+    cudaEventRecord(h->timed[k].a, h->stream);
+    return k;
+}
+
+void timed_end(sail_ctx *h, int k, int kind) {
+    if (k < 0) return;
+    cudaEventRecord(h->timed[k].b, h->stream);
+    h->timed[k].kind = kind;
+}
+
+// after a stream synchronisation: fold the recorded pairs into the totals
+void timed_collect(sail_ctx *h) {
+    for (int k = 0; k < h->n_timed; ++k) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->timed[k].a, h->timed[k].b) == cudaSuccess) {
+            h->ms[h->timed[k].kind] += ms;
+            h->n_kind[h->timed[k].kind] += 1;
+        }
+    }
+    h->n_timed = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sail_default_params(sail_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->n_walkers = 1024;
+    p->precision = SAIL_PREC_FP32;
+    p->n_sweeps = 20000;
+    p->sweeps_per_block = 100;
+    p->resync_every = 50;
+    p->branching = 1;
+    p->T_start = 10.0;
+    p->T_end = 1e-9;
+    p->branch_fraction = 0.25;
+    p->imprint_t = 0.1;
+    p->move_scale = 0.0;
+    p->y_p = 1.0;
+    p->y_m = 2.0;
+    p->y_min = 1e-4;
+    p->A = NAN;
+    p->B = NAN;
+    p->avg_chi2_factor = 1.5;
+    p->target_chi2 = 0.0;
+    p->seed = 0;
+    p->trace = 0;
+}
+
+const char *sail_last_error(void) { return g_err.c_str(); }
+
+int sail_workspace_size(int n_tau, int n_omega, const sail_params *p, size_t *bytes) {
+    if (!bytes) return fail(SAIL_EINVAL, "bytes is NULL");
+    sail_params q = *p;
+    if (!std::isfinite(q.B)) q.B = 0.0;  // size does not depend on B
+    const int rc = check_params(n_tau, n_omega, &q);
+    if (rc) return rc;
+    *bytes = make_layout(n_tau, n_omega, *p).total;
+    return SAIL_OK;
+}
+
+int sail_create(sail_t *out, const double *tau, const double *F, const double *sigma, int n_tau,
+                const double *omega, int n_omega, const sail_params *p, void *d_workspace, size_t ws_bytes,
+                void *stream) {
+    if (!out || !tau || !F || !sigma || !omega) return fail(SAIL_EINVAL, "NULL array argument");
+    *out = nullptr;
+    int rc = check_params(n_tau, n_omega, p);
+    if (rc) return rc;
+    if (!d_workspace) return fail(SAIL_EINVAL, "workspace is NULL");
+    if (((uintptr_t)d_workspace & 255) != 0) return fail(SAIL_EINVAL, "workspace must be 256-byte aligned");
+    const Layout L = make_layout(n_tau, n_omega, *p);
+    if (ws_bytes < L.total) return fail(SAIL_ENOMEM, "workspace has %zu bytes, needs %zu", ws_bytes, L.total);
+
+    // ---- grid and data (Sec. 2.1): equal bins of width dw starting at 0, centres x_j
+    const double dw = (omega[n_omega - 1] - omega[0]) / (double)(n_omega - 1);
+    if (!(dw > 0)) return fail(SAIL_EINVAL, "omega must increase");
+    for (int j = 0; j < n_omega; ++j)
+        if (!(std::fabs(omega[j] - (j + 0.5) * dw) <= 1e-9 * dw * (j + 1)))
+            return fail(SAIL_EINVAL, "omega[%d] is not the centre of bin %d of equal bins from 0", j, j);
+    for (int i = 0; i < n_tau; ++i) {
+        if (!(tau[i] >= 0) || !std::isfinite(tau[i])) return fail(SAIL_EINVAL, "tau[%d] must be finite and >= 0", i);
+        if (!(sigma[i] > 0) || !std::isfinite(sigma[i])) return fail(SAIL_EINVAL, "sigma[%d] must be finite and > 0", i);
+        if (!std::isfinite(F[i])) return fail(SAIL_EINVAL, "F[%d] is not finite", i);
+    }
+    double A = p->A;
+    const double B = p->B;
+    if (std::isnan(A)) {
+        // Sec. 2.2: F(0) = c_0 A with c_0 = dw / 2 pi
+        int i0 = -1;
+        for (int i = 0; i < n_tau; ++i) if (tau[i] == 0.0) { i0 = i; break; }
+        if (i0 < 0) return fail(SAIL_EINVAL, "A = NaN needs a point at tau = 0");
+        A = F[i0] / (dw / (2.0 * kPi));
+    }
+    if (!(A > 0) || !std::isfinite(A)) return fail(SAIL_EINVAL, "A must be finite and > 0");
+    const double x0 = omega[0], xN = omega[n_omega - 1];
+    if (!(B / A > x0 && B / A < xN))
+        return fail(SAIL_EINVAL, "B/A = %g lies outside the bin centres (%g, %g)", B / A, x0, xN);
+
+    const int PAD = (n_tau + 31) / 32 * 32;
+    const size_t NO = (size_t)n_omega;
+    // ---- weighted bin-integrated kernel, Eq. (correlation-model): column-major [j][i]
+    std::vector<double> K64(NO * PAD, 0.0), F64(PAD, 0.0);
+    std::vector<float> K32(NO * PAD, 0.0f), F32(PAD, 0.0f), beta(NO);
+    for (int i = 0; i < n_tau; ++i) {
+        for (int j = 0; j < n_omega; ++j) {
+            double Kij;
+            if (tau[i] == 0.0) Kij = dw / (2.0 * kPi);
+            else Kij = std::exp(-(double)j * dw * tau[i]) * (-std::expm1(-dw * tau[i])) / (2.0 * kPi * tau[i]);
+            K64[(size_t)j * PAD + i] = Kij / sigma[i];
+            K32[(size_t)j * PAD + i] = (float)(Kij / sigma[i]);
+        }
+        F64[i] = F[i] / sigma[i];
+        F32[i] = (float)F64[i];
+    }
+    for (int j = 0; j < n_omega; ++j) beta[j] = (float)(B - A * omega[j]);
+
+    // ---- start spectrum: largest entropy with sum a = A and sum a x = B, a_j ~ exp(-lambda x_j)
+    const double target = B / A, xc = 0.5 * (x0 + xN), span = xN - x0;
+    double lo = -700.0 / span, hi = 700.0 / span;
+    for (int it = 0; it < 400; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        double s0 = 0.0, s1 = 0.0;
+        for (int j = 0; j < n_omega; ++j) {
+            const double wgt = std::exp(-mid * (omega[j] - xc));
+            s0 += wgt;
+            s1 += wgt * omega[j];
+        }
+        if (s1 / s0 > target) lo = mid; else hi = mid;
+    }
+    const double lambda = 0.5 * (lo + hi);
+    std::vector<double> a0(NO);
+    double s0 = 0.0;
+    for (int j = 0; j < n_omega; ++j) { a0[j] = std::exp(-lambda * (omega[j] - xc)); s0 += a0[j]; }
+    for (int j = 0; j < n_omega; ++j) a0[j] = A * a0[j] / s0;
+    // residual and residue of the start spectrum (unit of T and chi2, Sec. 3)
+    std::vector<double> R0(PAD, 0.0);
+    double chi2_0 = 0.0;
+    for (int i = 0; i < n_tau; ++i) {
+        double model = 0.0;
+        for (int j = 0; j < n_omega; ++j) model += K64[(size_t)j * PAD + i] * a0[j];
+        R0[i] = F64[i] - model;
+        chi2_0 += R0[i] * R0[i];
+    }
+    // geometric temperature schedule in units of chi2_0
+    std::vector<double> T(p->n_sweeps);
+    for (int n = 0; n < p->n_sweeps; ++n) {
+        const double t = p->n_sweeps > 1 ? (double)n / (double)(p->n_sweeps - 1) : 0.0;
+        T[n] = chi2_0 * (p->T_start * std::pow(p->T_end / p->T_start, t));
+    }
+
+    sail_ctx *h = new sail_ctx();
+    h->prm = *p;
+    h->prm.A = A;
+    h->n_tau = n_tau;
+    h->n_omega = n_omega;
+    h->pad = PAD;
+    h->dw = dw;
+    h->A = A;
+    h->B = B;
+    h->lambda0 = lambda;
+    h->chi2_0 = chi2_0;
+    h->stream = (cudaStream_t)stream;
+    h->ws = (char *)d_workspace;
+    h->ws_bytes = ws_bytes;
+    h->L = L;
+    h->T = T;
+    char *ws = h->ws;
+    DevProblem &P = h->P;
+    P.n_tau = n_tau;
+    P.n_omega = n_omega;
+    P.n_walkers = p->n_walkers;
+    P.n_tau_pad = PAD;
+    P.n_sweeps = p->n_sweeps;
+    P.A = A;
+    P.B = B;
+    P.dw = dw;
+    P.move_scale = p->move_scale;
+    P.y_p = p->y_p;
+    P.y_m = p->y_m;
+    P.y_min = p->y_min;
+    P.seed = p->seed;
+    P.Khat64 = (const double *)(ws + L.Khat64);
+    P.Khat32 = (const float *)(ws + L.Khat32);
+    P.Fhat64 = (const double *)(ws + L.Fhat64);
+    P.Fhat32 = (const float *)(ws + L.Fhat32);
+    P.x64 = (const double *)(ws + L.x64);
+    P.beta32 = (const float *)(ws + L.beta32);
+    P.Tsweep = (const double *)(ws + L.Tsweep);
+    DevState &S = h->S;
+    S.a64 = p->precision == SAIL_PREC_FP64 ? (double *)(ws + L.a64) : nullptr;
+    S.R64 = p->precision == SAIL_PREC_FP64 ? (double *)(ws + L.R64) : nullptr;
+    S.b32 = p->precision == SAIL_PREC_FP32 ? (float *)(ws + L.b32) : nullptr;
+    S.g2 = p->precision == SAIL_PREC_FP32 ? (float *)(ws + L.g2) : nullptr;
+    S.R32 = p->precision == SAIL_PREC_FP32 ? (float *)(ws + L.R32) : nullptr;
+    S.chi2 = (double *)(ws + L.chi2);
+    S.acc_prev = (int *)(ws + L.acc_prev);
+    S.hash = (unsigned long long *)(ws + L.hash);
+    S.n_acc = (unsigned long long *)(ws + L.n_acc);
+    S.n_pos = (unsigned long long *)(ws + L.n_pos);
+    S.acc_trace = p->trace ? (int *)(ws + L.acc_trace) : nullptr;
+    BranchScratch &Bs = h->Bs;
+    Bs.m = (int *)(ws + L.m);
+    Bs.zero_l = (int *)(ws + L.zero_l);
+    Bs.donor_l = (int *)(ws + L.donor_l);
+    Bs.n_pairs = (int *)(ws + L.n_pairs);
+    Bs.delta = (double *)(ws + L.delta);
+    Bs.m_trace = p->trace ? (int *)(ws + L.m_trace) : nullptr;
+    Bs.delta_trace = p->trace ? (double *)(ws + L.delta_trace) : nullptr;
+
+    cudaStream_t st = h->stream;
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return cudaMemcpyAsync(ws + off, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    cudaError_t e = cudaSuccess;
+    std::vector<double> x(omega, omega + n_omega);
+    if (e == cudaSuccess) e = up(L.Khat64, K64.data(), K64.size() * 8);
+    if (e == cudaSuccess) e = up(L.Khat32, K32.data(), K32.size() * 4);
+    if (e == cudaSuccess) e = up(L.Fhat64, F64.data(), F64.size() * 8);
+    if (e == cudaSuccess) e = up(L.Fhat32, F32.data(), F32.size() * 4);
+    if (e == cudaSuccess) e = up(L.x64, x.data(), NO * 8);
+    if (e == cudaSuccess) e = up(L.beta32, beta.data(), NO * 4);
+    if (e == cudaSuccess) e = up(L.Tsweep, T.data(), T.size() * 8);
+    if (e == cudaSuccess) e = up(L.a0, a0.data(), NO * 8);
+    if (e == cudaSuccess) e = up(L.R0, R0.data(), PAD * 8);
+    if (e == cudaSuccess && p->trace)
+        e = cudaMemsetAsync(ws + L.acc_trace, 0, (size_t)p->n_sweeps * p->n_walkers * 4, st);
+    if (e == cudaSuccess)
+        e = launch_init_state(P, S, p->precision, (const double *)(ws + L.a0), (const double *)(ws + L.R0), chi2_0, st);
+    h->launches = 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "sail_create");
+    }
+    *out = h;
+    return SAIL_OK;
+}
+
+int sail_destroy(sail_t h) {
+    if (!h) return fail(SAIL_EINVAL, "NULL handle");
+    cudaStreamSynchronize(h->stream);
+    for (auto &t : h->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
+    delete h;
+    return SAIL_OK;
+}
+
+int sail_get_info(sail_t h, sail_info *info) {
+    if (!h || !info) return fail(SAIL_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->n_tau = h->n_tau;
+    info->n_omega = h->n_omega;
+    info->n_walkers = h->prm.n_walkers;
+    info->n_tau_pad = h->pad;
+    info->precision = h->prm.precision;
+    info->sweeps_done = h->sweeps_done;
+    info->blocks_done = h->blocks_done;
+    info->n_sweeps = h->prm.n_sweeps;
+    info->chi2_0 = h->chi2_0;
+    info->d_omega = h->dw;
+    info->A = h->A;
+    info->B = h->B;
+    info->lambda0 = h->lambda0;
+    info->kernel_launches = h->launches;
+    info->workspace_bytes = h->L.total;
+    info->sweep_ms = h->ms[kSweep];
+    info->resync_ms = h->ms[kResync];
+    info->branch_ms = h->ms[kBranch];
+    info->sweep_launches = h->n_kind[kSweep];
+    info->resync_launches = h->n_kind[kResync];
+    info->branch_launches = h->n_kind[kBranch];
+    info->moves = h->moves;
+    return SAIL_OK;
+}
+
+namespace {
+
+int average_to_host(sail_t h, double *mean, double *err, int *n_used, double *chi2_mean) {
+    char *ws = h->ws;
+    int l = 0;
+    cudaError_t e = launch_average(h->P, h->S, h->prm.precision, h->prm.avg_chi2_factor,
+                                   (double *)(ws + h->L.mean), (double *)(ws + h->L.err), (int *)(ws + h->L.n_used),
+                                   (double *)(ws + h->L.cut), (double *)(ws + h->L.R_mean),
+                                   (double *)(ws + h->L.chi2_mean), h->stream, &l);
+    h->launches += l;
+    if (e != cudaSuccess) return cuda_fail(e, "average");
+    const size_t NO = (size_t)h->n_omega;
+    if (mean) SAIL_CUDA(cudaMemcpyAsync(mean, ws + h->L.mean, NO * 8, cudaMemcpyDeviceToHost, h->stream), "average D2H");
+    if (err) SAIL_CUDA(cudaMemcpyAsync(err, ws + h->L.err, NO * 8, cudaMemcpyDeviceToHost, h->stream), "average D2H");
+    int nu = 0;
+    double c2 = 0;
+    SAIL_CUDA(cudaMemcpyAsync(&nu, ws + h->L.n_used, 4, cudaMemcpyDeviceToHost, h->stream), "average D2H");
+    SAIL_CUDA(cudaMemcpyAsync(&c2, ws + h->L.chi2_mean, 8, cudaMemcpyDeviceToHost, h->stream), "average D2H");
+    SAIL_CUDA(cudaStreamSynchronize(h->stream), "average sync");
+    if (n_used) *n_used = nu;
+    if (chi2_mean) *chi2_mean = c2;
+    return SAIL_OK;
+}
+
+}  // namespace
+
+int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) {
+    if (!h) return fail(SAIL_EINVAL, "NULL handle");
+    if (max_blocks < 0) return fail(SAIL_EINVAL, "max_blocks < 0");
+    const sail_params &p = h->prm;
+    const int k = p.sweeps_per_block;
+    int done = 0;
+    bool reached = false;
+    cudaStream_t st = h->stream;
+    while (done < max_blocks && h->sweeps_done < p.n_sweeps && !reached) {
+        const int n_begin = h->sweeps_done;
+        const int block_end = std::min((n_begin / k + 1) * k, p.n_sweeps);
+        int n = n_begin;
+        while (n < block_end) {
+            const int next = std::min((n / p.resync_every + 1) * p.resync_every, block_end);
+            int tk = timed_begin(h);
+            cudaError_t e = p.precision == SAIL_PREC_FP64 ? launch_sweep_fp64(h->P, h->S, n, next, st)
+                                                          : launch_sweep_fp32(h->P, h->S, n, next, st);
+            timed_end(h, tk, kSweep);
+            if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
+            tk = timed_begin(h);
+            e = launch_resync(h->P, h->S, p.precision, st);
+            timed_end(h, tk, kResync);
+            if (e != cudaSuccess) return cuda_fail(e, "resync launch");
+            h->launches += 2;
+            h->moves += (long long)(next - n) * p.n_walkers * h->n_omega;
+            n = next;
+        }
+        h->sweeps_done = block_end;
+        double delta = 0.0;
+        int zeros = 0;
+        const bool branched = p.branching && p.n_walkers > 1 && (block_end % k) == 0;
+        if (branched) {
+            int l = 0;
+            const int tk = timed_begin(h);
+            cudaError_t e = launch_branch(h->P, h->S, h->Bs, p.precision, block_end / k - 1, p.branch_fraction,
+                                          p.imprint_t, h->events, st, &l);
+            timed_end(h, tk, kBranch);
+            h->launches += l;
+            if (e != cudaSuccess) return cuda_fail(e, "branch launch");
+            h->events += 1;
+        }
+        cudaError_t e = launch_block_stats(h->P, h->S, (BlockCounters *)(h->ws + h->L.counters), st);
+        h->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(e, "stats launch");
+        BlockCounters bc{};
+        SAIL_CUDA(cudaMemcpyAsync(&bc, h->ws + h->L.counters, sizeof bc, cudaMemcpyDeviceToHost, st), "stats D2H");
+        if (branched) {
+            SAIL_CUDA(cudaMemcpyAsync(&delta, h->ws + h->L.delta, 8, cudaMemcpyDeviceToHost, st), "stats D2H");
+            SAIL_CUDA(cudaMemcpyAsync(&zeros, h->ws + h->L.n_pairs, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
+        }
+        SAIL_CUDA(cudaStreamSynchronize(st), "block sync");
+        timed_collect(h);
+        if (stats) {
+            sail_block_stats &s = stats[done];
+            std::memset(&s, 0, sizeof s);
+            const double proposed = (double)(block_end - n_begin) * p.n_walkers * h->n_omega;
+            s.block = h->blocks_done;
+            s.sweep_end = block_end;
+            s.T = h->T[block_end - 1];
+            s.chi2_min = bc.chi2_min;
+            s.chi2_mean = bc.chi2_sum / p.n_walkers;
+            s.acceptance = (double)(bc.acc - h->acc_seen) / proposed;
+            s.positivity_rejected = (double)(bc.pos - h->pos_seen) / proposed;
+            s.branch_delta = delta;
+            s.branch_zeros = zeros;
+        }
+        h->acc_seen = bc.acc;
+        h->pos_seen = bc.pos;
+        h->blocks_done += 1;
+        done += 1;
+        if (p.target_chi2 > 0) {
+            double c2 = 0;
+            const int rc = average_to_host(h, nullptr, nullptr, nullptr, &c2);
+            if (rc) return rc;
+            reached = c2 <= p.target_chi2;
+        }
+    }
+    if (n_done) *n_done = done;
+    if (p.target_chi2 > 0 && !reached && h->sweeps_done >= p.n_sweeps) return SAIL_NOT_CONVERGED;
+    return SAIL_OK;
+}
+
+int sail_average(sail_t h, double *S_mean, double *S_err, int *n_used, double *chi2_of_mean) {
+    if (!h || !S_mean) return fail(SAIL_EINVAL, "NULL argument");
+    return average_to_host(h, S_mean, S_err, n_used, chi2_of_mean);
+}
+
+int sail_get_state(sail_t h, double *a, double *R, double *chi2, int *acc_prev, uint64_t *hash) {
+    if (!h) return fail(SAIL_EINVAL, "NULL handle");
+    const size_t W = (size_t)h->prm.n_walkers, NO = (size_t)h->n_omega, PAD = (size_t)h->pad;
+    cudaStream_t st = h->stream;
+    char *ws = h->ws;
+    const bool f64 = h->prm.precision == SAIL_PREC_FP64;
+    std::vector<float> fbuf;
+    std::vector<double> rbuf;
+    if (a) {
+        if (f64) SAIL_CUDA(cudaMemcpyAsync(a, ws + h->L.a64, W * NO * 8, cudaMemcpyDeviceToHost, st), "D2H");
+        else { fbuf.resize(W * NO); SAIL_CUDA(cudaMemcpyAsync(fbuf.data(), ws + h->L.b32, W * NO * 4, cudaMemcpyDeviceToHost, st), "D2H"); }
+    }
+    std::vector<float> rf;
+    if (R) {
+        if (f64) { rbuf.resize(W * PAD); SAIL_CUDA(cudaMemcpyAsync(rbuf.data(), ws + h->L.R64, W * PAD * 8, cudaMemcpyDeviceToHost, st), "D2H"); }
+        else { rf.resize(W * PAD); SAIL_CUDA(cudaMemcpyAsync(rf.data(), ws + h->L.R32, W * PAD * 4, cudaMemcpyDeviceToHost, st), "D2H"); }
+    }
+    if (chi2) SAIL_CUDA(cudaMemcpyAsync(chi2, ws + h->L.chi2, W * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    if (acc_prev) SAIL_CUDA(cudaMemcpyAsync(acc_prev, ws + h->L.acc_prev, W * 4, cudaMemcpyDeviceToHost, st), "D2H");
+    if (hash) SAIL_CUDA(cudaMemcpyAsync(hash, ws + h->L.hash, W * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    SAIL_CUDA(cudaStreamSynchronize(st), "get_state sync");
+    if (a && !f64) for (size_t q = 0; q < W * NO; ++q) a[q] = (double)fbuf[q];
+    if (R) {
+        for (size_t w = 0; w < W; ++w)
+            for (int i = 0; i < h->n_tau; ++i)
+                R[w * h->n_tau + i] = f64 ? rbuf[w * PAD + i] : (double)rf[w * PAD + i];
+    }
+    return SAIL_OK;
+}
+
+int sail_set_state(sail_t h, const double *a, const int *acc_prev) {
+    if (!h || !a) return fail(SAIL_EINVAL, "NULL argument");
+    const size_t W = (size_t)h->prm.n_walkers, NO = (size_t)h->n_omega;
+    cudaStream_t st = h->stream;
+    char *ws = h->ws;
+    std::vector<float> fbuf, g;
+    if (h->prm.precision == SAIL_PREC_FP64) {
+        SAIL_CUDA(cudaMemcpyAsync(ws + h->L.a64, a, W * NO * 8, cudaMemcpyHostToDevice, st), "H2D");
+    } else {
+        fbuf.resize(W * NO);
+        for (size_t q = 0; q < W * NO; ++q) fbuf[q] = (float)a[q];
+        g.resize(2 * W);
+        for (size_t w = 0; w < W; ++w) { g[2 * w] = 1.0f; g[2 * w + 1] = 0.0f; }
+        SAIL_CUDA(cudaMemcpyAsync(ws + h->L.b32, fbuf.data(), W * NO * 4, cudaMemcpyHostToDevice, st), "H2D");
+        SAIL_CUDA(cudaMemcpyAsync(ws + h->L.g2, g.data(), W * 2 * 4, cudaMemcpyHostToDevice, st), "H2D");
+    }
+    if (acc_prev) SAIL_CUDA(cudaMemcpyAsync(ws + h->L.acc_prev, acc_prev, W * 4, cudaMemcpyHostToDevice, st), "H2D");
+    SAIL_CUDA(launch_resync(h->P, h->S, h->prm.precision, st), "resync launch");
+    h->launches += 1;
+    SAIL_CUDA(cudaStreamSynchronize(st), "set_state sync");
+    return SAIL_OK;
+}
+
+int sail_get_trace(sail_t h, int *acc, int *m, double *delta, int *n_events) {
+    if (!h) return fail(SAIL_EINVAL, "NULL handle");
+    if (!h->prm.trace) return fail(SAIL_ESTATE, "handle was created without trace");
+    const size_t W = (size_t)h->prm.n_walkers;
+    cudaStream_t st = h->stream;
+    if (acc && h->sweeps_done > 0)
+        SAIL_CUDA(cudaMemcpyAsync(acc, h->ws + h->L.acc_trace, (size_t)h->sweeps_done * W * 4, cudaMemcpyDeviceToHost, st), "D2H");
+    if (m && h->events > 0)
+        SAIL_CUDA(cudaMemcpyAsync(m, h->ws + h->L.m_trace, (size_t)h->events * W * 4, cudaMemcpyDeviceToHost, st), "D2H");
+    if (delta && h->events > 0)
+        SAIL_CUDA(cudaMemcpyAsync(delta, h->ws + h->L.delta_trace, (size_t)h->events * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    SAIL_CUDA(cudaStreamSynchronize(st), "trace sync");
+    if (n_events) *n_events = h->events;
+    return SAIL_OK;
+}
+
+int sail_delta_probe(sail_t h, int n, const int *walker, const int *p, const int *s, const double *eps,
+                     double *delta, int *ok) {
+    if (!h) return fail(SAIL_EINVAL, "NULL handle");
+    if (n < 0 || n > kProbeMax) return fail(SAIL_EINVAL, "n must be in [0, %d]", kProbeMax);
+    if (n == 0) return SAIL_OK;
+    if (!walker || !p || !s || !eps || !delta || !ok) return fail(SAIL_EINVAL, "NULL array argument");
+    for (int q = 0; q < n; ++q) {
+        if (walker[q] < 0 || walker[q] >= h->prm.n_walkers || p[q] < 0 || p[q] >= h->n_omega || s[q] < 0 ||
+            s[q] >= h->n_omega || p[q] == s[q] || !(std::fabs(eps[q]) < 1.0))
+            return fail(SAIL_EINVAL, "proposal %d out of range", q);
+    }
+    cudaStream_t st = h->stream;
+    char *ws = h->ws;
+    SAIL_CUDA(cudaMemcpyAsync(ws + h->L.pr_walker, walker, (size_t)n * 4, cudaMemcpyHostToDevice, st), "H2D");
+    SAIL_CUDA(cudaMemcpyAsync(ws + h->L.pr_p, p, (size_t)n * 4, cudaMemcpyHostToDevice, st), "H2D");
+    SAIL_CUDA(cudaMemcpyAsync(ws + h->L.pr_s, s, (size_t)n * 4, cudaMemcpyHostToDevice, st), "H2D");
+    SAIL_CUDA(cudaMemcpyAsync(ws + h->L.pr_eps, eps, (size_t)n * 8, cudaMemcpyHostToDevice, st), "H2D");
+    SAIL_CUDA(launch_probe(h->P, h->S, h->prm.precision, n, (const int *)(ws + h->L.pr_walker),
+                           (const int *)(ws + h->L.pr_p), (const int *)(ws + h->L.pr_s),
+                           (const double *)(ws + h->L.pr_eps), (double *)(ws + h->L.pr_delta),
+                           (int *)(ws + h->L.pr_ok), st),
+              "probe launch");
+    h->launches += 1;
+    SAIL_CUDA(cudaMemcpyAsync(delta, ws + h->L.pr_delta, (size_t)n * 8, cudaMemcpyDeviceToHost, st), "D2H");
+    SAIL_CUDA(cudaMemcpyAsync(ok, ws + h->L.pr_ok, (size_t)n * 4, cudaMemcpyDeviceToHost, st), "D2H");
+    SAIL_CUDA(cudaStreamSynchronize(st), "probe sync");
+    return SAIL_OK;
+}
+
+int sail_probe_read_bandwidth(const void *d_buf, size_t bytes, int reps, void *d_sink, void *stream) {
+    if (!d_buf || !d_sink || reps < 1 || bytes < 16 || (bytes & 15) || ((uintptr_t)d_buf & 15))
+        return fail(SAIL_EINVAL, "read probe needs a 16-byte aligned buffer of 16k bytes and reps >= 1");
+    SAIL_CUDA(launch_read_probe(d_buf, bytes, reps, d_sink, (cudaStream_t)stream), "read probe launch");
+    return SAIL_OK;
+}
+
+int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, void *stream) {
+    if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(SAIL_EINVAL, "bad arguments");
+    SAIL_CUDA(launch_philox(n, d_ctr, seed, d_out, (cudaStream_t)stream), "philox launch");
+    return SAIL_OK;
+}
+
+}  // extern "C"

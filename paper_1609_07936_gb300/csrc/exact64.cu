@@ -1,0 +1,708 @@
+// FP64 kernels whose every operation is rounded on its own (this file is compiled with
+// -fmad=false): the validation sweep, the residual recomputation, the branching solve and
+// imprint, the stochastic average and the state initialisation.  Sums run in the order the
+// method's definition states them (j ascending for a model value, i ascending for chi2,
+// walkers ascending for an average), so these kernels reproduce a plain sequential FP64
+// evaluation of the same formulas bit for bit, up to the library exp of the Metropolis test.
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "moves.cuh"
+#include "philox.cuh"
+#include "sail_internal.cuh"
+
+namespace sail {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// ------------------------------------------------------------------ state set-up
+__global__ void init_state_kernel(DevProblem P, DevState S, int precision, const double *a0,
+                                  const double *R0, double chi2_0) {
+    const int w = blockIdx.x;
+    if (w >= P.n_walkers) return;
+    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x) {
+        if (precision == 0) S.a64[(size_t)w * P.n_omega + j] = a0[j];
+        else S.b32[(size_t)w * P.n_omega + j] = (float)a0[j];
+    }
+    for (int i = threadIdx.x; i < P.n_tau_pad; i += blockDim.x) {
+        const double r = i < P.n_tau ? R0[i] : 0.0;
+        if (precision == 0) S.R64[(size_t)w * P.n_tau_pad + i] = r;
+        else S.R32[(size_t)w * P.n_tau_pad + i] = (float)r;
+    }
+    if (threadIdx.x == 0) {
+        S.chi2[w] = chi2_0;
+        S.acc_prev[w] = P.n_omega;
+        S.hash[w] = kFnvOffset;
+        S.n_acc[w] = 0;
+        S.n_pos[w] = 0;
+        if (precision != 0) {
+            S.g2[2 * w] = 1.0f;
+            S.g2[2 * w + 1] = 0.0f;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ validation sweep
+// One warp per walker.  Lane l holds R_i for i = l + 32 c.  Every move is Sec. 2.2:
+//   eps = 1 - r, delta_p = eps (B - A x_s) / (x_p - x_s), delta_s = eps (B - A x_p) / (x_s - x_p),
+//   a_p' = r a_p + delta_p, a_s' = r a_s + delta_s (rejected if either is negative),
+//   d_i = eps (Fhat_i - R_i) - delta_p Khat_ip - delta_s Khat_is,
+//   Delta chi2 = sum_i d_i (2 R_i + d_i), summed over i ascending,
+// accepted with probability min(1, exp(-Delta chi2 / T)) (Eq. probability-density); an
+// accepted move rescales every bin by r, writes a_p', a_s' and adds d to R.
+template <int C>
+__global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState S, int n0, int n1) {
+    const int lane = threadIdx.x & 31;
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (w >= P.n_walkers) return;
+    const int NT = P.n_tau, NO = P.n_omega, PAD = P.n_tau_pad;
+    double *a = S.a64 + (size_t)w * NO;
+    double R[C], Fh[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        R[c] = S.R64[(size_t)w * PAD + lane + 32 * c];
+        Fh[c] = P.Fhat64[lane + 32 * c];
+    }
+    double chi2 = S.chi2[w];
+    int accp = S.acc_prev[w];
+    unsigned long long h = S.hash[w], nacc = 0, npos = 0;
+    const uint2 key = philox_key(P.seed);
+    const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
+
+    for (int n = n0; n < n1; ++n) {
+        const double T = P.Tsweep[n];
+        const double y = amplitude(accp, NO, P.y_p, P.y_m, P.y_min);
+        int acc = 0;
+        for (int mv = 0; mv < NO; ++mv) {
+            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u), key);
+            int p, s;
+            move_bins(rnd.x, rnd.y, NO, p, s);
+            const double eps = (y * dmove) * (2.0 * unit64(rnd.z) - 1.0);
+            const double u = unit64(rnd.w);
+            const double r = 1.0 - eps;
+            const double xp = P.x64[p], xs = P.x64[s];
+            const double dp = eps * (P.B - P.A * xs) / (xp - xs);
+            const double ds = eps * (P.B - P.A * xp) / (xs - xp);
+            const double ap = r * a[p] + dp;
+            const double as = r * a[s] + ds;
+            unsigned code;
+            if (ap < 0.0 || as < 0.0) {
+                code = 2;
+                ++npos;
+            } else {
+                const double *Kp = P.Khat64 + (size_t)p * PAD;
+                const double *Ks = P.Khat64 + (size_t)s * PAD;
+                double d[C], t[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const int i = lane + 32 * c;
+                    const double M = Fh[c] - R[c];
+                    d[c] = eps * M - dp * Kp[i] - ds * Ks[i];
+                    t[c] = d[c] * (2.0 * R[c] + d[c]);
+                }
+                double D = 0.0;
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    for (int l = 0; l < 32; ++l) {
+                        const double v = __shfl_sync(kFull, t[c], l);
+                        if (32 * c + l < NT) D = D + v;
+                    }
+                }
+                if (D <= 0.0 || u < exp(-D / T)) {
+                    for (int j = lane; j < NO; j += 32) a[j] = r * a[j];
+                    __syncwarp();
+                    if (lane == 0) {
+                        a[p] = ap;
+                        a[s] = as;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int c = 0; c < C; ++c) R[c] = R[c] + d[c];
+                    chi2 = chi2 + D;
+                    ++acc;
+                    code = 1;
+                } else {
+                    code = 0;
+                }
+            }
+            h = (h ^ code) * kFnvPrime;
+        }
+        accp = acc;
+        nacc += acc;
+        if (S.acc_trace && lane == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) S.R64[(size_t)w * PAD + lane + 32 * c] = R[c];
+    if (lane == 0) {
+        S.chi2[w] = chi2;
+        S.acc_prev[w] = accp;
+        S.hash[w] = h;
+        S.n_acc[w] += nacc;
+        S.n_pos[w] += npos;
+    }
+}
+
+// ------------------------------------------------------------------ residual recomputation
+// R_i = Fhat_i - sum_j Khat_ij a_j with j ascending, chi2 = sum_i R_i^2 with i ascending.
+// One block per walker.  FP32 state enters as (double) b_j; the sweep kernel folds its
+// common scale into b before this runs.
+//
+// FP32 state only: rounding in the moves lets sum a and sum a x wander by ~1e-6 of A and B
+// over a resync interval (exact arithmetic keeps them fixed, Sec. 2.2).  Before the
+// residual is formed the spectrum is put back on both sum rules by the smallest affine
+// reweighting a_j <- a_j kappa (1 + lambda (x_j - c)), c = sum a x / sum a, with
+// kappa = A / sum a and lambda = (B/A - c) / var, which changes each bin by a factor
+// 1 + O(1e-6) and keeps a >= 0.
+__device__ void block_sum2(double &u, double &v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        u += __shfl_xor_sync(kFull, u, o);
+        v += __shfl_xor_sync(kFull, v, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
+    __syncthreads();
+    if (lane == 0) { red[warp] = u; red[32 + warp] = v; }
+    __syncthreads();
+    u = 0.0;
+    v = 0.0;
+    for (int k = 0; k < nw; ++k) { u += red[k]; v += red[32 + k]; }
+}
+
+__device__ void restore_sum_rules(const DevProblem &P, float *b, double *red) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x) {
+        s0 += (double)b[j];
+        s1 += (double)b[j] * P.x64[j];
+    }
+    block_sum2(s0, s1, red);
+    if (!(s0 > 0.0)) return;
+    const double c = s1 / s0;
+    double v2 = 0.0, unused = 0.0;
+    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x) {
+        const double dx = P.x64[j] - c;
+        v2 += (double)b[j] * dx * dx;
+    }
+    block_sum2(v2, unused, red);
+    const double var = v2 / s0;
+    const double kappa = P.A / s0;
+    double lambda = var > 0.0 ? (P.B / P.A - c) / var : 0.0;
+    if (!(fabs(lambda * (P.x64[P.n_omega - 1] - P.x64[0])) < 0.5)) lambda = 0.0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x)
+        b[j] = (float)((double)b[j] * (kappa * (1.0 + lambda * (P.x64[j] - c))));
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) resync_kernel(DevProblem P, DevState S, int precision) {
+    __shared__ double Rs[kMaxTau];
+    __shared__ double red[64];
+    const int w = blockIdx.x;
+    const int NO = P.n_omega, PAD = P.n_tau_pad;
+    if (precision != 0) restore_sum_rules(P, S.b32 + (size_t)w * NO, red);
+    for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+        double r = 0.0;
+        if (i < P.n_tau) {
+            double model = 0.0;
+            if (precision == 0) {
+                const double *a = S.a64 + (size_t)w * NO;
+                for (int j = 0; j < NO; ++j) model = model + P.Khat64[(size_t)j * PAD + i] * a[j];
+            } else {
+                const float *b = S.b32 + (size_t)w * NO;
+                for (int j = 0; j < NO; ++j) model = model + P.Khat64[(size_t)j * PAD + i] * (double)b[j];
+            }
+            r = P.Fhat64[i] - model;
+        }
+        Rs[i] = r;
+        if (precision == 0) S.R64[(size_t)w * PAD + i] = r;
+        else S.R32[(size_t)w * PAD + i] = (float)r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c2 = 0.0;
+        for (int i = 0; i < P.n_tau; ++i) c2 = c2 + Rs[i] * Rs[i];
+        S.chi2[w] = c2;
+    }
+}
+
+// ------------------------------------------------------------------ branching (Sec. 2.5)
+// Walker l has weight w_l = exp[-Delta (z_l - P_r)], z_l = (chi2_l - min) / (mean - min), and
+// multiplier m_l = floor(w_l + xi_l).  Writing Theta = exp(Delta P_r) and E_l = exp(-Delta z_l),
+// m_l = floor(Theta E_l + xi_l), which steps up by one at each "break point"
+// Delta z_l + ln(k - xi_l) = ln Theta, k = 1, 2, ...  P_r is fixed by sum m = N: ln Theta lies
+// between the N-th and (N+1)-th smallest break points of all walkers, found by bisection on
+// ln Theta until the count is exactly N.  Z(Delta) = #{m_l = 0}; Delta doubles from 1 until
+// Z >= round(f N), then bisects, stopping at the first Delta with Z = round(f N).
+struct SolveShared {
+    double red_d[32];
+    int red_i[32];
+    double bcast_d;
+    int bcast_i;
+    double theta;
+    double cmin, spread;
+    int scan[kSolveThreads / 32];
+};
+
+__device__ double block_sum_d(double v, SolveShared &sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh.red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh.red_d[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) sh.bcast_d = v;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
+
+__device__ int block_sum_i(int v, SolveShared &sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh.red_i[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh.red_i[lane] : 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+        if (lane == 0) sh.bcast_i = v;
+    }
+    __syncthreads();
+    return sh.bcast_i;
+}
+
+// Exclusive prefix sum over the block in thread order; returns this thread's offset and
+// writes the total to *total.
+__device__ int block_scan_excl(int v, int *total, SolveShared &sh) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    __syncthreads();
+    if (lane == 31) sh.scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        int x = lane < nw ? sh.scan[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < nw) sh.scan[lane] = x;  // inclusive over warps
+    }
+    __syncthreads();
+    const int warp_off = warp > 0 ? sh.scan[warp - 1] : 0;
+    *total = sh.scan[(blockDim.x >> 5) - 1];
+    return warp_off + incl - v;
+}
+
+// Multipliers at one Delta; returns Z.  Walker l = threadIdx.x + kSolveThreads * q.
+__device__ int multipliers_at(int N, const double *z, const double *xi, double Delta, int *m,
+                              SolveShared &sh) {
+    const int tid = threadIdx.x;
+    double E[kSolvePerThread];
+    double sE = 0.0;
+#pragma unroll
+    for (int q = 0; q < kSolvePerThread; ++q) {
+        const int l = tid + kSolveThreads * q;
+        E[q] = l < N ? exp(-Delta * z[q]) : 0.0;
+        sE += E[q];
+    }
+    sE = block_sum_d(sE, sh);
+    auto count_at = [&](double lnTheta, bool store) -> int {
+        if (tid < 32) {
+            const double Th = exp(lnTheta);
+            if (tid == 0) sh.theta = Th;
+        }
+        __syncthreads();
+        const double Th = sh.theta;
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < kSolvePerThread; ++q) {
+            const int l = tid + kSolveThreads * q;
+            int mq = 0;
+            if (l < N) {
+                const double v = floor(Th * E[q] + xi[q]);
+                mq = v >= (double)N ? N : (int)v;
+            }
+            if (store) m[q] = mq;
+            c += mq;
+        }
+        return block_sum_i(c, sh);
+    };
+    // Sum m is close to Theta * sum E; bracket ln Theta around ln(N / sum E).
+    const double guess = log((double)N / sE);
+    double lo = guess - 0.25, hi = guess + 0.25;
+    int clo = count_at(lo, false), chi = count_at(hi, false);
+    for (int it = 0; it < 200 && clo >= N; ++it) { lo -= (hi - lo); clo = count_at(lo, false); }
+    for (int it = 0; it < 200 && chi < N; ++it) { hi += (hi - lo); chi = count_at(hi, false); }
+    bool hit = false;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        const int c = count_at(mid, true);
+        if (c == N) { hit = true; break; }
+        if (c < N) lo = mid; else hi = mid;
+    }
+    if (!hit) {
+        // Break points tied at ln Theta: take the upper end and drop the surplus copies
+        // from the highest walker indices whose count rises across the final bracket.
+        int c = count_at(hi, true);
+        int mlo[kSolvePerThread];
+        {
+            if (tid < 32) { const double Th = exp(lo); if (tid == 0) sh.theta = Th; }
+            __syncthreads();
+            const double Th = sh.theta;
+#pragma unroll
+            for (int q = 0; q < kSolvePerThread; ++q) {
+                const int l = tid + kSolveThreads * q;
+                const double v = l < N ? floor(Th * E[q] + xi[q]) : 0.0;
+                mlo[q] = v >= (double)N ? N : (int)v;
+            }
+            __syncthreads();
+        }
+        for (int q = kSolvePerThread - 1; q >= 0 && c > N; --q) {
+            for (int t = kSolveThreads - 1; t >= 0 && c > N; --t) {
+                // serial over walkers in descending index order; thread t owns walker l
+                if (tid == t) {
+                    const int l = t + kSolveThreads * q;
+                    int take = 0;
+                    if (l < N) {
+                        const int extra = m[q] - mlo[q];
+                        take = extra < (c - N) ? extra : (c - N);
+                        m[q] -= take;
+                    }
+                    sh.bcast_i = take;
+                }
+                __syncthreads();
+                c -= sh.bcast_i;
+                __syncthreads();
+            }
+        }
+    }
+    int zc = 0;
+#pragma unroll
+    for (int q = 0; q < kSolvePerThread; ++q) {
+        const int l = tid + kSolveThreads * q;
+        zc += (l < N && m[q] == 0);
+    }
+    return block_sum_i(zc, sh);
+}
+
+__global__ void __launch_bounds__(kSolveThreads) branch_solve_kernel(DevProblem P, DevState S,
+                                                                     BranchScratch B, int block_index,
+                                                                     double fraction, int event) {
+    __shared__ SolveShared sh;
+    const int N = P.n_walkers, tid = threadIdx.x;
+    int Zt = (int)floor(fraction * N + 0.5);
+    if (Zt > N - 1) Zt = N - 1;
+    int m[kSolvePerThread];
+    double Delta = 0.0;
+    if (Zt <= 0) {
+#pragma unroll
+        for (int q = 0; q < kSolvePerThread; ++q) m[q] = 1;
+    } else {
+        if (tid == 0) {
+            double cmin = S.chi2[0], csum = 0.0;
+            for (int l = 0; l < N; ++l) {
+                if (S.chi2[l] < cmin) cmin = S.chi2[l];
+                csum += S.chi2[l];
+            }
+            sh.cmin = cmin;
+            sh.spread = csum / N - cmin;
+        }
+        __syncthreads();
+        const double cmin = sh.cmin, spread = sh.spread;
+        double z[kSolvePerThread], xi[kSolvePerThread];
+        const uint2 key = philox_key(P.seed);
+#pragma unroll
+        for (int q = 0; q < kSolvePerThread; ++q) {
+            const int l = tid + kSolveThreads * q;
+            z[q] = 0.0;
+            xi[q] = 0.5;
+            if (l < N) {
+                z[q] = spread > 0.0 ? (S.chi2[l] - cmin) / spread : 0.0;
+                xi[q] = unit64(philox4x32_10(make_uint4((uint32_t)l, (uint32_t)block_index, 0u, 1u), key).x);
+            }
+        }
+        double lo = 0.0, hi = 1.0;
+        int Zhi = multipliers_at(N, z, xi, hi, m, sh);
+        for (int it = 0; it < 64 && Zhi < Zt; ++it) {
+            lo = hi;
+            hi = 2.0 * hi;
+            Zhi = multipliers_at(N, z, xi, hi, m, sh);
+        }
+        if (Zhi != Zt) {
+            for (int it = 0; it < 64; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                const int Zm = multipliers_at(N, z, xi, mid, m, sh);
+                if (Zm == Zt) { hi = mid; Zhi = Zm; break; }
+                if (Zm < Zt) lo = mid; else { hi = mid; Zhi = Zm; }
+            }
+        }
+        multipliers_at(N, z, xi, hi, m, sh);
+        Delta = hi;
+    }
+    // Pairing: zero-multiplier walkers ascending, matched with surplus copies (walker l
+    // listed m_l - 1 times) ascending.  Walker order is q-major, thread-minor.
+    int zero_base = 0, copy_base = 0;
+#pragma unroll
+    for (int q = 0; q < kSolvePerThread; ++q) {
+        const int l = tid + kSolveThreads * q;
+        const bool valid = l < N;
+        const int isz = valid && m[q] == 0;
+        const int surplus = valid && m[q] > 1 ? m[q] - 1 : 0;
+        int tz, tc;
+        const int zo = block_scan_excl(isz, &tz, sh);
+        const int co = block_scan_excl(surplus, &tc, sh);
+        if (valid) {
+            B.m[l] = m[q];
+            if (isz) B.zero_l[zero_base + zo] = l;
+            for (int k = 0; k < surplus; ++k) B.donor_l[copy_base + co + k] = l;
+            if (B.m_trace) B.m_trace[(size_t)event * N + l] = m[q];
+        }
+        zero_base += tz;
+        copy_base += tc;
+    }
+    if (tid == 0) {
+        B.n_pairs[0] = zero_base < copy_base ? zero_base : copy_base;
+        B.delta[0] = Delta;
+        if (B.delta_trace) B.delta_trace[event] = Delta;
+    }
+}
+
+// Imprinting (Sec. 2.5): a^(l1) <- t a^(l2) + (1 - t) a^(l1); the residual mixes the same way
+// by linearity and chi2 of l1 is summed again.  One block per pair; no donor is imprinted.
+__global__ void __launch_bounds__(128) imprint_kernel(DevProblem P, DevState S, BranchScratch B,
+                                                      int precision, double t) {
+    __shared__ double Rs[kMaxTau];
+    const int q = blockIdx.x;
+    if (q >= B.n_pairs[0]) return;
+    const int l1 = B.zero_l[q], l2 = B.donor_l[q];
+    const double omt = 1.0 - t;
+    const int NO = P.n_omega, PAD = P.n_tau_pad;
+    if (precision == 0) {
+        double *a1 = S.a64 + (size_t)l1 * NO;
+        const double *a2 = S.a64 + (size_t)l2 * NO;
+        for (int j = threadIdx.x; j < NO; j += blockDim.x) a1[j] = t * a2[j] + omt * a1[j];
+        for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+            const double r = t * S.R64[(size_t)l2 * PAD + i] + omt * S.R64[(size_t)l1 * PAD + i];
+            S.R64[(size_t)l1 * PAD + i] = r;
+            Rs[i] = r;
+        }
+    } else {
+        float *b1 = S.b32 + (size_t)l1 * NO;
+        const float *b2 = S.b32 + (size_t)l2 * NO;
+        const float tf = (float)t, omtf = (float)omt;
+        for (int j = threadIdx.x; j < NO; j += blockDim.x) b1[j] = tf * b2[j] + omtf * b1[j];
+        for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+            const double r = t * (double)S.R32[(size_t)l2 * PAD + i] + omt * (double)S.R32[(size_t)l1 * PAD + i];
+            S.R32[(size_t)l1 * PAD + i] = (float)r;
+            Rs[i] = (double)(float)r;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c2 = 0.0;
+        for (int i = 0; i < P.n_tau; ++i) c2 = c2 + Rs[i] * Rs[i];
+        S.chi2[l1] = c2;
+    }
+}
+
+// ------------------------------------------------------------------ statistics
+__global__ void block_stats_kernel(DevProblem P, DevState S, BlockCounters *out) {
+    double cmin = DBL_MAX, csum = 0.0;
+    unsigned long long acc = 0, pos = 0;
+    for (int w = threadIdx.x; w < P.n_walkers; w += blockDim.x) {
+        const double c = S.chi2[w];
+        cmin = c < cmin ? c : cmin;
+        csum += c;
+        acc += S.n_acc[w];
+        pos += S.n_pos[w];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double c = __shfl_xor_sync(kFull, cmin, o);
+        cmin = c < cmin ? c : cmin;
+        csum += __shfl_xor_sync(kFull, csum, o);
+        acc += __shfl_xor_sync(kFull, acc, o);
+        pos += __shfl_xor_sync(kFull, pos, o);
+    }
+    __shared__ double smin[32], ssum[32];
+    __shared__ unsigned long long sacc[32], spos[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { smin[warp] = cmin; ssum[warp] = csum; sacc[warp] = acc; spos[warp] = pos; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+            cmin = smin[k] < cmin ? smin[k] : cmin;
+            csum += ssum[k];
+            acc += sacc[k];
+            pos += spos[k];
+        }
+        out->chi2_min = cmin;
+        out->chi2_sum = csum;
+        out->acc = acc;
+        out->pos = pos;
+    }
+}
+
+// ------------------------------------------------------------------ stochastic average
+// Walkers with chi2 <= factor * min chi2; mean over them (walkers ascending) and the standard
+// error sqrt(sum (a - mean)^2 / (n - 1)) / sqrt(n) per bin (Sec. 1).
+__global__ void average_select_kernel(DevProblem P, DevState S, double factor, int *n_used,
+                                      double *cut_out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double cmin = S.chi2[0];
+    for (int w = 1; w < P.n_walkers; ++w) if (S.chi2[w] < cmin) cmin = S.chi2[w];
+    const double cut = factor * cmin;
+    int used = 0;
+    for (int w = 0; w < P.n_walkers; ++w) used += (S.chi2[w] <= cut);
+    *n_used = used;
+    *cut_out = cut;
+}
+
+__global__ void average_bins_kernel(DevProblem P, DevState S, int precision, const int *n_used,
+                                    const double *cut_in, double *mean, double *err) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n_omega) return;
+    const double cut = *cut_in;
+    const int used = *n_used;
+    auto at = [&](int w) -> double {
+        if (precision == 0) return S.a64[(size_t)w * P.n_omega + j];
+        return (double)S.b32[(size_t)w * P.n_omega + j];
+    };
+    double m = 0.0;
+    for (int w = 0; w < P.n_walkers; ++w) if (S.chi2[w] <= cut) m += at(w);
+    m /= used;
+    double e = 0.0;
+    if (used > 1) {
+        for (int w = 0; w < P.n_walkers; ++w) {
+            if (!(S.chi2[w] <= cut)) continue;
+            const double v = at(w) - m;
+            e += v * v;
+        }
+        e = sqrt(e / (used - 1)) / sqrt((double)used);
+    }
+    mean[j] = m;
+    if (err) err[j] = e;
+}
+
+__global__ void __launch_bounds__(128) residual_of_kernel(DevProblem P, const double *a, double *R,
+                                                          double *chi2) {
+    __shared__ double Rs[kMaxTau];
+    for (int i = threadIdx.x; i < P.n_tau_pad; i += blockDim.x) {
+        double r = 0.0;
+        if (i < P.n_tau) {
+            double model = 0.0;
+            for (int j = 0; j < P.n_omega; ++j) model = model + P.Khat64[(size_t)j * P.n_tau_pad + i] * a[j];
+            r = P.Fhat64[i] - model;
+        }
+        Rs[i] = r;
+        if (R) R[i] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c2 = 0.0;
+        for (int i = 0; i < P.n_tau; ++i) c2 = c2 + Rs[i] * Rs[i];
+        *chi2 = c2;
+    }
+}
+
+__global__ void philox_kernel(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint4 c = make_uint4(ctr[4 * q], ctr[4 * q + 1], ctr[4 * q + 2], ctr[4 * q + 3]);
+    const uint4 r = philox4x32_10(c, philox_key(seed));
+    out[4 * q] = r.x;
+    out[4 * q + 1] = r.y;
+    out[4 * q + 2] = r.z;
+    out[4 * q + 3] = r.w;
+}
+
+template <int C>
+cudaError_t launch_sweep64_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    const int threads = 128;
+    const int blocks = (P.n_walkers * 32 + threads - 1) / threads;
+    sweep_fp64_kernel<C><<<blocks, threads, 0, st>>>(P, S, n0, n1);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_init_state(const DevProblem &P, const DevState &S, int precision, const double *a0,
+                              const double *R0, double chi2_0, cudaStream_t st) {
+    init_state_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision, a0, R0, chi2_0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    switch (P.n_tau_pad / 32) {
+        case 1: return launch_sweep64_c<1>(P, S, n0, n1, st);
+        case 2: return launch_sweep64_c<2>(P, S, n0, n1, st);
+        case 3: return launch_sweep64_c<3>(P, S, n0, n1, st);
+        case 4: return launch_sweep64_c<4>(P, S, n0, n1, st);
+        case 5: return launch_sweep64_c<5>(P, S, n0, n1, st);
+        case 6: return launch_sweep64_c<6>(P, S, n0, n1, st);
+        case 7: return launch_sweep64_c<7>(P, S, n0, n1, st);
+        case 8: return launch_sweep64_c<8>(P, S, n0, n1, st);
+        case 9: return launch_sweep64_c<9>(P, S, n0, n1, st);
+        case 10: return launch_sweep64_c<10>(P, S, n0, n1, st);
+        case 11: return launch_sweep64_c<11>(P, S, n0, n1, st);
+        case 12: return launch_sweep64_c<12>(P, S, n0, n1, st);
+        case 13: return launch_sweep64_c<13>(P, S, n0, n1, st);
+        case 14: return launch_sweep64_c<14>(P, S, n0, n1, st);
+        case 15: return launch_sweep64_c<15>(P, S, n0, n1, st);
+        case 16: return launch_sweep64_c<16>(P, S, n0, n1, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, cudaStream_t st) {
+    resync_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,
+                          int block_index, double fraction, double imprint_t, int event, cudaStream_t st,
+                          int *launches) {
+    branch_solve_kernel<<<1, kSolveThreads, 0, st>>>(P, S, B, block_index, fraction, event);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    imprint_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, B, precision, imprint_t);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_stats(const DevProblem &P, const DevState &S, BlockCounters *out, cudaStream_t st) {
+    block_stats_kernel<<<1, 1024, 0, st>>>(P, S, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_average(const DevProblem &P, const DevState &S, int precision, double factor, double *mean,
+                           double *err, int *n_used, double *cut, double *R_mean, double *chi2_mean,
+                           cudaStream_t st, int *launches) {
+    average_select_kernel<<<1, 32, 0, st>>>(P, S, factor, n_used, cut);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    average_bins_kernel<<<(P.n_omega + 127) / 128, 128, 0, st>>>(P, S, precision, n_used, cut, mean, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    residual_of_kernel<<<1, 128, 0, st>>>(P, mean, R_mean, chi2_mean);
+    *launches += 3;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    philox_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, ctr, seed, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sail

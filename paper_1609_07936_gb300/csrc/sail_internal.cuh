@@ -1,0 +1,92 @@
+// Internal declarations shared by the kernels and the host side of libsail.
+// Layouts in device memory (all arrays 256-byte aligned inside the caller's workspace):
+//   Khat64 / Khat32  [n_omega][n_tau_pad]  column j of K_ij / sigma_i, zero past n_tau
+//   Fhat64 / Fhat32  [n_tau_pad]           F_i / sigma_i, zero past n_tau
+//   x64              [n_omega]             bin centres
+//   beta32           [n_omega]             B - A x_j
+//   Tsweep           [n_sweeps]            absolute temperature of each sweep
+//   a64  (FP64)      [n_walkers][n_omega]  spectra
+//   b32  (FP32)      [n_walkers][n_omega]  spectra / common scale g
+//   g2   (FP32)      [n_walkers][2]        common scale as an unevaluated float pair (hi, lo)
+//   R64 / R32        [n_walkers][n_tau_pad] residuals, zero past n_tau
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sail {
+
+constexpr int kMaxChunks = 16;        // residual chunks of 32 per lane: n_tau <= 512
+constexpr int kMaxTau = 32 * kMaxChunks;
+constexpr int kProbeMax = 65536;      // proposals per sail_delta_probe call
+constexpr int kSolveThreads = 1024;   // branching solve: one block
+constexpr int kSolvePerThread = 16;   // walkers per solve thread: n_walkers <= 16384
+constexpr int kMaxWalkers = kSolveThreads * kSolvePerThread;
+constexpr unsigned long long kFnvOffset = 0xCBF29CE484222325ull;
+constexpr unsigned long long kFnvPrime = 0x100000001B3ull;
+
+struct DevProblem {
+    int n_tau, n_omega, n_walkers, n_tau_pad, n_sweeps;
+    double A, B, dw;
+    double move_scale, y_p, y_m, y_min;
+    uint64_t seed;
+    const double *Khat64;
+    const float *Khat32;
+    const double *Fhat64;
+    const float *Fhat32;
+    const double *x64;
+    const float *beta32;
+    const double *Tsweep;
+};
+
+struct DevState {
+    double *a64;
+    float *b32;
+    float *g2;
+    double *R64;
+    float *R32;
+    double *chi2;
+    int *acc_prev;
+    unsigned long long *hash;
+    unsigned long long *n_acc;
+    unsigned long long *n_pos;
+    int *acc_trace;        // [n_sweeps][n_walkers] or null
+};
+
+struct BranchScratch {
+    int *m;                // [n_walkers] multipliers
+    int *zero_l;           // [n_walkers] imprinted walkers, ascending
+    int *donor_l;          // [n_walkers] donor of each imprinted walker
+    int *n_pairs;          // [1]
+    double *delta;         // [1] Delta of the solve
+    int *m_trace;          // [max_events][n_walkers] or null
+    double *delta_trace;   // [max_events] or null
+};
+
+struct BlockCounters {     // device-side block statistics, read back once per block
+    double chi2_min, chi2_sum;
+    unsigned long long acc, pos;
+};
+
+// ---- launchers (return cudaGetLastError() of the launch) ----
+cudaError_t launch_init_state(const DevProblem &P, const DevState &S, int precision,
+                              const double *a0, const double *R0, double chi2_0, cudaStream_t st);
+cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int sweep_begin,
+                              int sweep_end, cudaStream_t st);
+cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_begin,
+                              int sweep_end, cudaStream_t st);
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, cudaStream_t st);
+cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
+                          int precision, int block_index, double fraction, double imprint_t,
+                          int event, cudaStream_t st, int *launches);
+cudaError_t launch_block_stats(const DevProblem &P, const DevState &S, BlockCounters *out,
+                               cudaStream_t st);
+cudaError_t launch_average(const DevProblem &P, const DevState &S, int precision, double factor,
+                           double *mean, double *err, int *n_used, double *cut, double *R_mean,
+                           double *chi2_mean, cudaStream_t st, int *launches);
+cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, int n,
+                         const int *walker, const int *p, const int *s, const double *eps,
+                         double *delta, int *ok, cudaStream_t st);
+cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st);
+cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
+
+}  // namespace sail

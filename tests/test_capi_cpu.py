@@ -1,0 +1,88 @@
+"""The C ABI without a GPU: the library loads, exports every declared entry point,
+fills the paper's defaults and refuses bad arguments in its host-side checks."""
+import ctypes
+import json
+import math
+import os
+import re
+
+import pytest
+
+import paper_1609_07936_gb300 as sail
+from paper_1609_07936_gb300 import _capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sail.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sail_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported():
+    L = sail.load()
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(names) == sorted(_capi.EXPORTS)
+
+
+def test_defaults_are_the_papers():
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_parameters.json")))
+    p = sail.Params.library_defaults()
+    for k in ("T_start", "sweeps_per_block", "branch_fraction", "imprint_t", "y_p", "y_m"):
+        assert getattr(p, k) == gold[k]["value"], k
+    assert math.isnan(p.A) and math.isnan(p.B)
+
+
+def test_struct_sizes_match_the_header():
+    # sail_params: 6 ints, 12 doubles, one uint64, 8 ints -> 160 bytes with alignment
+    assert ctypes.sizeof(_capi.CParams) == 6 * 4 + 12 * 8 + 8 + 8 * 4
+    assert ctypes.sizeof(_capi.CBlockStats) == 8 + 6 * 8 + 8
+
+
+def test_workspace_size_and_refusals():
+    p = sail.Params(n_walkers=4096, n_sweeps=20000)
+    n = sail.workspace_size(200, 1000, p)
+    # at least the FP32 spectra, residuals and both kernel tables
+    assert n >= 4096 * 1000 * 4 + 4096 * 224 * 4 + 1000 * 224 * 12
+    assert sail.workspace_size(200, 1000, sail.Params(n_walkers=4096, precision=sail.PREC_FP64)) > n
+    with pytest.raises(sail.SailError) as e:
+        sail.workspace_size(0, 1000, p)
+    assert e.value.code == _capi.SAIL_EINVAL
+    with pytest.raises(sail.SailError):
+        sail.workspace_size(600, 1000, p)           # more than 512 tau points
+    with pytest.raises(sail.SailError):
+        sail.workspace_size(200, 1, p)              # one bin
+    with pytest.raises(sail.SailError):
+        sail.workspace_size(200, 1000, sail.Params(n_walkers=0))
+    with pytest.raises(sail.SailError):
+        sail.workspace_size(200, 1000, sail.Params(branch_fraction=1.0))
+    with pytest.raises(sail.SailError):
+        sail.workspace_size(200, 1000, sail.Params(T_start=-1.0))
+
+
+def test_create_refuses_bad_inputs_before_touching_the_device():
+    L = sail.load()
+    import numpy as np
+    tau = np.linspace(0, 1, 4)
+    F = np.ones(4)
+    sig = np.ones(4)
+    om = (np.arange(8) + 0.5) * 0.5
+    p = sail.Params(n_walkers=2, B=1.0, A=1.0).c()
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptr = lambda a: a.ctypes.data_as(dp)
+    # NULL workspace
+    rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p), None, 0, None)
+    assert rc == _capi.SAIL_EINVAL
+    # unaligned workspace pointer, refused before any copy
+    rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
+                       ctypes.c_void_p(16), 1 << 30, None)
+    assert rc == _capi.SAIL_EINVAL and b"aligned" in L.sail_last_error()
+    # too small
+    rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
+                       ctypes.c_void_p(256), 16, None)
+    assert rc == _capi.SAIL_ENOMEM
