@@ -38,11 +38,11 @@ METRIC = "walker-moves/sec"
 MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 
 
-def params_for(seed: int, timing: bool = True):
+def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
-                      sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
+                      sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing)
     return P, prm
 
@@ -154,13 +154,13 @@ def run_gpu(args, rank, world, local_rank):
     l2_gbs = measure_read_bandwidth(torch, sail, 32 << 20, 400)
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
-    P, prm = params_for(seed=1000 + rank)
+    P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
     del warm
 
-    P, prm = params_for(seed=rank)
+    P, prm = params_for(seed=rank, resync_every=args.resync_every)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -294,6 +294,8 @@ def main():
     ap.add_argument("--cpu-sample-walkers", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,
+                    help="sweeps per sweep-kernel launch; smaller values give short launches for profiling")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", args.gpus if args.gpus == 1 else 1))
