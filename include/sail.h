@@ -188,6 +188,30 @@ int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, vo
  * HBM (a buffer far larger). */
 int sail_probe_read_bandwidth(const void *d_buf, size_t bytes, int reps, void *d_sink, void *stream);
 
+/*
+ * Residue chi2 = sum_i ((F_i - sum_j K_ij a_j) / sigma_i)^2 of n_spectra histogram spectra,
+ * for callers that cannot allocate device memory.  The paper has no counterpart: this is a
+ * variant of the residual recomputation that sail_anneal and sail_set_state run inside a
+ * handle's workspace.  Every other entry point needs that caller-allocated workspace; a
+ * plug-in inside a program whose allocator owns the whole device memory, or a service loop
+ * that must not pay for cudaMalloc / cudaFree, cannot provide one.  This one allocates
+ * nothing: its only scratch (the weighted kernel table and data) lives in a fixed array of
+ * 8 MiB + 4 KiB that every GPU loading the library holds until the process exits.
+ *   d_tau, d_F, d_sigma [n_tau], d_omega [n_omega] (bin centres from 0, as in sail_create),
+ *   d_a [n_spectra * n_omega]: device inputs.  d_chi2 [n_spectra] and, if not NULL,
+ *   d_R [n_spectra * n_tau] (residuals F/sigma - K a/sigma): device outputs.
+ * Limits: 1 <= n_tau <= 512 and n_omega * (n_tau rounded up to 32) <= 1,048,576; larger
+ * sizes return SAIL_EINVAL with a message.  The grid is not checked.  Kernels run on
+ * stream; the call returns without synchronising.
+ * The first call on each device looks up the scratch array's device address with that
+ * device current, so make that first call before any stream capture.  All calls share the
+ * one array, which keeps the last call's contents: calls whose kernels overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ */
+int sail_residue_noalloc(const double *d_tau, const double *d_F, const double *d_sigma, int n_tau,
+                         const double *d_omega, int n_omega, const double *d_a, int n_spectra,
+                         double *d_chi2, double *d_R, void *stream);
+
 /* Frees the host side of the handle; the workspace stays the caller's. */
 int sail_destroy(sail_t h);
 

@@ -31,7 +31,7 @@ PREC_FP32 = 1
 EXPORTS = [
     "sail_default_params", "sail_workspace_size", "sail_create", "sail_anneal", "sail_average",
     "sail_get_info", "sail_get_state", "sail_set_state", "sail_get_trace", "sail_delta_probe",
-    "sail_philox", "sail_probe_read_bandwidth", "sail_destroy", "sail_last_error",
+    "sail_philox", "sail_probe_read_bandwidth", "sail_residue_noalloc", "sail_destroy", "sail_last_error",
 ]
 
 
@@ -105,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.sail_delta_probe.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, _ip]
     L.sail_philox.argtypes = [ctypes.c_int, vp, ctypes.c_uint64, vp, vp]
     L.sail_probe_read_bandwidth.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, vp, vp]
+    L.sail_residue_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
     L.sail_destroy.argtypes = [vp]
     L.sail_last_error.argtypes = []
     L.sail_last_error.restype = ctypes.c_char_p

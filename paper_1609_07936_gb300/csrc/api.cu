@@ -29,6 +29,20 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+}  // namespace
+
+int sail::set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char *what) {
     return fail(SAIL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }

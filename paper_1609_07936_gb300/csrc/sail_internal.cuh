@@ -89,4 +89,7 @@ cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, 
 cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 
+// Records the message sail_last_error() returns on this thread; returns code.
+int set_error(int code, const char *fmt, ...);
+
 }  // namespace sail
