@@ -22,6 +22,7 @@ UNITS = {
     "api.cu": [],
     "exact64.cu": ["-fmad=false"],
     "sweep_fp32.cu": [],
+    "resync_fp32.cu": [],
     "noalloc.cu": ["-fmad=false"],
 }
 

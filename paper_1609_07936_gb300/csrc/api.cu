@@ -58,7 +58,7 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, Tsweep, a0, R0;
+    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Tsweep, a0, R0;
     size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos;
     size_t acc_trace, m_trace, delta_trace;
     size_t m, zero_l, donor_l, n_pairs, delta, counters;
@@ -80,6 +80,9 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
     L.Fhat32 = take(PAD * 4);
     L.x64 = take(NO * 8);
     L.beta32 = take(NO * 4);
+    L.rgap32 = take(NO * 4);
+    L.Qhi32 = take((NO + 31) / 32 * PAD * 4);
+    L.Qlo32 = take(32 * PAD * 4);
     L.Tsweep = take((size_t)p.n_sweeps * 8);
     L.a0 = take(NO * 8);
     L.R0 = take(PAD * 8);
@@ -287,6 +290,17 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
 
     const int PAD = (n_tau + 31) / 32 * 32;
     const size_t NO = (size_t)n_omega;
+    if (p->precision == SAIL_PREC_FP32) {
+        DevProblem probe{};
+        probe.n_omega = n_omega;
+        probe.n_tau_pad = PAD;
+        int dev = 0, smem_max = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
+            sweep_fp32_table_bytes(probe) > (size_t)smem_max)
+            return fail(SAIL_EINVAL, "FP32 sweep tables need %zu bytes of shared memory, the device has %d",
+                        sweep_fp32_table_bytes(probe), smem_max);
+    }
     // ---- weighted bin-integrated kernel, Eq. (correlation-model): column-major [j][i]
     std::vector<double> K64(NO * PAD, 0.0), F64(PAD, 0.0);
     std::vector<float> K32(NO * PAD, 0.0f), F32(PAD, 0.0f), beta(NO);
@@ -302,6 +316,14 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         F32[i] = (float)F64[i];
     }
     for (int j = 0; j < n_omega; ++j) beta[j] = (float)(B - A * omega[j]);
+    // FP32 sweep tables: Khat_{i,32h+l} = Khat_{i,32h} q_i^l (Eq. efficient-correlation-model)
+    const int NH = (n_omega + 31) / 32;
+    std::vector<float> Qhi((size_t)NH * PAD, 0.0f), Qlo((size_t)32 * PAD, 0.0f), rgap(NO, 0.0f);
+    for (int h = 0; h < NH; ++h)
+        for (int i = 0; i < n_tau; ++i) Qhi[(size_t)h * PAD + i] = (float)K64[(size_t)(32 * h) * PAD + i];
+    for (int l = 0; l < 32; ++l)
+        for (int i = 0; i < n_tau; ++i) Qlo[(size_t)l * PAD + i] = (float)std::exp(-(double)l * dw * tau[i]);
+    for (int k = 1; k < n_omega; ++k) rgap[k] = (float)(1.0 / ((double)k * dw));
 
     // ---- start spectrum: largest entropy with sum a = A and sum a x = B, a_j ~ exp(-lambda x_j)
     const double target = B / A, xc = 0.5 * (x0 + xN), span = xN - x0;
@@ -375,6 +397,9 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.Fhat32 = (const float *)(ws + L.Fhat32);
     P.x64 = (const double *)(ws + L.x64);
     P.beta32 = (const float *)(ws + L.beta32);
+    P.rgap32 = (const float *)(ws + L.rgap32);
+    P.Qhi32 = (const float *)(ws + L.Qhi32);
+    P.Qlo32 = (const float *)(ws + L.Qlo32);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;
     S.a64 = p->precision == SAIL_PREC_FP64 ? (double *)(ws + L.a64) : nullptr;
@@ -409,6 +434,9 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     if (e == cudaSuccess) e = up(L.Fhat32, F32.data(), F32.size() * 4);
     if (e == cudaSuccess) e = up(L.x64, x.data(), NO * 8);
     if (e == cudaSuccess) e = up(L.beta32, beta.data(), NO * 4);
+    if (e == cudaSuccess) e = up(L.rgap32, rgap.data(), NO * 4);
+    if (e == cudaSuccess) e = up(L.Qhi32, Qhi.data(), Qhi.size() * 4);
+    if (e == cudaSuccess) e = up(L.Qlo32, Qlo.data(), Qlo.size() * 4);
     if (e == cudaSuccess) e = up(L.Tsweep, T.data(), T.size() * 8);
     if (e == cudaSuccess) e = up(L.a0, a0.data(), NO * 8);
     if (e == cudaSuccess) e = up(L.R0, R0.data(), PAD * 8);
@@ -511,10 +539,11 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
             timed_end(h, tk, kSweep);
             if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
             tk = timed_begin(h);
-            e = launch_resync(h->P, h->S, p.precision, st);
+            int l = 0;
+            e = launch_resync(h->P, h->S, p.precision, 1, st, &l);
             timed_end(h, tk, kResync);
             if (e != cudaSuccess) return cuda_fail(e, "resync launch");
-            h->launches += 2;
+            h->launches += 1 + l;
             h->moves += (long long)(next - n) * p.n_walkers * h->n_omega;
             n = next;
         }
@@ -625,8 +654,9 @@ int sail_set_state(sail_t h, const double *a, const int *acc_prev) {
         SAIL_CUDA(cudaMemcpyAsync(ws + h->L.g2, g.data(), W * 2 * 4, cudaMemcpyHostToDevice, st), "H2D");
     }
     if (acc_prev) SAIL_CUDA(cudaMemcpyAsync(ws + h->L.acc_prev, acc_prev, W * 4, cudaMemcpyHostToDevice, st), "H2D");
-    SAIL_CUDA(launch_resync(h->P, h->S, h->prm.precision, st), "resync launch");
-    h->launches += 1;
+    int l = 0;
+    SAIL_CUDA(launch_resync(h->P, h->S, h->prm.precision, 0, st, &l), "resync launch");
+    h->launches += l;
     SAIL_CUDA(cudaStreamSynchronize(st), "set_state sync");
     return SAIL_OK;
 }

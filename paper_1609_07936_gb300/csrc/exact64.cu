@@ -195,12 +195,15 @@ __device__ void restore_sum_rules(const DevProblem &P, float *b, double *red) {
     __syncthreads();
 }
 
+__global__ void __launch_bounds__(128) restore_kernel(DevProblem P, DevState S) {
+    __shared__ double red[64];
+    restore_sum_rules(P, S.b32 + (size_t)blockIdx.x * P.n_omega, red);
+}
+
 __global__ void __launch_bounds__(128) resync_kernel(DevProblem P, DevState S, int precision) {
     __shared__ double Rs[kMaxTau];
-    __shared__ double red[64];
     const int w = blockIdx.x;
     const int NO = P.n_omega, PAD = P.n_tau_pad;
-    if (precision != 0) restore_sum_rules(P, S.b32 + (size_t)w * NO, red);
     for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
         double r = 0.0;
         if (i < P.n_tau) {
@@ -664,9 +667,21 @@ cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int n0, in
     }
 }
 
-cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, cudaStream_t st) {
-    resync_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision);
-    return cudaGetLastError();
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, cudaStream_t st,
+                          int *launches) {
+    if (precision == 0) {
+        resync_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision);
+        *launches += 1;
+        return cudaGetLastError();
+    }
+    if (restore) {
+        restore_kernel<<<P.n_walkers, 128, 0, st>>>(P, S);
+        *launches += 1;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    *launches += 1;
+    return launch_resync_fp32(P, S, st);
 }
 
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,

@@ -4,6 +4,9 @@
 //   Fhat64 / Fhat32  [n_tau_pad]           F_i / sigma_i, zero past n_tau
 //   x64              [n_omega]             bin centres
 //   beta32           [n_omega]             B - A x_j
+//   rgap32           [n_omega]             1 / (k dw), k = 0..n_omega-1 (k = 0 unused)
+//   Qhi32            [ceil(n_omega/32)][n_tau_pad]  Khat_{i,32h}
+//   Qlo32            [32][n_tau_pad]        q_i^l = e^{-l dw tau_i}; Khat_{i,32h+l} = Qhi[h][i] Qlo[l][i]
 //   Tsweep           [n_sweeps]            absolute temperature of each sweep
 //   a64  (FP64)      [n_walkers][n_omega]  spectra
 //   b32  (FP32)      [n_walkers][n_omega]  spectra / common scale g
@@ -35,6 +38,9 @@ struct DevProblem {
     const float *Fhat32;
     const double *x64;
     const float *beta32;
+    const float *rgap32;
+    const float *Qhi32;
+    const float *Qlo32;
     const double *Tsweep;
 };
 
@@ -74,7 +80,11 @@ cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int sweep_
                               int sweep_end, cudaStream_t st);
 cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_begin,
                               int sweep_end, cudaStream_t st);
-cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, cudaStream_t st);
+// FP64 state: sequential FP64 recomputation.  FP32 state: optional sum-rule restoration
+// (restore != 0), then the tiled GEMM of resync_fp32.cu.
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, cudaStream_t st,
+                          int *launches);
+cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStream_t st);
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);
@@ -87,6 +97,8 @@ cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, 
                          const int *walker, const int *p, const int *s, const double *eps,
                          double *delta, int *ok, cudaStream_t st);
 cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st);
+// Shared memory the FP32 sweep needs for its kernel tables (must fit one block).
+size_t sweep_fp32_table_bytes(const DevProblem &P);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 
 // Records the message sail_last_error() returns on this thread; returns code.

@@ -1,14 +1,23 @@
 // FP32 production sweep (Sec. 2.2 moves, Eq. probability-density acceptance) and the
 // proposal probe.
 //
-// One warp per walker; lane l holds R_i and M_i = Fhat_i - R_i for i = l + 32 c in
-// registers.  A walker's spectrum is stored as a = g b: an accepted move multiplies the
-// common scale g by r (kept as an unevaluated pair of floats, so its error stays ~1e-14
-// over a whole resync interval) and writes only b_p and b_s, so a move touches two bins
-// of the spectrum and two columns of the kernel table, as Sec. 2.2 notes.  Random words
-// for 32 consecutive moves are drawn at once, one Philox call per lane, and broadcast by
-// shuffle.  Delta chi2 = sum_i d_i (2 R_i + d_i) is reduced by an xor butterfly.  The
-// scale is folded back into b when the kernel ends, so residual recomputation sees a = b.
+// Kernel columns from two small tables.  Eq. (efficient-correlation-model) writes the bin
+// kernel as c_i q_i^j with q_i = e^{-dw tau_i}; so with j = 32 h + l,
+//     Khat_ij = Khat_{i,32h} * q_i^l = Qhi[h][i] * Qlo[l][i],
+// and the two tables ((N_omega/32 + 32) rows of n_tau_pad floats, 57 KB at 200 x 1000) sit in
+// shared memory.  A move reads its two columns from there: no L2 traffic, no L2 latency.
+//
+// Walker layout.  One persistent block per SM; 16 lanes per walker (two walkers per warp),
+// lane l of a half-warp holding R_i and M_i = Fhat_i - R_i for i = 32 c + 2 l, 32 c + 2 l + 1.
+// The move's scalar work (random words, bins, amplitudes, positivity, Metropolis) is shared by
+// the two walkers of a warp.  Random words for 16 consecutive moves are drawn at once, one
+// Philox call per lane, and broadcast by shuffle within the half-warp.  Delta chi2 =
+// sum_i d_i (2 R_i + d_i) is reduced by an xor butterfly over the half-warp.
+//
+// Spectrum.  a = g b: an accepted move multiplies the common scale g by r (an unevaluated
+// pair of floats, error ~1e-14 over a launch) and writes only b_p and b_s.  When the block's
+// spectra fit in shared memory next to the tables they are staged there for the launch.  The
+// scale is folded back into b when the launch ends, so residual recomputation sees a = b.
 #include <cmath>
 #include <cstdint>
 
@@ -21,10 +30,11 @@ namespace sail {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kThreads = 512;          // at most 16 warps (32 walkers) per round
 
-__device__ __forceinline__ float warp_sum(float v) {
+__device__ __forceinline__ float half_sum(float v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
@@ -38,123 +48,205 @@ __device__ __forceinline__ void pair_scale(float &hi, float &lo, float r) {
     hi = s;
 }
 
-template <int C>
-__global__ void __launch_bounds__(128) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1) {
-    const int lane = threadIdx.x & 31;
-    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (w >= P.n_walkers) return;
-    const int NO = P.n_omega, PAD = P.n_tau_pad;
-    const float *__restrict__ K = P.Khat32;
-    const float *__restrict__ beta = P.beta32;
-    float *b = S.b32 + (size_t)w * NO;
+// The FP32 move amplitudes of Eqs. (update-delta-p/s): rgap[k] = 1 / (k dw).
+__device__ __forceinline__ void deltas(float eps, int p, int s, const float *beta, const float *rgap,
+                                       float &dp, float &ds) {
+    const int k = p - s;
+    const float inv_gap = k > 0 ? rgap[k] : -rgap[-k];   // 1 / (x_p - x_s)
+    dp = (eps * beta[s]) * inv_gap;
+    ds = -(eps * beta[p]) * inv_gap;
+}
 
-    float R[C], M[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) {
-        R[c] = S.R32[(size_t)w * PAD + lane + 32 * c];
-        M[c] = P.Fhat32[lane + 32 * c] - R[c];
+struct SweepGeom {
+    int pairs_total;      // ceil(n_walkers / 2)
+    int pairs_per_cta;
+    int warps;            // warps per block
+    int rounds;           // pairs handled one after another by each warp
+    int stage_b;          // spectra staged in shared memory
+};
+
+template <int C2>
+__global__ void __launch_bounds__(kThreads) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
+                                                              SweepGeom G) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    float *sQhi = sm;
+    float *sQlo = sQhi + (size_t)NH * PAD;
+    float *sBeta = sQlo + (size_t)32 * PAD;
+    float *sRgap = sBeta + NO;
+    float *sB = sRgap + NO;      // staged spectra [2 * pairs_per_cta][NO] when G.stage_b
+    {
+        const float4 *g4 = reinterpret_cast<const float4 *>(P.Qhi32);
+        float4 *s4 = reinterpret_cast<float4 *>(sQhi);
+        for (int q = threadIdx.x; q < NH * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+        g4 = reinterpret_cast<const float4 *>(P.Qlo32);
+        s4 = reinterpret_cast<float4 *>(sQlo);
+        for (int q = threadIdx.x; q < 32 * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+        for (int q = threadIdx.x; q < NO; q += blockDim.x) {
+            sBeta[q] = P.beta32[q];
+            sRgap[q] = P.rgap32[q];
+        }
     }
-    float ghi = S.g2[2 * w], glo = S.g2[2 * w + 1];
-    double chi2 = S.chi2[w];
-    int accp = S.acc_prev[w];
-    unsigned long long h = S.hash[w], nacc = 0, npos = 0;
+    const int pair_lo = blockIdx.x * G.pairs_per_cta;
+    const int pair_hi = min(pair_lo + G.pairs_per_cta, G.pairs_total);
+    const int walker_lo = 2 * pair_lo;
+    const int walker_hi = min(2 * pair_hi, P.n_walkers);
+    if (G.stage_b) {
+        const size_t n = (size_t)(walker_hi - walker_lo) * NO;
+        const float *src = S.b32 + (size_t)walker_lo * NO;
+        for (size_t q = threadIdx.x; q < n; q += blockDim.x) sB[q] = src[q];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4, warp = threadIdx.x >> 5;
     const uint2 key = philox_key(P.seed);
     const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
-    const float dwf = (float)P.dw;
 
-    for (int n = n0; n < n1; ++n) {
-        const float invT = (float)(1.0 / P.Tsweep[n]);
-        const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
-        int acc = 0, pos = 0;
-        float dchi = 0.0f;
-        uint4 batch = make_uint4(0u, 0u, 0u, 0u);
-        for (int mv = 0; mv < NO; ++mv) {
-            const int src = mv & 31;
-            if (src == 0) batch = philox4x32_10(make_uint4((uint32_t)(mv + lane), (uint32_t)n, (uint32_t)w, 0u), key);
-            const uint32_t w0 = __shfl_sync(kFull, batch.x, src);
-            const uint32_t w1 = __shfl_sync(kFull, batch.y, src);
-            const uint32_t w2 = __shfl_sync(kFull, batch.z, src);
-            const uint32_t w3 = __shfl_sync(kFull, batch.w, src);
-            int p, s;
-            move_bins(w0, w1, NO, p, s);
-            const float eps = yd * (2.0f * unit32(w2) - 1.0f);
-            const float u = unit32(w3);
-            const float r = 1.0f - eps;
-            const float gap = (float)(p - s) * dwf;      // x_p - x_s
-            const float dp = eps * beta[s] / gap;
-            const float ds = -eps * beta[p] / gap;
-            const float ap = fmaf(r, ghi * b[p], dp);
-            const float as = fmaf(r, ghi * b[s], ds);
-            unsigned code;
-            if (ap < 0.0f || as < 0.0f) {
-                code = 2;
-                ++pos;
-            } else {
-                const float *Kp = K + (size_t)p * PAD + lane;
-                const float *Ks = K + (size_t)s * PAD + lane;
-                float d[C];
-                float part = 0.0f;
+    for (int round = 0; round < G.rounds; ++round) {
+        const int pair = pair_lo + round * G.warps + warp;
+        if (pair >= pair_hi) break;                       // uniform across the warp
+        const int w = 2 * pair + half;
+        const bool active = w < P.n_walkers;
+        const int wr = active ? w : 2 * pair;             // a valid walker to read from
+        float *b = G.stage_b ? sB + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+
+        float R[2 * C2], M[2 * C2];
 #pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    d[c] = fmaf(-ds, __ldg(Ks + 32 * c), fmaf(-dp, __ldg(Kp + 32 * c), eps * M[c]));
-                    part = fmaf(d[c], fmaf(2.0f, R[c], d[c]), part);
-                }
-                const float D = warp_sum(part);
-                if (D <= 0.0f || u < __expf(-D * invT)) {
-#pragma unroll
-                    for (int c = 0; c < C; ++c) {
-                        R[c] += d[c];
-                        M[c] -= d[c];
-                    }
-                    pair_scale(ghi, glo, r);
-                    if (lane == 0) {
-                        b[p] = ap / ghi;
-                        b[s] = as / ghi;
-                    }
-                    __syncwarp();
-                    dchi += D;
-                    ++acc;
-                    code = 1;
-                } else {
-                    code = 0;
-                }
-            }
-            h = (h ^ code) * kFnvPrime;
+        for (int c = 0; c < C2; ++c) {
+            const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + 32 * c + 2 * hl);
+            const float2 f2 = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
+            R[2 * c] = r2.x;
+            R[2 * c + 1] = r2.y;
+            M[2 * c] = f2.x - r2.x;
+            M[2 * c + 1] = f2.y - r2.y;
         }
-        chi2 += (double)dchi;
-        accp = acc;
-        nacc += acc;
-        npos += pos;
-        if (S.acc_trace && lane == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
-    }
-    // fold the common scale into the stored spectrum
-    for (int j = lane; j < NO; j += 32) {
-        const float v = b[j];
-        b[j] = fmaf(glo, v, ghi * v);
-    }
+        float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
+        double chi2 = S.chi2[wr];
+        int accp = S.acc_prev[wr];
+        unsigned long long nacc = 0, npos = 0;
+
+        for (int n = n0; n < n1; ++n) {
+            const float invT = (float)(1.0 / P.Tsweep[n]);
+            const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
+            int acc = 0, pos = 0;
+            float dchi = 0.0f;
+            uint4 batch = make_uint4(0u, 0u, 0u, 0u);
+            for (int mv = 0; mv < NO; ++mv) {
+                const int src = mv & 15;
+                if (src == 0)
+                    batch = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
+                const uint32_t w0 = __shfl_sync(kFull, batch.x, src, 16);
+                const uint32_t w1 = __shfl_sync(kFull, batch.y, src, 16);
+                const uint32_t w2 = __shfl_sync(kFull, batch.z, src, 16);
+                const uint32_t w3 = __shfl_sync(kFull, batch.w, src, 16);
+                int p, s;
+                move_bins(w0, w1, NO, p, s);
+                const float eps = yd * (2.0f * unit32(w2) - 1.0f);
+                const float u = unit32(w3);
+                const float r = 1.0f - eps;
+                float dp, ds;
+                deltas(eps, p, s, sBeta, sRgap, dp, ds);
+                const float ap = fmaf(r, ghi * b[p], dp);
+                const float as = fmaf(r, ghi * b[s], ds);
+                const bool ok = active && ap >= 0.0f && as >= 0.0f;
+                pos += (active && !ok);
+                if (__any_sync(kFull, ok)) {
+                    const float *qhp = sQhi + (p >> 5) * PAD + 2 * hl;
+                    const float *qlp = sQlo + (p & 31) * PAD + 2 * hl;
+                    const float *qhs = sQhi + (s >> 5) * PAD + 2 * hl;
+                    const float *qls = sQlo + (s & 31) * PAD + 2 * hl;
+                    float d[2 * C2];
+                    float part = 0.0f;
 #pragma unroll
-    for (int c = 0; c < C; ++c) S.R32[(size_t)w * PAD + lane + 32 * c] = R[c];
-    if (lane == 0) {
-        S.g2[2 * w] = 1.0f;
-        S.g2[2 * w + 1] = 0.0f;
-        S.chi2[w] = chi2;
-        S.acc_prev[w] = accp;
-        S.hash[w] = h;
-        S.n_acc[w] += nacc;
-        S.n_pos[w] += npos;
+                    for (int c = 0; c < C2; ++c) {
+                        const float2 a1 = *reinterpret_cast<const float2 *>(qhp + 32 * c);
+                        const float2 a2 = *reinterpret_cast<const float2 *>(qlp + 32 * c);
+                        const float2 b1 = *reinterpret_cast<const float2 *>(qhs + 32 * c);
+                        const float2 b2 = *reinterpret_cast<const float2 *>(qls + 32 * c);
+                        d[2 * c] = fmaf(-ds, b1.x * b2.x, fmaf(-dp, a1.x * a2.x, eps * M[2 * c]));
+                        d[2 * c + 1] = fmaf(-ds, b1.y * b2.y, fmaf(-dp, a1.y * a2.y, eps * M[2 * c + 1]));
+                        part = fmaf(d[2 * c], fmaf(2.0f, R[2 * c], d[2 * c]), part);
+                        part = fmaf(d[2 * c + 1], fmaf(2.0f, R[2 * c + 1], d[2 * c + 1]), part);
+                    }
+                    const float D = half_sum(part);
+                    if (ok && (D <= 0.0f || u < __expf(-D * invT))) {
+#pragma unroll
+                        for (int c = 0; c < 2 * C2; ++c) {
+                            R[c] += d[c];
+                            M[c] -= d[c];
+                        }
+                        pair_scale(ghi, glo, r);
+                        if (hl == 0) {
+                            const float inv_g = 1.0f / ghi;
+                            b[p] = ap * inv_g;
+                            b[s] = as * inv_g;
+                        }
+                        dchi += D;
+                        ++acc;
+                    }
+                }
+                __syncwarp();
+            }
+            chi2 += (double)dchi;
+            accp = acc;
+            nacc += acc;
+            npos += pos;
+            if (active && S.acc_trace && hl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+        }
+        if (!active) continue;
+        // fold the common scale into the spectrum and write the walker back
+        float *bg = S.b32 + (size_t)w * NO;
+        for (int j = hl; j < NO; j += 16) {
+            const float v = b[j];
+            bg[j] = fmaf(glo, v, ghi * v);
+        }
+#pragma unroll
+        for (int c = 0; c < C2; ++c)
+            *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = make_float2(R[2 * c], R[2 * c + 1]);
+        if (hl == 0) {
+            S.g2[2 * w] = 1.0f;
+            S.g2[2 * w + 1] = 0.0f;
+            S.chi2[w] = chi2;
+            S.acc_prev[w] = accp;
+            S.n_acc[w] += nacc;
+            S.n_pos[w] += npos;
+        }
     }
 }
 
-template <int C>
+size_t table_bytes(const DevProblem &P) {
+    const size_t NH = (size_t)(P.n_omega + 31) / 32;
+    return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
+}
+
+template <int C2>
 cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
-    const int threads = 128;
-    const int blocks = (P.n_walkers * 32 + threads - 1) / threads;
-    sweep_fp32_kernel<C><<<blocks, threads, 0, st>>>(P, S, n0, n1);
+    int dev = 0, sms = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    SweepGeom G;
+    G.pairs_total = (P.n_walkers + 1) / 2;
+    const int ctas = G.pairs_total < sms ? G.pairs_total : sms;
+    G.pairs_per_cta = (G.pairs_total + ctas - 1) / ctas;
+    const int max_warps = kThreads / 32;
+    G.rounds = (G.pairs_per_cta + max_warps - 1) / max_warps;
+    G.warps = (G.pairs_per_cta + G.rounds - 1) / G.rounds;
+    const size_t tb = table_bytes(P);
+    const size_t staged = (size_t)2 * G.pairs_per_cta * P.n_omega * 4;
+    if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
+    G.stage_b = tb + staged <= (size_t)smem_max;
+    const size_t smem = tb + (G.stage_b ? staged : 0);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int n_ctas = (G.pairs_total + G.pairs_per_cta - 1) / G.pairs_per_cta;
+    sweep_fp32_kernel<C2><<<n_ctas, G.warps * 32, smem, st>>>(P, S, n0, n1, G);
     return cudaGetLastError();
 }
 
-// The proposal probe: one warp per proposal, the handle's own move arithmetic on the
-// stored state, no state change.
+// The proposal probe: one warp per proposal, the FP32 arithmetic of the sweep (or FP64 for a
+// validation handle) on the stored state, no state change.
 __global__ void probe_kernel(DevProblem P, DevState S, int precision, int n, const int *walker,
                              const int *pp, const int *ss, const double *epsv, double *delta, int *ok) {
     const int lane = threadIdx.x & 31;
@@ -186,9 +278,8 @@ __global__ void probe_kernel(DevProblem P, DevState S, int precision, int n, con
     const float eps = (float)epsv[q], r = 1.0f - eps;
     const float ghi = S.g2[2 * w];
     const float *b = S.b32 + (size_t)w * NO;
-    const float gap = (float)(p - s) * (float)P.dw;
-    const float dp = eps * P.beta32[s] / gap;
-    const float ds = -eps * P.beta32[p] / gap;
+    float dp, ds;
+    deltas(eps, p, s, P.beta32, P.rgap32, dp, ds);
     const float ap = fmaf(r, ghi * b[p], dp), as = fmaf(r, ghi * b[s], ds);
     if (ap < 0.0f || as < 0.0f) {
         if (lane == 0) { ok[q] = 0; delta[q] = 0.0; }
@@ -198,10 +289,12 @@ __global__ void probe_kernel(DevProblem P, DevState S, int precision, int n, con
     for (int i = lane; i < PAD; i += 32) {
         const float R = S.R32[(size_t)w * PAD + i];
         const float M = P.Fhat32[i] - R;
-        const float d = fmaf(-ds, P.Khat32[(size_t)s * PAD + i], fmaf(-dp, P.Khat32[(size_t)p * PAD + i], eps * M));
+        const float Kp = P.Qhi32[(p >> 5) * PAD + i] * P.Qlo32[(p & 31) * PAD + i];
+        const float Ks = P.Qhi32[(s >> 5) * PAD + i] * P.Qlo32[(s & 31) * PAD + i];
+        const float d = fmaf(-ds, Ks, fmaf(-dp, Kp, eps * M));
         part = fmaf(d, fmaf(2.0f, R, d), part);
     }
-    part = warp_sum(part);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
     if (lane == 0) { ok[q] = 1; delta[q] = (double)part; }
 }
 
@@ -220,6 +313,8 @@ __global__ void read_probe_kernel(const uint4 *__restrict__ buf, size_t n16, int
 }
 
 }  // namespace
+
+size_t sweep_fp32_table_bytes(const DevProblem &P) { return table_bytes(P); }
 
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st) {
     int dev = 0, sms = 0;
