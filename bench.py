@@ -118,6 +118,21 @@ def measure_read_bandwidth(torch, sail, nbytes: int, reps: int) -> float:
     return best
 
 
+def measure_smem_bandwidth(torch, sail, reps: int) -> float:
+    st = torch.cuda.current_stream()
+    sail._capi.smem_bandwidth_probe(64, st)
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(3):
+        e0.record(st)
+        nbytes = sail._capi.smem_bandwidth_probe(reps, st)
+        e1.record(st)
+        st.synchronize()
+        best = max(best, nbytes / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
 def kernel_traffic():
     """DRAM traffic per sweep launch from the committed ncu summary, if the kernel source
     is unchanged since the capture; else None."""
@@ -150,7 +165,9 @@ def run_gpu(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    # roofline denominator: read bandwidth of an L2-resident buffer (32 MiB, x400)
+    # roofline denominators: shared-memory read bandwidth (the sweep's kernel tables live
+    # there) and, for reference, the read bandwidth of an L2-resident buffer (32 MiB, x400)
+    smem_gbs = measure_smem_bandwidth(torch, sail, 20000)
     l2_gbs = measure_read_bandwidth(torch, sail, 32 << 20, 400)
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
@@ -190,7 +207,9 @@ def run_gpu(args, rank, world, local_rank):
     launches = info1["kernel_launches"] - info0["kernel_launches"] + args.steps  # + one flush per step
     own_launches = info1["kernel_launches"] - info0["kernel_launches"]
     moves_per_launch = (info1["moves"] - info0["moves"]) / max(sweep_n, 1)
-    bytes_per_move = 2 * N_TAU * 4 + 16        # two K columns (FP32) + b_p, b_s read and written
+    # algorithmic shared-memory bytes per walker-move: two kernel columns, each the product
+    # of two FP32 factor rows of N_tau entries, plus b_p and b_s
+    bytes_per_move = 4 * N_TAU * 4 + 8
     achieved = moves_per_launch * bytes_per_move / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9
     clk = clocks.summary(local_rank)
 
@@ -233,10 +252,12 @@ def run_gpu(args, rank, world, local_rank):
             "config": {"workload": WORKLOAD, "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
-            "roofline": {"kernel": "sweep_fp32", "bound": "l2", "achieved": achieved,
-                         "peak": l2_gbs, "unit": "GB/s", "frac": achieved / l2_gbs,
+            "roofline": {"kernel": "sweep_fp32", "bound": "smem", "achieved": achieved,
+                         "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
                          "traffic": kernel_traffic(),
-                         "peak_source": "measured live: 16-byte loads over an L2-resident 32 MiB buffer",
+                         "peak_source": "measured live: conflict-free 16-byte shared-memory loads, 2 blocks x 1024 "
+                                        "threads per SM",
+                         "l2_read_gbs_measured": l2_gbs,
                          "algorithmic_bytes_per_move": bytes_per_move,
                          "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
                          "sweep_share_of_step": sweep_ms / ms},

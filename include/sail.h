@@ -188,6 +188,13 @@ int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, vo
  * HBM (a buffer far larger). */
 int sail_probe_read_bandwidth(const void *d_buf, size_t bytes, int reps, void *d_sink, void *stream);
 
+/* Measurement utility for the roofline (no counterpart in the paper): two blocks per SM read
+ * a 32 KiB shared-memory buffer with conflict-free 16-byte loads, reps loads per thread; the
+ * number of bytes read goes to *bytes_read (host).  Timed by the caller on its stream, it
+ * gives the shared-memory read bandwidth the FP32 sweep's kernel tables are read at.
+ * d_sink: 8 bytes of device memory. */
+int sail_probe_smem_bandwidth(int reps, void *d_sink, void *stream, double *bytes_read);
+
 /*
  * Residue chi2 = sum_i ((F_i - sum_j K_ij a_j) / sigma_i)^2 of n_spectra histogram spectra,
  * for callers that cannot allocate device memory.  The paper has no counterpart: this is a

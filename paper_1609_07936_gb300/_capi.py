@@ -31,7 +31,8 @@ PREC_FP32 = 1
 EXPORTS = [
     "sail_default_params", "sail_workspace_size", "sail_create", "sail_anneal", "sail_average",
     "sail_get_info", "sail_get_state", "sail_set_state", "sail_get_trace", "sail_delta_probe",
-    "sail_philox", "sail_probe_read_bandwidth", "sail_residue_noalloc", "sail_destroy", "sail_last_error",
+    "sail_philox", "sail_probe_read_bandwidth", "sail_probe_smem_bandwidth", "sail_residue_noalloc",
+    "sail_destroy", "sail_last_error",
 ]
 
 
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.sail_delta_probe.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, _ip]
     L.sail_philox.argtypes = [ctypes.c_int, vp, ctypes.c_uint64, vp, vp]
     L.sail_probe_read_bandwidth.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, vp, vp]
+    L.sail_probe_smem_bandwidth.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sail_residue_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
     L.sail_destroy.argtypes = [vp]
     L.sail_last_error.argtypes = []
@@ -292,6 +294,17 @@ def read_bandwidth_probe(buf, reps: int, stream=None) -> None:
     nbytes = buf.numel() * buf.element_size() // 16 * 16
     _check(load().sail_probe_read_bandwidth(ctypes.c_void_p(buf.data_ptr()), nbytes, int(reps),
                                             ctypes.c_void_p(sink.data_ptr()), ctypes.c_void_p(st.cuda_stream)))
+
+
+def smem_bandwidth_probe(reps: int, stream=None) -> float:
+    """Launches the shared-memory read probe; returns the bytes it reads (timed by the caller)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    sink = torch.zeros(8, dtype=torch.uint8, device="cuda")
+    nbytes = ctypes.c_double(0.0)
+    _check(load().sail_probe_smem_bandwidth(int(reps), ctypes.c_void_p(sink.data_ptr()),
+                                            ctypes.c_void_p(st.cuda_stream), ctypes.byref(nbytes)))
+    return nbytes.value
 
 
 def philox(ctr: np.ndarray, seed: int):

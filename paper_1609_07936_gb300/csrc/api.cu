@@ -61,7 +61,7 @@ struct Layout {
     size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Tsweep, a0, R0;
     size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos;
     size_t acc_trace, m_trace, delta_trace;
-    size_t m, zero_l, donor_l, n_pairs, delta, counters;
+    size_t m, zero_l, donor_l, n_pairs, delta, counters, bz, bxi, cand, cand_Z, ctl;
     size_t mean, err, R_mean, chi2_mean, n_used, cut;
     size_t pr_walker, pr_p, pr_s, pr_eps, pr_delta, pr_ok;
     size_t total;
@@ -110,6 +110,11 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
     L.donor_l = take(W * 4);
     L.n_pairs = take(4);
     L.delta = take(8);
+    L.bz = take(W * 8);
+    L.bxi = take(W * 8);
+    L.cand = take(128 * 8);
+    L.cand_Z = take(128 * 4);
+    L.ctl = take(64);
     L.counters = take(sizeof(BlockCounters));
     L.mean = take(NO * 8);
     L.err = take(NO * 8);
@@ -421,6 +426,11 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     Bs.delta = (double *)(ws + L.delta);
     Bs.m_trace = p->trace ? (int *)(ws + L.m_trace) : nullptr;
     Bs.delta_trace = p->trace ? (double *)(ws + L.delta_trace) : nullptr;
+    Bs.z = (double *)(ws + L.bz);
+    Bs.xi = (double *)(ws + L.bxi);
+    Bs.cand = (double *)(ws + L.cand);
+    Bs.cand_Z = (int *)(ws + L.cand_Z);
+    Bs.ctl = (void *)(ws + L.ctl);
 
     cudaStream_t st = h->stream;
     auto up = [&](size_t off, const void *src, size_t bytes) {
@@ -710,6 +720,12 @@ int sail_probe_read_bandwidth(const void *d_buf, size_t bytes, int reps, void *d
     if (!d_buf || !d_sink || reps < 1 || bytes < 16 || (bytes & 15) || ((uintptr_t)d_buf & 15))
         return fail(SAIL_EINVAL, "read probe needs a 16-byte aligned buffer of 16k bytes and reps >= 1");
     SAIL_CUDA(launch_read_probe(d_buf, bytes, reps, d_sink, (cudaStream_t)stream), "read probe launch");
+    return SAIL_OK;
+}
+
+int sail_probe_smem_bandwidth(int reps, void *d_sink, void *stream, double *bytes_read) {
+    if (!d_sink || !bytes_read || reps < 1) return fail(SAIL_EINVAL, "smem probe needs a sink, a byte count and reps >= 1");
+    SAIL_CUDA(launch_smem_probe(reps, d_sink, (cudaStream_t)stream, bytes_read), "smem probe launch");
     return SAIL_OK;
 }
 

@@ -304,14 +304,15 @@ __device__ int block_scan_excl(int v, int *total, SolveShared &sh) {
     return warp_off + incl - v;
 }
 
-// Multipliers at one Delta; returns Z.  Walker l = threadIdx.x + kSolveThreads * q.
+// Multipliers at one Delta; returns Z.  Walker l = threadIdx.x + kSolveThreads * q, q < PT.
+template <int PT>
 __device__ int multipliers_at(int N, const double *z, const double *xi, double Delta, int *m,
                               SolveShared &sh) {
     const int tid = threadIdx.x;
-    double E[kSolvePerThread];
+    double E[PT];
     double sE = 0.0;
 #pragma unroll
-    for (int q = 0; q < kSolvePerThread; ++q) {
+    for (int q = 0; q < PT; ++q) {
         const int l = tid + kSolveThreads * q;
         E[q] = l < N ? exp(-Delta * z[q]) : 0.0;
         sE += E[q];
@@ -326,7 +327,7 @@ __device__ int multipliers_at(int N, const double *z, const double *xi, double D
         const double Th = sh.theta;
         int c = 0;
 #pragma unroll
-        for (int q = 0; q < kSolvePerThread; ++q) {
+        for (int q = 0; q < PT; ++q) {
             const int l = tid + kSolveThreads * q;
             int mq = 0;
             if (l < N) {
@@ -356,20 +357,20 @@ __device__ int multipliers_at(int N, const double *z, const double *xi, double D
         // Break points tied at ln Theta: take the upper end and drop the surplus copies
         // from the highest walker indices whose count rises across the final bracket.
         int c = count_at(hi, true);
-        int mlo[kSolvePerThread];
+        int mlo[PT];
         {
             if (tid < 32) { const double Th = exp(lo); if (tid == 0) sh.theta = Th; }
             __syncthreads();
             const double Th = sh.theta;
 #pragma unroll
-            for (int q = 0; q < kSolvePerThread; ++q) {
+            for (int q = 0; q < PT; ++q) {
                 const int l = tid + kSolveThreads * q;
                 const double v = l < N ? floor(Th * E[q] + xi[q]) : 0.0;
                 mlo[q] = v >= (double)N ? N : (int)v;
             }
             __syncthreads();
         }
-        for (int q = kSolvePerThread - 1; q >= 0 && c > N; --q) {
+        for (int q = PT - 1; q >= 0 && c > N; --q) {
             for (int t = kSolveThreads - 1; t >= 0 && c > N; --t) {
                 // serial over walkers in descending index order; thread t owns walker l
                 if (tid == t) {
@@ -390,73 +391,167 @@ __device__ int multipliers_at(int N, const double *z, const double *xi, double D
     }
     int zc = 0;
 #pragma unroll
-    for (int q = 0; q < kSolvePerThread; ++q) {
+    for (int q = 0; q < PT; ++q) {
         const int l = tid + kSolveThreads * q;
         zc += (l < N && m[q] == 0);
     }
     return block_sum_i(zc, sh);
 }
 
-__global__ void __launch_bounds__(kSolveThreads) branch_solve_kernel(DevProblem P, DevState S,
-                                                                     BranchScratch B, int block_index,
-                                                                     double fraction, int event) {
-    __shared__ SolveShared sh;
+// The Delta search runs as speculative rounds over many blocks: every trial Delta the
+// sequential search could visit next is evaluated at once, one block (one SM) per trial, and
+// a one-thread control kernel replays the sequential search over the results.  Round 0 holds
+// the doubling trials 2^k, k = 0..64; each later round a depth-7 tree of bisection midpoints.
+// The replay takes exactly the steps, trial values and early exit of the sequential search,
+// so the chosen Delta and multipliers are the same; one SM per trial brings 127 SMs' FP64
+// units to bear on what is otherwise a long chain on one SM.
+constexpr int kTreeDepth = 7;
+constexpr int kMaxCand = (1 << kTreeDepth) - 1;   // 127 >= the 65 doubling trials
+
+struct SolveCtl {
+    double lo, hi, Delta;
+    int Zhi, Zt, done, it, n_cand;
+};
+
+template <int PT>
+__device__ void load_zxi(const BranchScratch &B, int N, double *z, double *xi) {
+#pragma unroll
+    for (int q = 0; q < PT; ++q) {
+        const int l = threadIdx.x + kSolveThreads * q;
+        z[q] = l < N ? B.z[l] : 0.0;
+        xi[q] = l < N ? B.xi[l] : 0.5;
+    }
+}
+
+__global__ void __launch_bounds__(kSolveThreads) branch_prep_kernel(DevProblem P, DevState S, BranchScratch B,
+                                                                    int block_index, double fraction) {
+    __shared__ double s_cmin, s_spread;
     const int N = P.n_walkers, tid = threadIdx.x;
+    SolveCtl *ctl = reinterpret_cast<SolveCtl *>(B.ctl);
     int Zt = (int)floor(fraction * N + 0.5);
     if (Zt > N - 1) Zt = N - 1;
-    int m[kSolvePerThread];
-    double Delta = 0.0;
-    if (Zt <= 0) {
-#pragma unroll
-        for (int q = 0; q < kSolvePerThread; ++q) m[q] = 1;
-    } else {
-        if (tid == 0) {
-            double cmin = S.chi2[0], csum = 0.0;
-            for (int l = 0; l < N; ++l) {
-                if (S.chi2[l] < cmin) cmin = S.chi2[l];
-                csum += S.chi2[l];
-            }
-            sh.cmin = cmin;
-            sh.spread = csum / N - cmin;
+    if (tid == 0) {
+        double cmin = S.chi2[0], csum = 0.0;
+        for (int l = 0; l < N; ++l) {
+            if (S.chi2[l] < cmin) cmin = S.chi2[l];
+            csum += S.chi2[l];
         }
-        __syncthreads();
-        const double cmin = sh.cmin, spread = sh.spread;
-        double z[kSolvePerThread], xi[kSolvePerThread];
-        const uint2 key = philox_key(P.seed);
-#pragma unroll
-        for (int q = 0; q < kSolvePerThread; ++q) {
-            const int l = tid + kSolveThreads * q;
-            z[q] = 0.0;
-            xi[q] = 0.5;
-            if (l < N) {
-                z[q] = spread > 0.0 ? (S.chi2[l] - cmin) / spread : 0.0;
-                xi[q] = unit64(philox4x32_10(make_uint4((uint32_t)l, (uint32_t)block_index, 0u, 1u), key).x);
-            }
+        s_cmin = cmin;
+        s_spread = csum / N - cmin;
+        ctl->Zt = Zt;
+        ctl->done = Zt <= 0;
+        ctl->it = 0;
+        ctl->lo = 0.0;
+        ctl->hi = 1.0;
+        ctl->Delta = 0.0;
+        ctl->n_cand = 65;
+    }
+    if (tid < 65) B.cand[tid] = ldexp(1.0, tid);
+    __syncthreads();
+    const double cmin = s_cmin, spread = s_spread;
+    const uint2 key = philox_key(P.seed);
+    for (int l = tid; l < N; l += blockDim.x) {
+        B.z[l] = spread > 0.0 ? (S.chi2[l] - cmin) / spread : 0.0;
+        B.xi[l] = unit64(philox4x32_10(make_uint4((uint32_t)l, (uint32_t)block_index, 0u, 1u), key).x);
+    }
+}
+
+template <int PT>
+__global__ void __launch_bounds__(kSolveThreads) branch_eval_kernel(int N, BranchScratch B) {
+    __shared__ SolveShared sh;
+    const SolveCtl *ctl = reinterpret_cast<const SolveCtl *>(B.ctl);
+    if (ctl->done || (int)blockIdx.x >= ctl->n_cand) return;   // uniform per block
+    double z[PT], xi[PT];
+    int m[PT];
+    load_zxi<PT>(B, N, z, xi);
+    const int Z = multipliers_at<PT>(N, z, xi, B.cand[blockIdx.x], m, sh);
+    if (threadIdx.x == 0) B.cand_Z[blockIdx.x] = Z;
+}
+
+// Writes the 127 midpoints of a depth-7 bisection tree over (lo, hi) in heap order: node n
+// (1-based) holds the interval reached by the outcomes on its path; its children 2n and 2n+1
+// are the intervals after "Z > target" (hi <- mid) and "Z < target" (lo <- mid).
+__device__ void build_tree(double lo, double hi, double *cand) {
+    double nlo[kMaxCand + 1], nhi[kMaxCand + 1];
+    nlo[1] = lo;
+    nhi[1] = hi;
+    for (int n = 1; n <= kMaxCand; ++n) {
+        const double mid = 0.5 * (nlo[n] + nhi[n]);
+        cand[n - 1] = mid;
+        if (2 * n <= kMaxCand) {
+            nlo[2 * n] = nlo[n];
+            nhi[2 * n] = mid;
+            nlo[2 * n + 1] = mid;
+            nhi[2 * n + 1] = nhi[n];
         }
+    }
+}
+
+__global__ void branch_control_kernel(BranchScratch B, int round) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    SolveCtl *ctl = reinterpret_cast<SolveCtl *>(B.ctl);
+    if (ctl->done) return;
+    const int Zt = ctl->Zt;
+    if (round == 0) {
+        // doubling: hi = 1, 2, 4, ... while Z(hi) < target, at most 64 doublings
         double lo = 0.0, hi = 1.0;
-        int Zhi = multipliers_at(N, z, xi, hi, m, sh);
-        for (int it = 0; it < 64 && Zhi < Zt; ++it) {
+        int k = 0, Zhi = B.cand_Z[0];
+        while (k < 64 && Zhi < Zt) {
             lo = hi;
             hi = 2.0 * hi;
-            Zhi = multipliers_at(N, z, xi, hi, m, sh);
+            ++k;
+            Zhi = B.cand_Z[k];
         }
-        if (Zhi != Zt) {
-            for (int it = 0; it < 64; ++it) {
-                const double mid = 0.5 * (lo + hi);
-                if (mid <= lo || mid >= hi) break;
-                const int Zm = multipliers_at(N, z, xi, mid, m, sh);
-                if (Zm == Zt) { hi = mid; Zhi = Zm; break; }
-                if (Zm < Zt) lo = mid; else { hi = mid; Zhi = Zm; }
-            }
+        ctl->lo = lo;
+        ctl->hi = hi;
+        ctl->Zhi = Zhi;
+        if (Zhi == Zt) {
+            ctl->done = 1;
+            ctl->Delta = hi;
+            return;
         }
-        multipliers_at(N, z, xi, hi, m, sh);
-        Delta = hi;
+    } else {
+        double lo = ctl->lo, hi = ctl->hi;
+        int n = 1;
+        for (int d = 0; d < kTreeDepth; ++d) {
+            if (ctl->it >= 64) { ctl->done = 1; ctl->Delta = hi; return; }
+            const double mid = B.cand[n - 1];
+            if (mid <= lo || mid >= hi) { ctl->done = 1; ctl->Delta = hi; return; }
+            const int Zm = B.cand_Z[n - 1];
+            ctl->it += 1;
+            if (Zm == Zt) { ctl->done = 1; ctl->Delta = mid; return; }
+            if (Zm < Zt) { lo = mid; n = 2 * n + 1; }
+            else { hi = mid; n = 2 * n; }
+        }
+        ctl->lo = lo;
+        ctl->hi = hi;
     }
-    // Pairing: zero-multiplier walkers ascending, matched with surplus copies (walker l
-    // listed m_l - 1 times) ascending.  Walker order is q-major, thread-minor.
+    if (ctl->it >= 64) { ctl->done = 1; ctl->Delta = ctl->hi; return; }
+    build_tree(ctl->lo, ctl->hi, B.cand);
+    ctl->n_cand = kMaxCand;
+}
+
+// Final multipliers at the chosen Delta and the imprint pairing: zero-multiplier walkers
+// ascending, matched with surplus copies (walker l listed m_l - 1 times) ascending.
+template <int PT>
+__global__ void __launch_bounds__(kSolveThreads) branch_final_kernel(int N, BranchScratch B, int event) {
+    __shared__ SolveShared sh;
+    const SolveCtl *ctl = reinterpret_cast<const SolveCtl *>(B.ctl);
+    const int tid = threadIdx.x;
+    int m[PT];
+    double Delta = 0.0;
+    if (ctl->Zt <= 0) {
+#pragma unroll
+        for (int q = 0; q < PT; ++q) m[q] = 1;
+    } else {
+        double z[PT], xi[PT];
+        load_zxi<PT>(B, N, z, xi);
+        Delta = ctl->done ? ctl->Delta : ctl->hi;
+        multipliers_at<PT>(N, z, xi, Delta, m, sh);
+    }
     int zero_base = 0, copy_base = 0;
 #pragma unroll
-    for (int q = 0; q < kSolvePerThread; ++q) {
+    for (int q = 0; q < PT; ++q) {
         const int l = tid + kSolveThreads * q;
         const bool valid = l < N;
         const int isz = valid && m[q] == 0;
@@ -478,6 +573,24 @@ __global__ void __launch_bounds__(kSolveThreads) branch_solve_kernel(DevProblem 
         B.delta[0] = Delta;
         if (B.delta_trace) B.delta_trace[event] = Delta;
     }
+}
+
+template <int PT>
+cudaError_t launch_solve(const DevProblem &P, const DevState &S, const BranchScratch &B, int block_index,
+                         double fraction, int event, cudaStream_t st, int *launches) {
+    const int N = P.n_walkers;
+    branch_prep_kernel<<<1, kSolveThreads, 0, st>>>(P, S, B, block_index, fraction);
+    branch_eval_kernel<PT><<<kMaxCand, kSolveThreads, 0, st>>>(N, B);
+    branch_control_kernel<<<1, 32, 0, st>>>(B, 0);
+    *launches += 3;
+    for (int r = 1; r <= (64 + kTreeDepth - 1) / kTreeDepth; ++r) {
+        branch_eval_kernel<PT><<<kMaxCand, kSolveThreads, 0, st>>>(N, B);
+        branch_control_kernel<<<1, 32, 0, st>>>(B, r);
+        *launches += 2;
+    }
+    branch_final_kernel<PT><<<1, kSolveThreads, 0, st>>>(N, B, event);
+    *launches += 1;
+    return cudaGetLastError();
 }
 
 // Imprinting (Sec. 2.5): a^(l1) <- t a^(l2) + (1 - t) a^(l1); the residual mixes the same way
@@ -687,11 +800,13 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,
                           int block_index, double fraction, double imprint_t, int event, cudaStream_t st,
                           int *launches) {
-    branch_solve_kernel<<<1, kSolveThreads, 0, st>>>(P, S, B, block_index, fraction, event);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e;
+    if (P.n_walkers <= kSolveThreads * 4) e = launch_solve<4>(P, S, B, block_index, fraction, event, st, launches);
+    else if (P.n_walkers <= kSolveThreads * 8) e = launch_solve<8>(P, S, B, block_index, fraction, event, st, launches);
+    else e = launch_solve<16>(P, S, B, block_index, fraction, event, st, launches);
     if (e != cudaSuccess) return e;
     imprint_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, B, precision, imprint_t);
-    *launches += 2;
+    *launches += 1;
     return cudaGetLastError();
 }
 

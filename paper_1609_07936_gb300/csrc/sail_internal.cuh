@@ -66,6 +66,11 @@ struct BranchScratch {
     double *delta;         // [1] Delta of the solve
     int *m_trace;          // [max_events][n_walkers] or null
     double *delta_trace;   // [max_events] or null
+    double *z;             // [n_walkers] normalised chi2 of the solve
+    double *xi;            // [n_walkers] branching draws
+    double *cand;          // [128] trial Deltas of one speculative round
+    int *cand_Z;           // [128] zero counts at the trials
+    void *ctl;             // search state (64 bytes)
 };
 
 struct BlockCounters {     // device-side block statistics, read back once per block
@@ -100,6 +105,7 @@ cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *o
 // Shared memory the FP32 sweep needs for its kernel tables (must fit one block).
 size_t sweep_fp32_table_bytes(const DevProblem &P);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
+cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes);
 
 // Records the message sail_last_error() returns on this thread; returns code.
 int set_error(int code, const char *fmt, ...);

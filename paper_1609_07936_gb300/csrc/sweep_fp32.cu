@@ -312,7 +312,39 @@ __global__ void read_probe_kernel(const uint4 *__restrict__ buf, size_t n16, int
     if (acc == 0x9E3779B9u) sink[0] = acc;  // keeps the loads; practically never taken
 }
 
+// Shared-memory read bandwidth: each thread reads 16-byte words of a 32 KiB block-local
+// buffer, a warp's 32 lanes on 512 consecutive bytes (no bank conflicts), reps times; the
+// loads are volatile so none is merged or hoisted.
+__global__ void __launch_bounds__(1024) smem_probe_kernel(int reps, unsigned long long *sink) {
+    __shared__ uint4 buf[2048];
+    for (int q = threadIdx.x; q < 2048; q += blockDim.x) buf[q] = make_uint4(q, q * 3u, q * 5u, q * 7u);
+    __syncthreads();
+    uint32_t acc = 0;
+    int idx = threadIdx.x;
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
+#pragma unroll 8
+    for (int r = 0; r < reps; ++r) {
+        uint32_t x, y, z, w;
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x), "=r"(y), "=r"(z), "=r"(w)
+                     : "r"(base + 16u * (uint32_t)idx));
+        acc ^= x ^ y ^ z ^ w;
+        idx = (idx + 1056) & 2047;   // next 512-byte row for the warp, shifted by 32 words
+    }
+    if (acc == 0x9E3779B9u) sink[0] = acc;  // keeps the loads; practically never taken
+}
+
 }  // namespace
+
+cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = 2 * sms;
+    smem_probe_kernel<<<blocks, 1024, 0, st>>>(reps, (unsigned long long *)sink);
+    *bytes = (double)blocks * 1024.0 * (double)reps * 16.0;
+    return cudaGetLastError();
+}
 
 size_t sweep_fp32_table_bytes(const DevProblem &P) { return table_bytes(P); }
 
