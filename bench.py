@@ -32,18 +32,22 @@ N_TAU, N_OMEGA, N_WALKERS = 200, 1000, 4096
 SWEEPS_PER_BLOCK, RESYNC_EVERY, N_SWEEPS = 100, 50, 20000
 NOISE = 1e-4
 WORKLOAD = (f"paper_scale_double_lorentz: N_tau={N_TAU} on [0,8], N_omega={N_OMEGA} on [0,20], "
-            f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, FP64 resync every {RESYNC_EVERY} sweeps, "
+            f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, tensor-core resync every {RESYNC_EVERY} sweeps, "
             f"branching every {SWEEPS_PER_BLOCK} sweeps (f=1/4, t=0.1), {N_SWEEPS}-sweep schedule T 10->1e-9")
 METRIC = "walker-moves/sec"
 MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 
 
-def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY):
+RESYNC_KIND = 1    # residual recomputation on the tensor cores (tcgen05, TF32 x3)
+
+
+def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
-                      T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing)
+                      T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
+                      resync_kind=resync_kind)
     return P, prm
 
 
@@ -171,13 +175,13 @@ def run_gpu(args, rank, world, local_rank):
     l2_gbs = measure_read_bandwidth(torch, sail, 32 << 20, 400)
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
-    P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every)
+    P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
     del warm
 
-    P, prm = params_for(seed=rank, resync_every=args.resync_every)
+    P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -217,7 +221,7 @@ def run_gpu(args, rank, world, local_rank):
     # K blocks (per-block statistics D2H), average (D2H of the spectrum and errors)
     e2e = None
     if not args.no_e2e:
-        P2, prm2 = params_for(seed=rank + 77, timing=False)
+        P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -315,6 +319,8 @@ def main():
     ap.add_argument("--cpu-sample-walkers", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1],
+                    help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,
                     help="sweeps per sweep-kernel launch; smaller values give short launches for profiling")
     args = ap.parse_args()

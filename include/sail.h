@@ -37,6 +37,7 @@ extern "C" {
 #define SAIL_ENOMEM (-2)       /* workspace smaller than sail_workspace_size() */
 #define SAIL_ECUDA (-3)        /* a CUDA runtime call or kernel launch failed */
 #define SAIL_ESTATE (-4)       /* call not valid in the handle's current state */
+#define SAIL_ETIMEOUT (-5)     /* a bounded device-side wait gave up (results of that call invalid) */
 
 /* Arithmetic of the Metropolis moves. */
 #define SAIL_PREC_FP64 0   /* validation path: FP64 state, explicit rescale of every bin, sums in the
@@ -70,7 +71,9 @@ typedef struct sail_params {
                                branching multipliers (validation; enlarges the workspace) */
     int timing;             /* 1: time every kernel with CUDA events on the handle's stream;
                                totals appear in sail_info */
-    int reserved[6];
+    int resync_kind;        /* FP32 state: 0 = FP32-FMA GEMM with FP64 chunk sums, 1 = tensor
+                               cores (tcgen05 TF32, three-term split) */
+    int reserved[5];
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */

@@ -24,6 +24,9 @@ SAIL_EINVAL = -1
 SAIL_ENOMEM = -2
 SAIL_ECUDA = -3
 SAIL_ESTATE = -4
+SAIL_ETIMEOUT = -5
+RESYNC_FP32 = 0
+RESYNC_TENSOR = 1
 PREC_FP64 = 0
 PREC_FP32 = 1
 
@@ -44,7 +47,8 @@ class CParams(ctypes.Structure):
         ("imprint_t", ctypes.c_double), ("move_scale", ctypes.c_double), ("y_p", ctypes.c_double),
         ("y_m", ctypes.c_double), ("y_min", ctypes.c_double), ("A", ctypes.c_double), ("B", ctypes.c_double),
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
-        ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("reserved", ctypes.c_int * 6),
+        ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
+        ("reserved", ctypes.c_int * 5),
     ]
 
 
@@ -162,6 +166,7 @@ class Params:
     seed: int = 0
     trace: bool = False
     timing: bool = False
+    resync_kind: int = 0
 
     def c(self) -> CParams:
         p = CParams()

@@ -23,6 +23,7 @@ UNITS = {
     "exact64.cu": ["-fmad=false"],
     "sweep_fp32.cu": [],
     "resync_fp32.cu": [],
+    "resync_tc.cu": [],
     "noalloc.cu": ["-fmad=false"],
 }
 

@@ -58,7 +58,8 @@ constexpr double kPi = 3.14159265358979323846;
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Tsweep, a0, R0;
+    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Khi32, Klo32, Tsweep, a0, R0;
+    size_t status;
     size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos;
     size_t acc_trace, m_trace, delta_trace;
     size_t m, zero_l, donor_l, n_pairs, delta, counters, bz, bxi, cand, cand_Z, ctl;
@@ -83,6 +84,10 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
     L.rgap32 = take(NO * 4);
     L.Qhi32 = take((NO + 31) / 32 * PAD * 4);
     L.Qlo32 = take(32 * PAD * 4);
+    const size_t NOP = (NO + 31) / 32 * 32;
+    L.Khi32 = take(PAD * NOP * 4);
+    L.Klo32 = take(PAD * NOP * 4);
+    L.status = take(4);
     L.Tsweep = take((size_t)p.n_sweeps * 8);
     L.a0 = take(NO * 8);
     L.R0 = take(PAD * 8);
@@ -151,6 +156,7 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->move_scale < 1) || std::isnan(p->move_scale)) return fail(SAIL_EINVAL, "move_scale must be < 1");
     if (!std::isfinite(p->B)) return fail(SAIL_EINVAL, "B must be given (Sec. 2.2)");
     if (!(p->avg_chi2_factor >= 1)) return fail(SAIL_EINVAL, "avg_chi2_factor must be >= 1");
+    if (p->resync_kind != 0 && p->resync_kind != 1) return fail(SAIL_EINVAL, "resync_kind must be 0 or 1");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -173,6 +179,7 @@ struct sail_ctx {
     int sweeps_done, blocks_done, events;
     long long launches, moves;
     unsigned long long acc_seen, pos_seen;
+    int *status;             // device status word: nonzero after a timed-out device wait
     // optional per-kernel timing: event pairs recorded around launches, read at block ends
     struct Timed { cudaEvent_t a, b; int kind; };
     std::vector<Timed> timed;
@@ -329,6 +336,21 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     for (int l = 0; l < 32; ++l)
         for (int i = 0; i < n_tau; ++i) Qlo[(size_t)l * PAD + i] = (float)std::exp(-(double)l * dw * tau[i]);
     for (int k = 1; k < n_omega; ++k) rgap[k] = (float)(1.0 / ((double)k * dw));
+    // tensor-core resync tables, K-major [i][j]: Khi = Khat cut to TF32, Klo = the remainder
+    const int NOP = (n_omega + 31) / 32 * 32;
+    std::vector<float> Khi((size_t)PAD * NOP, 0.0f), Klo((size_t)PAD * NOP, 0.0f);
+    for (int i = 0; i < n_tau; ++i)
+        for (int j = 0; j < n_omega; ++j) {
+            const double k64 = K64[(size_t)j * PAD + i];
+            uint32_t bits;
+            const float f = (float)k64;
+            std::memcpy(&bits, &f, 4);
+            bits &= 0xFFFFE000u;
+            float hi;
+            std::memcpy(&hi, &bits, 4);
+            Khi[(size_t)i * NOP + j] = hi;
+            Klo[(size_t)i * NOP + j] = (float)(k64 - (double)hi);
+        }
 
     // ---- start spectrum: largest entropy with sum a = A and sum a x = B, a_j ~ exp(-lambda x_j)
     const double target = B / A, xc = 0.5 * (x0 + xN), span = xN - x0;
@@ -405,6 +427,10 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.rgap32 = (const float *)(ws + L.rgap32);
     P.Qhi32 = (const float *)(ws + L.Qhi32);
     P.Qlo32 = (const float *)(ws + L.Qlo32);
+    P.Khi32 = (const float *)(ws + L.Khi32);
+    P.Klo32 = (const float *)(ws + L.Klo32);
+    P.n_omega_pad = NOP;
+    h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;
     S.a64 = p->precision == SAIL_PREC_FP64 ? (double *)(ws + L.a64) : nullptr;
@@ -447,6 +473,9 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     if (e == cudaSuccess) e = up(L.rgap32, rgap.data(), NO * 4);
     if (e == cudaSuccess) e = up(L.Qhi32, Qhi.data(), Qhi.size() * 4);
     if (e == cudaSuccess) e = up(L.Qlo32, Qlo.data(), Qlo.size() * 4);
+    if (e == cudaSuccess) e = up(L.Khi32, Khi.data(), Khi.size() * 4);
+    if (e == cudaSuccess) e = up(L.Klo32, Klo.data(), Klo.size() * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.status, 0, 4, st);
     if (e == cudaSuccess) e = up(L.Tsweep, T.data(), T.size() * 8);
     if (e == cudaSuccess) e = up(L.a0, a0.data(), NO * 8);
     if (e == cudaSuccess) e = up(L.R0, R0.data(), PAD * 8);
@@ -550,7 +579,7 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
             if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
             tk = timed_begin(h);
             int l = 0;
-            e = launch_resync(h->P, h->S, p.precision, 1, st, &l);
+            e = launch_resync(h->P, h->S, p.precision, 1, p.resync_kind, h->status, st, &l);
             timed_end(h, tk, kResync);
             if (e != cudaSuccess) return cuda_fail(e, "resync launch");
             h->launches += 1 + l;
@@ -575,13 +604,16 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
         h->launches += 1;
         if (e != cudaSuccess) return cuda_fail(e, "stats launch");
         BlockCounters bc{};
+        int dev_status = 0;
         SAIL_CUDA(cudaMemcpyAsync(&bc, h->ws + h->L.counters, sizeof bc, cudaMemcpyDeviceToHost, st), "stats D2H");
+        SAIL_CUDA(cudaMemcpyAsync(&dev_status, h->status, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
         if (branched) {
             SAIL_CUDA(cudaMemcpyAsync(&delta, h->ws + h->L.delta, 8, cudaMemcpyDeviceToHost, st), "stats D2H");
             SAIL_CUDA(cudaMemcpyAsync(&zeros, h->ws + h->L.n_pairs, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
         }
         SAIL_CUDA(cudaStreamSynchronize(st), "block sync");
         timed_collect(h);
+        if (dev_status) return fail(SAIL_ETIMEOUT, "a device-side wait timed out (status %d)", dev_status);
         if (stats) {
             sail_block_stats &s = stats[done];
             std::memset(&s, 0, sizeof s);
@@ -665,7 +697,7 @@ int sail_set_state(sail_t h, const double *a, const int *acc_prev) {
     }
     if (acc_prev) SAIL_CUDA(cudaMemcpyAsync(ws + h->L.acc_prev, acc_prev, W * 4, cudaMemcpyHostToDevice, st), "H2D");
     int l = 0;
-    SAIL_CUDA(launch_resync(h->P, h->S, h->prm.precision, 0, st, &l), "resync launch");
+    SAIL_CUDA(launch_resync(h->P, h->S, h->prm.precision, 0, h->prm.resync_kind, h->status, st, &l), "resync launch");
     h->launches += l;
     SAIL_CUDA(cudaStreamSynchronize(st), "set_state sync");
     return SAIL_OK;

@@ -780,8 +780,8 @@ cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int n0, in
     }
 }
 
-cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, cudaStream_t st,
-                          int *launches) {
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
+                          int *status, cudaStream_t st, int *launches) {
     if (precision == 0) {
         resync_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision);
         *launches += 1;
@@ -793,8 +793,8 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    *launches += 1;
-    return launch_resync_fp32(P, S, st);
+    *launches += kind == 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
+    return kind == 1 ? launch_resync_tc(P, S, status, st) : launch_resync_fp32(P, S, st);
 }
 
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,

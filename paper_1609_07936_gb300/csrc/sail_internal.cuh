@@ -41,6 +41,9 @@ struct DevProblem {
     const float *rgap32;
     const float *Qhi32;
     const float *Qlo32;
+    const float *Khi32;    // [n_tau_pad][n_omega_pad] Khat cut to TF32 (K-major, tensor-core resync)
+    const float *Klo32;    // [n_tau_pad][n_omega_pad] Khat - Khi
+    int n_omega_pad;       // n_omega rounded up to 32
     const double *Tsweep;
 };
 
@@ -87,9 +90,12 @@ cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_
                               int sweep_end, cudaStream_t st);
 // FP64 state: sequential FP64 recomputation.  FP32 state: optional sum-rule restoration
 // (restore != 0), then the tiled GEMM of resync_fp32.cu.
-cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, cudaStream_t st,
-                          int *launches);
+cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
+                          int *status, cudaStream_t st, int *launches);
 cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStream_t st);
+// Tensor-core (tcgen05, TF32 x3) residual recomputation for FP32 state; status[0] <- 1 on a
+// timed-out wait.
+cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st);
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);
