@@ -426,15 +426,18 @@ __device__ void load_zxi(const BranchScratch &B, int N, double *z, double *xi) {
 __global__ void __launch_bounds__(kSolveThreads) branch_prep_kernel(DevProblem P, DevState S, BranchScratch B,
                                                                     int block_index, double fraction) {
     __shared__ double s_cmin, s_spread;
+    extern __shared__ double s_chi2[];           // the walkers' chi2, staged for the ordered sum
     const int N = P.n_walkers, tid = threadIdx.x;
     SolveCtl *ctl = reinterpret_cast<SolveCtl *>(B.ctl);
     int Zt = (int)floor(fraction * N + 0.5);
     if (Zt > N - 1) Zt = N - 1;
+    for (int l = tid; l < N; l += blockDim.x) s_chi2[l] = S.chi2[l];
+    __syncthreads();
     if (tid == 0) {
-        double cmin = S.chi2[0], csum = 0.0;
+        double cmin = s_chi2[0], csum = 0.0;
         for (int l = 0; l < N; ++l) {
-            if (S.chi2[l] < cmin) cmin = S.chi2[l];
-            csum += S.chi2[l];
+            if (s_chi2[l] < cmin) cmin = s_chi2[l];
+            csum += s_chi2[l];
         }
         s_cmin = cmin;
         s_spread = csum / N - cmin;
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(kSolveThreads) branch_prep_kernel(DevProblem P
     const double cmin = s_cmin, spread = s_spread;
     const uint2 key = philox_key(P.seed);
     for (int l = tid; l < N; l += blockDim.x) {
-        B.z[l] = spread > 0.0 ? (S.chi2[l] - cmin) / spread : 0.0;
+        B.z[l] = spread > 0.0 ? (s_chi2[l] - cmin) / spread : 0.0;
         B.xi[l] = unit64(philox4x32_10(make_uint4((uint32_t)l, (uint32_t)block_index, 0u, 1u), key).x);
     }
 }
@@ -579,7 +582,10 @@ template <int PT>
 cudaError_t launch_solve(const DevProblem &P, const DevState &S, const BranchScratch &B, int block_index,
                          double fraction, int event, cudaStream_t st, int *launches) {
     const int N = P.n_walkers;
-    branch_prep_kernel<<<1, kSolveThreads, 0, st>>>(P, S, B, block_index, fraction);
+    const size_t staged = (size_t)N * sizeof(double);   // <= 128 KiB (16384 walkers)
+    cudaError_t e0 = cudaFuncSetAttribute(branch_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
+    if (e0 != cudaSuccess) return e0;
+    branch_prep_kernel<<<1, kSolveThreads, staged, st>>>(P, S, B, block_index, fraction);
     branch_eval_kernel<PT><<<kMaxCand, kSolveThreads, 0, st>>>(N, B);
     branch_control_kernel<<<1, 32, 0, st>>>(B, 0);
     *launches += 3;
