@@ -222,6 +222,50 @@ int sail_residue_noalloc(const double *d_tau, const double *d_F, const double *d
                          const double *d_omega, int n_omega, const double *d_a, int n_spectra,
                          double *d_chi2, double *d_R, void *stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent inversions (each a k-vector or data set of its own, Sec. 2.1) annealed
+ * together: every block, one persistent sweep launch covers the walkers of all problems
+ * (blocks of the GPU take (problem, walker range) items from a queue), then each problem's
+ * residual recomputation, branching and statistics run as for a single handle.  A problem's
+ * results do not depend on the other problems in the batch: its random numbers are keyed by
+ * its own seed and walker indices, and every step of its arithmetic is per walker or per
+ * problem.  All problems use FP32 precision and share sweeps_per_block and resync_every. */
+typedef struct sail_batch_ctx *sail_batch_t;
+
+typedef struct sail_problem {
+    const double *tau, *F, *sigma; /* host arrays of n_tau, as in sail_create */
+    int n_tau;
+    const double *omega;           /* host array of n_omega bin centres */
+    int n_omega;
+    sail_params params;            /* precision SAIL_PREC_FP32 */
+} sail_problem;
+
+/* Workspace bytes for a batch of n problems (their handles' workspaces plus the queue). */
+int sail_batch_workspace_size(int n, const sail_problem *probs, size_t *bytes);
+
+/* Creates every problem's handle inside d_workspace (ws_bytes >= sail_batch_workspace_size)
+ * on stream.  autotune = 1 lets the first sweep launches and residual recomputations try the
+ * candidate walker-to-block mappings (items of 4, 8 or 16 walker pairs per block) and
+ * tensor-core tile widths, timing each with CUDA events, and keep the fastest; results do
+ * not depend on either choice. */
+int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int autotune, void *d_workspace,
+                      size_t ws_bytes, void *stream);
+
+/* Runs up to max_blocks blocks for every problem with sweeps left (and, with a target, not
+ * yet converged); *n_done: blocks run. */
+int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done);
+
+/* The handle of problem k for sail_average, sail_get_state, sail_get_info ... (owned by the
+ * batch: do not destroy it, do not anneal it on its own). */
+int sail_batch_handle(sail_batch_t b, int k, sail_t *h);
+
+/* The autotuner's choice of walker pairs per block item, the device time per walker-move of
+ * the last batched sweep launch (ns, 0 before any), and the batched sweep launches so far
+ * (each problem's own kernel count is in its sail_info). */
+int sail_batch_tuning(sail_batch_t b, int *item_pairs, double *ns_per_move, long long *sweep_launches);
+
+int sail_batch_destroy(sail_batch_t b);
+
 /* Frees the host side of the handle; the workspace stays the caller's. */
 int sail_destroy(sail_t h);
 

@@ -35,7 +35,8 @@ EXPORTS = [
     "sail_default_params", "sail_workspace_size", "sail_create", "sail_anneal", "sail_average",
     "sail_get_info", "sail_get_state", "sail_set_state", "sail_get_trace", "sail_delta_probe",
     "sail_philox", "sail_probe_read_bandwidth", "sail_probe_smem_bandwidth", "sail_residue_noalloc",
-    "sail_destroy", "sail_last_error",
+    "sail_batch_workspace_size", "sail_batch_create", "sail_batch_anneal", "sail_batch_handle",
+    "sail_batch_tuning", "sail_batch_destroy", "sail_destroy", "sail_last_error",
 ]
 
 
@@ -49,6 +50,14 @@ class CParams(ctypes.Structure):
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
         ("reserved", ctypes.c_int * 5),
+    ]
+
+
+class CProblem(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.POINTER(ctypes.c_double)), ("F", ctypes.POINTER(ctypes.c_double)),
+        ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_tau", ctypes.c_int),
+        ("omega", ctypes.POINTER(ctypes.c_double)), ("n_omega", ctypes.c_int), ("params", CParams),
     ]
 
 
@@ -112,6 +121,13 @@ def load(path: str = LIB_PATH):
     L.sail_probe_read_bandwidth.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, vp, vp]
     L.sail_probe_smem_bandwidth.argtypes = [ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double)]
     L.sail_residue_noalloc.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp, vp, vp]
+    L.sail_batch_workspace_size.argtypes = [ctypes.c_int, ctypes.POINTER(CProblem), ctypes.POINTER(ctypes.c_size_t)]
+    L.sail_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(CProblem), ctypes.c_int, vp,
+                                    ctypes.c_size_t, vp]
+    L.sail_batch_anneal.argtypes = [vp, ctypes.c_int, _ip]
+    L.sail_batch_handle.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+    L.sail_batch_tuning.argtypes = [vp, _ip, _dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.sail_batch_destroy.argtypes = [vp]
     L.sail_destroy.argtypes = [vp]
     L.sail_last_error.argtypes = []
     L.sail_last_error.restype = ctypes.c_char_p
@@ -215,10 +231,22 @@ class Sail:
                                     ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
                                     ctypes.c_void_p(self.stream.cuda_stream)))
 
+    @classmethod
+    def _view(cls, handle, n_tau, n_omega, params: "Params", owner):
+        """A handle owned by a batch: usable for queries, never destroyed here."""
+        self = cls.__new__(cls)
+        self.params = params
+        self.lib = load()
+        self.n_tau, self.n_omega, self.n_walkers = n_tau, n_omega, params.n_walkers
+        self._h = handle
+        self._owner = owner
+        self.last_status = 0
+        return self
+
     def close(self):
-        if self._h:
+        if self._h and getattr(self, "_owner", None) is None:
             self.lib.sail_destroy(self._h)
-            self._h = ctypes.c_void_p()
+        self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:
@@ -289,6 +317,67 @@ class Sail:
         _check(self.lib.sail_delta_probe(self._h, n, _ptr(walker, _ip), _ptr(p, _ip), _ptr(s, _ip), _ptr(eps),
                                          _ptr(delta), _ptr(ok, _ip)))
         return delta, ok.astype(bool)
+
+
+class Batch:
+    """Many independent inversions annealed together (one persistent sweep launch per segment)."""
+
+    def __init__(self, problems, autotune: bool = True, stream=None):
+        """problems: list of (tau, F, sigma, omega, Params); all FP32, same block and resync periods."""
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Batch needs a CUDA device")
+        self.lib = load()
+        self._arrays = []
+        cp = (CProblem * len(problems))()
+        self.shapes = []
+        for k, (tau, F, sigma, omega, prm) in enumerate(problems):
+            arrs = [_f64(x) for x in (tau, F, sigma, omega)]
+            self._arrays.append(arrs)
+            cp[k].tau, cp[k].F, cp[k].sigma = (_ptr(a) for a in arrs[:3])
+            cp[k].n_tau = arrs[0].size
+            cp[k].omega = _ptr(arrs[3])
+            cp[k].n_omega = arrs[3].size
+            cp[k].params = prm.c()
+            self.shapes.append((arrs[0].size, arrs[3].size, prm))
+        nbytes = ctypes.c_size_t(0)
+        _check(self.lib.sail_batch_workspace_size(len(problems), cp, ctypes.byref(nbytes)))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        self._b = ctypes.c_void_p()
+        _check(self.lib.sail_batch_create(ctypes.byref(self._b), len(problems), cp, int(autotune),
+                                          ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                          ctypes.c_void_p(self.stream.cuda_stream)))
+        self.handles = []
+        for k, (nt, no, prm) in enumerate(self.shapes):
+            h = ctypes.c_void_p()
+            _check(self.lib.sail_batch_handle(self._b, k, ctypes.byref(h)))
+            self.handles.append(Sail._view(h, nt, no, prm, self))
+
+    def anneal(self, max_blocks: int = 1 << 30) -> int:
+        done = ctypes.c_int(0)
+        _check(self.lib.sail_batch_anneal(self._b, int(max_blocks), ctypes.byref(done)))
+        return done.value
+
+    def tuning(self):
+        ip = ctypes.c_int(0)
+        ns = ctypes.c_double(0.0)
+        nl = ctypes.c_longlong(0)
+        _check(self.lib.sail_batch_tuning(self._b, ctypes.byref(ip), ctypes.byref(ns), ctypes.byref(nl)))
+        return {"item_pairs": ip.value, "ns_per_move": ns.value, "sweep_launches": nl.value}
+
+    def close(self):
+        if self._b:
+            for h in self.handles:
+                h._h = ctypes.c_void_p()
+            self.lib.sail_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def read_bandwidth_probe(buf, reps: int, stream=None) -> None:

@@ -180,6 +180,8 @@ struct sail_ctx {
     long long launches, moves;
     unsigned long long acc_seen, pos_seen;
     int *status;             // device status word: nonzero after a timed-out device wait
+    bool converged;          // chi2 of the averaged spectrum reached target_chi2
+    double chi2_of_mean;
     // optional per-kernel timing: event pairs recorded around launches, read at block ends
     struct Timed { cudaEvent_t a, b; int kind; };
     std::vector<Timed> timed;
@@ -558,89 +560,143 @@ int average_to_host(sail_t h, double *mean, double *err, int *n_used, double *ch
 
 }  // namespace
 
+}  // extern "C"
+
+namespace {
+
+// ---- one block of the schedule (Sec. 3), in steps shared by single and batched annealing ----
+struct BlockPending {
+    int n_begin, block_end;
+    bool branched;
+    BlockCounters bc;
+    int dev_status;
+    double delta;
+    int zeros;
+};
+
+bool handle_active(const sail_ctx *h) { return h->sweeps_done < h->prm.n_sweeps && !h->converged; }
+
+int block_end_of(const sail_ctx *h) {
+    const int k = h->prm.sweeps_per_block;
+    return std::min((h->sweeps_done / k + 1) * k, h->prm.n_sweeps);
+}
+
+int next_resync(const sail_ctx *h, int n, int block_end) {
+    return std::min((n / h->prm.resync_every + 1) * h->prm.resync_every, block_end);
+}
+
+// residual recomputation after sweeps [n, next) ran
+int segment_done(sail_ctx *h, int n, int next) {
+    const sail_params &p = h->prm;
+    const int tk = timed_begin(h);
+    int l = 0;
+    const cudaError_t e = launch_resync(h->P, h->S, p.precision, 1, p.resync_kind, h->status, h->stream, &l);
+    timed_end(h, tk, kResync);
+    if (e != cudaSuccess) return cuda_fail(e, "resync launch");
+    h->launches += l;
+    h->moves += (long long)(next - n) * p.n_walkers * h->n_omega;
+    return SAIL_OK;
+}
+
+// branching and statistics at the block end; the read-backs are queued, not waited for
+int block_tail(sail_ctx *h, BlockPending &b) {
+    const sail_params &p = h->prm;
+    const int k = p.sweeps_per_block;
+    cudaStream_t st = h->stream;
+    h->sweeps_done = b.block_end;
+    b.delta = 0.0;
+    b.zeros = 0;
+    b.dev_status = 0;
+    b.branched = p.branching && p.n_walkers > 1 && (b.block_end % k) == 0;
+    if (b.branched) {
+        int l = 0;
+        const int tk = timed_begin(h);
+        const cudaError_t e = launch_branch(h->P, h->S, h->Bs, p.precision, b.block_end / k - 1, p.branch_fraction,
+                                            p.imprint_t, h->events, st, &l);
+        timed_end(h, tk, kBranch);
+        h->launches += l;
+        if (e != cudaSuccess) return cuda_fail(e, "branch launch");
+        h->events += 1;
+    }
+    const cudaError_t e = launch_block_stats(h->P, h->S, (BlockCounters *)(h->ws + h->L.counters), st);
+    h->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(e, "stats launch");
+    SAIL_CUDA(cudaMemcpyAsync(&b.bc, h->ws + h->L.counters, sizeof b.bc, cudaMemcpyDeviceToHost, st), "stats D2H");
+    SAIL_CUDA(cudaMemcpyAsync(&b.dev_status, h->status, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
+    if (b.branched) {
+        SAIL_CUDA(cudaMemcpyAsync(&b.delta, h->ws + h->L.delta, 8, cudaMemcpyDeviceToHost, st), "stats D2H");
+        SAIL_CUDA(cudaMemcpyAsync(&b.zeros, h->ws + h->L.n_pairs, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
+    }
+    return SAIL_OK;
+}
+
+// after the stream synchronisation: statistics, counters, target check
+int block_finish(sail_ctx *h, const BlockPending &b, sail_block_stats *out) {
+    const sail_params &p = h->prm;
+    timed_collect(h);
+    if (b.dev_status) return fail(SAIL_ETIMEOUT, "a device-side wait timed out (status %d)", b.dev_status);
+    if (out) {
+        sail_block_stats &s = *out;
+        std::memset(&s, 0, sizeof s);
+        const double proposed = (double)(b.block_end - b.n_begin) * p.n_walkers * h->n_omega;
+        s.block = h->blocks_done;
+        s.sweep_end = b.block_end;
+        s.T = h->T[b.block_end - 1];
+        s.chi2_min = b.bc.chi2_min;
+        s.chi2_mean = b.bc.chi2_sum / p.n_walkers;
+        s.acceptance = (double)(b.bc.acc - h->acc_seen) / proposed;
+        s.positivity_rejected = (double)(b.bc.pos - h->pos_seen) / proposed;
+        s.branch_delta = b.delta;
+        s.branch_zeros = b.zeros;
+    }
+    h->acc_seen = b.bc.acc;
+    h->pos_seen = b.bc.pos;
+    h->blocks_done += 1;
+    if (p.target_chi2 > 0) {
+        double c2 = 0;
+        const int rc = average_to_host(h, nullptr, nullptr, nullptr, &c2);
+        if (rc) return rc;
+        h->chi2_of_mean = c2;
+        h->converged = c2 <= p.target_chi2;
+    }
+    return SAIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) {
     if (!h) return fail(SAIL_EINVAL, "NULL handle");
     if (max_blocks < 0) return fail(SAIL_EINVAL, "max_blocks < 0");
     const sail_params &p = h->prm;
-    const int k = p.sweeps_per_block;
     int done = 0;
-    bool reached = false;
     cudaStream_t st = h->stream;
-    while (done < max_blocks && h->sweeps_done < p.n_sweeps && !reached) {
-        const int n_begin = h->sweeps_done;
-        const int block_end = std::min((n_begin / k + 1) * k, p.n_sweeps);
-        int n = n_begin;
-        while (n < block_end) {
-            const int next = std::min((n / p.resync_every + 1) * p.resync_every, block_end);
-            int tk = timed_begin(h);
-            cudaError_t e = p.precision == SAIL_PREC_FP64 ? launch_sweep_fp64(h->P, h->S, n, next, st)
-                                                          : launch_sweep_fp32(h->P, h->S, n, next, st);
+    while (done < max_blocks && handle_active(h)) {
+        BlockPending b{};
+        b.n_begin = h->sweeps_done;
+        b.block_end = block_end_of(h);
+        for (int n = b.n_begin; n < b.block_end;) {
+            const int next = next_resync(h, n, b.block_end);
+            const int tk = timed_begin(h);
+            const cudaError_t e = p.precision == SAIL_PREC_FP64 ? launch_sweep_fp64(h->P, h->S, n, next, st)
+                                                                : launch_sweep_fp32(h->P, h->S, n, next, st);
             timed_end(h, tk, kSweep);
+            h->launches += 1;
             if (e != cudaSuccess) return cuda_fail(e, "sweep launch");
-            tk = timed_begin(h);
-            int l = 0;
-            e = launch_resync(h->P, h->S, p.precision, 1, p.resync_kind, h->status, st, &l);
-            timed_end(h, tk, kResync);
-            if (e != cudaSuccess) return cuda_fail(e, "resync launch");
-            h->launches += 1 + l;
-            h->moves += (long long)(next - n) * p.n_walkers * h->n_omega;
+            const int rc = segment_done(h, n, next);
+            if (rc) return rc;
             n = next;
         }
-        h->sweeps_done = block_end;
-        double delta = 0.0;
-        int zeros = 0;
-        const bool branched = p.branching && p.n_walkers > 1 && (block_end % k) == 0;
-        if (branched) {
-            int l = 0;
-            const int tk = timed_begin(h);
-            cudaError_t e = launch_branch(h->P, h->S, h->Bs, p.precision, block_end / k - 1, p.branch_fraction,
-                                          p.imprint_t, h->events, st, &l);
-            timed_end(h, tk, kBranch);
-            h->launches += l;
-            if (e != cudaSuccess) return cuda_fail(e, "branch launch");
-            h->events += 1;
-        }
-        cudaError_t e = launch_block_stats(h->P, h->S, (BlockCounters *)(h->ws + h->L.counters), st);
-        h->launches += 1;
-        if (e != cudaSuccess) return cuda_fail(e, "stats launch");
-        BlockCounters bc{};
-        int dev_status = 0;
-        SAIL_CUDA(cudaMemcpyAsync(&bc, h->ws + h->L.counters, sizeof bc, cudaMemcpyDeviceToHost, st), "stats D2H");
-        SAIL_CUDA(cudaMemcpyAsync(&dev_status, h->status, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
-        if (branched) {
-            SAIL_CUDA(cudaMemcpyAsync(&delta, h->ws + h->L.delta, 8, cudaMemcpyDeviceToHost, st), "stats D2H");
-            SAIL_CUDA(cudaMemcpyAsync(&zeros, h->ws + h->L.n_pairs, 4, cudaMemcpyDeviceToHost, st), "stats D2H");
-        }
+        int rc = block_tail(h, b);
+        if (rc) return rc;
         SAIL_CUDA(cudaStreamSynchronize(st), "block sync");
-        timed_collect(h);
-        if (dev_status) return fail(SAIL_ETIMEOUT, "a device-side wait timed out (status %d)", dev_status);
-        if (stats) {
-            sail_block_stats &s = stats[done];
-            std::memset(&s, 0, sizeof s);
-            const double proposed = (double)(block_end - n_begin) * p.n_walkers * h->n_omega;
-            s.block = h->blocks_done;
-            s.sweep_end = block_end;
-            s.T = h->T[block_end - 1];
-            s.chi2_min = bc.chi2_min;
-            s.chi2_mean = bc.chi2_sum / p.n_walkers;
-            s.acceptance = (double)(bc.acc - h->acc_seen) / proposed;
-            s.positivity_rejected = (double)(bc.pos - h->pos_seen) / proposed;
-            s.branch_delta = delta;
-            s.branch_zeros = zeros;
-        }
-        h->acc_seen = bc.acc;
-        h->pos_seen = bc.pos;
-        h->blocks_done += 1;
+        rc = block_finish(h, b, stats ? &stats[done] : nullptr);
+        if (rc) return rc;
         done += 1;
-        if (p.target_chi2 > 0) {
-            double c2 = 0;
-            const int rc = average_to_host(h, nullptr, nullptr, nullptr, &c2);
-            if (rc) return rc;
-            reached = c2 <= p.target_chi2;
-        }
     }
     if (n_done) *n_done = done;
-    if (p.target_chi2 > 0 && !reached && h->sweeps_done >= p.n_sweeps) return SAIL_NOT_CONVERGED;
+    if (p.target_chi2 > 0 && !h->converged && h->sweeps_done >= p.n_sweeps) return SAIL_NOT_CONVERGED;
     return SAIL_OK;
 }
 
@@ -764,6 +820,294 @@ int sail_probe_smem_bandwidth(int reps, void *d_sink, void *stream, double *byte
 int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, void *stream) {
     if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return fail(SAIL_EINVAL, "bad arguments");
     SAIL_CUDA(launch_philox(n, d_ctr, seed, d_out, (cudaStream_t)stream), "philox launch");
+    return SAIL_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- batches
+namespace {
+
+constexpr int kTuneCandidates[3] = {16, 8, 4};   // walker pairs per queue item (= warps per block)
+
+}  // namespace
+
+struct sail_batch_ctx {
+    std::vector<sail_t> h;
+    cudaStream_t stream;
+    char *ws;
+    size_t ws_bytes;
+    BatchProblem *d_probs;
+    BatchItem *d_items;
+    int *d_counter;
+    size_t max_items;
+    size_t smem;               // shared memory of the batched sweep: the largest problem tables
+    int autotune;
+    int item_pairs;            // chosen mapping
+    int tune_next;             // next candidate to try (autotune), or 3 when done
+    double tune_ns[3];         // device ns per walker-move of each candidate
+    double last_ns;
+    long long sweep_launches, last_seg_moves;
+    cudaEvent_t ev0, ev1;
+    // tensor-core tile width tuning per n_tau_pad class: candidates, trial times
+    struct TcTune { int pad; int cand[8]; int n_cand; int next; double ns[8]; int chosen; };
+    std::vector<TcTune> tc;
+};
+
+namespace {
+
+size_t batch_header_bytes(int n, const sail_problem *probs) {
+    size_t items = 0;
+    for (int k = 0; k < n; ++k) items += (size_t)(probs[k].params.n_walkers + 1) / 2;
+    return align_up((size_t)n * sizeof(BatchProblem)) + align_up(items * sizeof(BatchItem)) + 256;
+}
+
+int check_batch(int n, const sail_problem *probs) {
+    if (n < 1 || !probs) return fail(SAIL_EINVAL, "a batch needs n >= 1 problems");
+    for (int k = 0; k < n; ++k) {
+        const sail_params &p = probs[k].params;
+        if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "problem %d: batches run FP32 precision", k);
+        if (p.sweeps_per_block != probs[0].params.sweeps_per_block || p.resync_every != probs[0].params.resync_every)
+            return fail(SAIL_EINVAL, "problem %d: sweeps_per_block and resync_every must match problem 0", k);
+        const int rc = check_params(probs[k].n_tau, probs[k].n_omega, &p);
+        if (rc) return rc;
+    }
+    return SAIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sail_batch_workspace_size(int n, const sail_problem *probs, size_t *bytes) {
+    if (!bytes) return fail(SAIL_EINVAL, "bytes is NULL");
+    int rc = check_batch(n, probs);
+    if (rc) return rc;
+    size_t total = batch_header_bytes(n, probs);
+    for (int k = 0; k < n; ++k) {
+        size_t b = 0;
+        rc = sail_workspace_size(probs[k].n_tau, probs[k].n_omega, &probs[k].params, &b);
+        if (rc) return rc;
+        total += align_up(b);
+    }
+    *bytes = total;
+    return SAIL_OK;
+}
+
+int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int autotune, void *d_workspace,
+                      size_t ws_bytes, void *stream) {
+    if (!out) return fail(SAIL_EINVAL, "out is NULL");
+    *out = nullptr;
+    size_t need = 0;
+    int rc = sail_batch_workspace_size(n, probs, &need);
+    if (rc) return rc;
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return fail(SAIL_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < need) return fail(SAIL_ENOMEM, "batch workspace has %zu bytes, needs %zu", ws_bytes, need);
+    sail_batch_ctx *b = new sail_batch_ctx();
+    b->stream = (cudaStream_t)stream;
+    b->ws = (char *)d_workspace;
+    b->ws_bytes = ws_bytes;
+    size_t off = 0;
+    b->d_probs = (BatchProblem *)(b->ws + off);
+    off += align_up((size_t)n * sizeof(BatchProblem));
+    b->d_items = (BatchItem *)(b->ws + off);
+    b->max_items = 0;
+    for (int k = 0; k < n; ++k) b->max_items += (size_t)(probs[k].params.n_walkers + 1) / 2;
+    off += align_up(b->max_items * sizeof(BatchItem));
+    b->d_counter = (int *)(b->ws + off);
+    off += 256;
+    b->smem = 0;
+    for (int k = 0; k < n; ++k) {
+        size_t sub = 0;
+        sail_workspace_size(probs[k].n_tau, probs[k].n_omega, &probs[k].params, &sub);
+        sail_t h = nullptr;
+        const sail_problem &q = probs[k];
+        rc = sail_create(&h, q.tau, q.F, q.sigma, q.n_tau, q.omega, q.n_omega, &q.params, b->ws + off, sub, stream);
+        if (rc) {
+            for (sail_t x : b->h) sail_destroy(x);
+            delete b;
+            return rc;
+        }
+        b->h.push_back(h);
+        b->smem = std::max(b->smem, sweep_fp32_table_bytes(h->P));
+        off += align_up(sub);
+    }
+    b->autotune = autotune;
+    b->item_pairs = kTuneCandidates[0];
+    b->tune_next = autotune ? 0 : 3;
+    b->last_ns = 0.0;
+    cudaEventCreate(&b->ev0);
+    cudaEventCreate(&b->ev1);
+    if (autotune) {
+        for (sail_t h : b->h) {
+            const int pad = h->pad;
+            bool seen = false;
+            for (auto &t : b->tc) seen = seen || t.pad == pad;
+            if (seen) continue;
+            sail_batch_ctx::TcTune t{};
+            t.pad = pad;
+            for (int nc = 128; nc >= 16 && t.n_cand < 3; nc -= 16)
+                if (pad % nc == 0) t.cand[t.n_cand++] = nc;
+            t.next = 0;
+            t.chosen = 0;
+            b->tc.push_back(t);
+        }
+    }
+    *out = b;
+    return SAIL_OK;
+}
+
+int sail_batch_destroy(sail_batch_t b) {
+    if (!b) return fail(SAIL_EINVAL, "NULL batch");
+    cudaStreamSynchronize(b->stream);
+    for (sail_t h : b->h) sail_destroy(h);
+    cudaEventDestroy(b->ev0);
+    cudaEventDestroy(b->ev1);
+    delete b;
+    return SAIL_OK;
+}
+
+int sail_batch_handle(sail_batch_t b, int k, sail_t *h) {
+    if (!b || !h || k < 0 || k >= (int)b->h.size()) return fail(SAIL_EINVAL, "bad batch index");
+    *h = b->h[k];
+    return SAIL_OK;
+}
+
+int sail_batch_tuning(sail_batch_t b, int *item_pairs, double *ns_per_move, long long *sweep_launches) {
+    if (!b) return fail(SAIL_EINVAL, "NULL batch");
+    if (item_pairs) *item_pairs = b->item_pairs;
+    if (ns_per_move) *ns_per_move = b->last_ns;
+    if (sweep_launches) *sweep_launches = b->sweep_launches;
+    return SAIL_OK;
+}
+
+int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
+    if (!b) return fail(SAIL_EINVAL, "NULL batch");
+    if (max_blocks < 0) return fail(SAIL_EINVAL, "max_blocks < 0");
+    const int N = (int)b->h.size();
+    cudaStream_t st = b->stream;
+    std::vector<BlockPending> pend(N);
+    std::vector<int> cur(N), active(N);
+    std::vector<BatchProblem> hp(N);
+    std::vector<BatchItem> items;
+    int done = 0;
+    while (done < max_blocks) {
+        bool any = false;
+        for (int k = 0; k < N; ++k) {
+            active[k] = handle_active(b->h[k]);
+            if (!active[k]) continue;
+            any = true;
+            pend[k] = BlockPending{};
+            pend[k].n_begin = b->h[k]->sweeps_done;
+            pend[k].block_end = block_end_of(b->h[k]);
+            cur[k] = pend[k].n_begin;
+        }
+        if (!any) break;
+        for (;;) {
+            // one segment: every problem with sweeps left in this block advances to its next resync
+            items.clear();
+            long long seg_moves = 0;
+            for (int k = 0; k < N; ++k) {
+                sail_ctx *h = b->h[k];
+                hp[k].P = h->P;
+                hp[k].S = h->S;
+                hp[k].n0 = hp[k].n1 = 0;
+                if (!active[k] || cur[k] >= pend[k].block_end) continue;
+                hp[k].n0 = cur[k];
+                hp[k].n1 = next_resync(h, cur[k], pend[k].block_end);
+                seg_moves += (long long)(hp[k].n1 - hp[k].n0) * h->prm.n_walkers * h->n_omega;
+                const int pairs = (h->prm.n_walkers + 1) / 2;
+                for (int lo = 0; lo < pairs; lo += b->item_pairs)
+                    items.push_back(BatchItem{k, lo, std::min(lo + b->item_pairs, pairs)});
+            }
+            if (items.empty()) break;
+            SAIL_CUDA(cudaMemcpyAsync(b->d_probs, hp.data(), (size_t)N * sizeof(BatchProblem), cudaMemcpyHostToDevice, st),
+                      "batch H2D");
+            SAIL_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem),
+                                      cudaMemcpyHostToDevice, st), "batch H2D");
+            cudaEventRecord(b->ev0, st);
+            cudaError_t e = launch_sweep_batch(b->d_probs, b->d_items, (int)items.size(), b->d_counter, b->smem,
+                                               b->item_pairs, st);
+            cudaEventRecord(b->ev1, st);
+            if (e != cudaSuccess) return cuda_fail(e, "batched sweep launch");
+            for (int k = 0; k < N; ++k) {
+                if (hp[k].n1 <= hp[k].n0) continue;
+                sail_ctx *h = b->h[k];
+                // tensor-core tile width: try the candidates of this n_tau_pad class in turn
+                cudaEvent_t t0 = nullptr, t1 = nullptr;
+                sail_batch_ctx::TcTune *tt = nullptr;
+                for (auto &t : b->tc)
+                    if (t.pad == h->pad) tt = &t;
+                if (tt && h->prm.resync_kind == 1) {
+                    if (tt->next < tt->n_cand) {
+                        h->P.tc_cols = tt->cand[tt->next];
+                        cudaEventCreate(&t0);
+                        cudaEventCreate(&t1);
+                        cudaEventRecord(t0, st);
+                    } else {
+                        h->P.tc_cols = tt->chosen;
+                    }
+                }
+                const int rc = segment_done(h, hp[k].n0, hp[k].n1);
+                if (t0) {
+                    cudaEventRecord(t1, st);
+                    cudaEventSynchronize(t1);
+                    float ms = 0.0f;
+                    cudaEventElapsedTime(&ms, t0, t1);
+                    const double per = ms * 1e6 / ((double)h->prm.n_walkers * h->n_omega * h->pad);
+                    tt->ns[tt->next] = per;
+                    tt->next += 1;
+                    if (tt->next == tt->n_cand) {
+                        int best = 0;
+                        for (int c = 1; c < tt->n_cand; ++c)
+                            if (tt->ns[c] < tt->ns[best]) best = c;
+                        tt->chosen = tt->cand[best];
+                    }
+                    cudaEventDestroy(t0);
+                    cudaEventDestroy(t1);
+                }
+                if (rc) return rc;
+                cur[k] = hp[k].n1;
+            }
+            b->sweep_launches += 1;
+            b->last_seg_moves = seg_moves;
+            // walker-to-block mapping: time this launch, try the next candidate, keep the fastest
+            if (b->tune_next < 3) {
+                SAIL_CUDA(cudaEventSynchronize(b->ev1), "batch timing");
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+                b->last_ns = seg_moves > 0 ? ms * 1e6 / (double)seg_moves : 0.0;
+                b->tune_ns[b->tune_next] = b->last_ns;
+                b->tune_next += 1;
+                if (b->tune_next < 3) {
+                    b->item_pairs = kTuneCandidates[b->tune_next];
+                } else {
+                    int best = 0;
+                    for (int c = 1; c < 3; ++c)
+                        if (b->tune_ns[c] < b->tune_ns[best]) best = c;
+                    b->item_pairs = kTuneCandidates[best];
+                }
+            }
+        }
+        for (int k = 0; k < N; ++k) {
+            if (!active[k]) continue;
+            const int rc = block_tail(b->h[k], pend[k]);
+            if (rc) return rc;
+        }
+        SAIL_CUDA(cudaStreamSynchronize(st), "batch block sync");
+        if (b->tune_next >= 3 && b->last_seg_moves > 0) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess)
+                b->last_ns = ms * 1e6 / (double)b->last_seg_moves;
+        }
+        for (int k = 0; k < N; ++k) {
+            if (!active[k]) continue;
+            const int rc = block_finish(b->h[k], pend[k], nullptr);
+            if (rc) return rc;
+        }
+        done += 1;
+    }
+    if (n_done) *n_done = done;
     return SAIL_OK;
 }
 

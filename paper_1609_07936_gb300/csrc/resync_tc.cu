@@ -261,11 +261,14 @@ cudaError_t launch_nc(const DevProblem &P, const DevState &S, int *status, cudaS
 
 }  // namespace
 
-// Columns per block: the widest multiple of 16 that divides n_tau_pad and is <= 128.
+// Columns per block: P.tc_cols if set (a multiple of 16 dividing n_tau_pad, <= 128), else
+// the widest such width.  Every width gives the same result bit for bit: each column's sum
+// runs over the same tiles in the same order.
 cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st) {
     const int pad = P.n_tau_pad;
     for (int nc = 128; nc >= 16; nc -= 16) {
         if (pad % nc) continue;
+        if (P.tc_cols > 0 && nc != P.tc_cols) continue;
         switch (nc) {
             case 128: return launch_nc<128>(P, S, status, st);
             case 112: return launch_nc<112>(P, S, status, st);

@@ -44,6 +44,7 @@ struct DevProblem {
     const float *Khi32;    // [n_tau_pad][n_omega_pad] Khat cut to TF32 (K-major, tensor-core resync)
     const float *Klo32;    // [n_tau_pad][n_omega_pad] Khat - Khi
     int n_omega_pad;       // n_omega rounded up to 32
+    int tc_cols;           // tau columns per tensor-core resync block (0: the widest that fits)
     const double *Tsweep;
 };
 
@@ -110,6 +111,19 @@ cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, 
 cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st);
 // Shared memory the FP32 sweep needs for its kernel tables (must fit one block).
 size_t sweep_fp32_table_bytes(const DevProblem &P);
+
+// One problem of a batched sweep launch: sweeps [n0, n1) (n0 == n1: nothing this launch).
+struct BatchProblem {
+    DevProblem P;
+    DevState S;
+    int n0, n1;
+};
+struct BatchItem {      // pairs [pair_lo, pair_hi) of problem prob, one pair per warp
+    int prob, pair_lo, pair_hi;
+};
+// Persistent FP32 sweep over many problems: blocks of `warps` warps take items from the queue.
+cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                               size_t smem, int warps, cudaStream_t st);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes);
 

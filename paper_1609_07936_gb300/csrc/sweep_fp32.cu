@@ -65,29 +65,156 @@ struct SweepGeom {
     int stage_b;          // spectra staged in shared memory
 };
 
+// Loads a problem's kernel factor tables, beta and the reciprocal gaps into shared memory.
+__device__ void load_tables(const DevProblem &P, float *sm) {
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    float *sQhi = sm;
+    float *sQlo = sQhi + (size_t)NH * PAD;
+    float *sBeta = sQlo + (size_t)32 * PAD;
+    float *sRgap = sBeta + NO;
+    const float4 *g4 = reinterpret_cast<const float4 *>(P.Qhi32);
+    float4 *s4 = reinterpret_cast<float4 *>(sQhi);
+    for (int q = threadIdx.x; q < NH * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+    g4 = reinterpret_cast<const float4 *>(P.Qlo32);
+    s4 = reinterpret_cast<float4 *>(sQlo);
+    for (int q = threadIdx.x; q < 32 * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+    for (int q = threadIdx.x; q < NO; q += blockDim.x) {
+        sBeta[q] = P.beta32[q];
+        sRgap[q] = P.rgap32[q];
+    }
+}
+
+// Sweeps [n0, n1) for the two walkers 2 pair, 2 pair + 1 of one problem on one warp (half-warp
+// per walker).  sm holds the problem's tables; b_stage, if not null, the staged spectra of
+// walkers walker_lo.. .
+template <int C2>
+__device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1, int pair, const float *sm,
+                         float *b_stage, int walker_lo) {
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    const float *sQhi = sm;
+    const float *sQlo = sQhi + (size_t)NH * PAD;
+    const float *sBeta = sQlo + (size_t)32 * PAD;
+    const float *sRgap = sBeta + NO;
+    const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+    const uint2 key = philox_key(P.seed);
+    const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
+
+    const int w = 2 * pair + half;
+    const bool active = w < P.n_walkers;
+    const int wr = active ? w : 2 * pair;             // a valid walker to read from
+    float *b = b_stage ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+
+    float R[2 * C2], M[2 * C2];
+#pragma unroll
+    for (int c = 0; c < C2; ++c) {
+        const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + 32 * c + 2 * hl);
+        const float2 f2 = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
+        R[2 * c] = r2.x;
+        R[2 * c + 1] = r2.y;
+        M[2 * c] = f2.x - r2.x;
+        M[2 * c + 1] = f2.y - r2.y;
+    }
+    float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
+    double chi2 = S.chi2[wr];
+    int accp = S.acc_prev[wr];
+    unsigned long long nacc = 0, npos = 0;
+
+    for (int n = n0; n < n1; ++n) {
+        const float invT = (float)(1.0 / P.Tsweep[n]);
+        const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
+        int acc = 0, pos = 0;
+        float dchi = 0.0f;
+        uint4 batch = make_uint4(0u, 0u, 0u, 0u);
+        for (int mv = 0; mv < NO; ++mv) {
+            const int src = mv & 15;
+            if (src == 0)
+                batch = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
+            const uint32_t w0 = __shfl_sync(kFull, batch.x, src, 16);
+            const uint32_t w1 = __shfl_sync(kFull, batch.y, src, 16);
+            const uint32_t w2 = __shfl_sync(kFull, batch.z, src, 16);
+            const uint32_t w3 = __shfl_sync(kFull, batch.w, src, 16);
+            int p, s;
+            move_bins(w0, w1, NO, p, s);
+            const float eps = yd * (2.0f * unit32(w2) - 1.0f);
+            const float u = unit32(w3);
+            const float r = 1.0f - eps;
+            float dp, ds;
+            deltas(eps, p, s, sBeta, sRgap, dp, ds);
+            const float ap = fmaf(r, ghi * b[p], dp);
+            const float as = fmaf(r, ghi * b[s], ds);
+            const bool ok = active && ap >= 0.0f && as >= 0.0f;
+            pos += (active && !ok);
+            if (__any_sync(kFull, ok)) {
+                const float *qhp = sQhi + (p >> 5) * PAD + 2 * hl;
+                const float *qlp = sQlo + (p & 31) * PAD + 2 * hl;
+                const float *qhs = sQhi + (s >> 5) * PAD + 2 * hl;
+                const float *qls = sQlo + (s & 31) * PAD + 2 * hl;
+                float d[2 * C2];
+                float part = 0.0f;
+#pragma unroll
+                for (int c = 0; c < C2; ++c) {
+                    const float2 a1 = *reinterpret_cast<const float2 *>(qhp + 32 * c);
+                    const float2 a2 = *reinterpret_cast<const float2 *>(qlp + 32 * c);
+                    const float2 b1 = *reinterpret_cast<const float2 *>(qhs + 32 * c);
+                    const float2 b2 = *reinterpret_cast<const float2 *>(qls + 32 * c);
+                    d[2 * c] = fmaf(-ds, b1.x * b2.x, fmaf(-dp, a1.x * a2.x, eps * M[2 * c]));
+                    d[2 * c + 1] = fmaf(-ds, b1.y * b2.y, fmaf(-dp, a1.y * a2.y, eps * M[2 * c + 1]));
+                    part = fmaf(d[2 * c], fmaf(2.0f, R[2 * c], d[2 * c]), part);
+                    part = fmaf(d[2 * c + 1], fmaf(2.0f, R[2 * c + 1], d[2 * c + 1]), part);
+                }
+                const float D = half_sum(part);
+                if (ok && (D <= 0.0f || u < __expf(-D * invT))) {
+#pragma unroll
+                    for (int c = 0; c < 2 * C2; ++c) {
+                        R[c] += d[c];
+                        M[c] -= d[c];
+                    }
+                    pair_scale(ghi, glo, r);
+                    if (hl == 0) {
+                        const float inv_g = 1.0f / ghi;
+                        b[p] = ap * inv_g;
+                        b[s] = as * inv_g;
+                    }
+                    dchi += D;
+                    ++acc;
+                }
+            }
+            __syncwarp();
+        }
+        chi2 += (double)dchi;
+        accp = acc;
+        nacc += acc;
+        npos += pos;
+        if (active && S.acc_trace && hl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+    }
+    if (!active) return;
+    // fold the common scale into the spectrum and write the walker back
+    float *bg = S.b32 + (size_t)w * NO;
+    for (int j = hl; j < NO; j += 16) {
+        const float v = b[j];
+        bg[j] = fmaf(glo, v, ghi * v);
+    }
+#pragma unroll
+    for (int c = 0; c < C2; ++c)
+        *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = make_float2(R[2 * c], R[2 * c + 1]);
+    if (hl == 0) {
+        S.g2[2 * w] = 1.0f;
+        S.g2[2 * w + 1] = 0.0f;
+        S.chi2[w] = chi2;
+        S.acc_prev[w] = accp;
+        S.n_acc[w] += nacc;
+        S.n_pos[w] += npos;
+    }
+}
+
 template <int C2>
 __global__ void __launch_bounds__(kThreads) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom G) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
-    float *sQhi = sm;
-    float *sQlo = sQhi + (size_t)NH * PAD;
-    float *sBeta = sQlo + (size_t)32 * PAD;
-    float *sRgap = sBeta + NO;
-    float *sB = sRgap + NO;      // staged spectra [2 * pairs_per_cta][NO] when G.stage_b
-    {
-        const float4 *g4 = reinterpret_cast<const float4 *>(P.Qhi32);
-        float4 *s4 = reinterpret_cast<float4 *>(sQhi);
-        for (int q = threadIdx.x; q < NH * PAD / 4; q += blockDim.x) s4[q] = g4[q];
-        g4 = reinterpret_cast<const float4 *>(P.Qlo32);
-        s4 = reinterpret_cast<float4 *>(sQlo);
-        for (int q = threadIdx.x; q < 32 * PAD / 4; q += blockDim.x) s4[q] = g4[q];
-        for (int q = threadIdx.x; q < NO; q += blockDim.x) {
-            sBeta[q] = P.beta32[q];
-            sRgap[q] = P.rgap32[q];
-        }
-    }
+    float *sB = sm + (size_t)(NH + 32) * PAD + 2 * NO;   // staged spectra [2 * pairs_per_cta][NO]
+    load_tables(P, sm);
     const int pair_lo = blockIdx.x * G.pairs_per_cta;
     const int pair_hi = min(pair_lo + G.pairs_per_cta, G.pairs_total);
     const int walker_lo = 2 * pair_lo;
@@ -98,119 +225,59 @@ __global__ void __launch_bounds__(kThreads) sweep_fp32_kernel(DevProblem P, DevS
         for (size_t q = threadIdx.x; q < n; q += blockDim.x) sB[q] = src[q];
     }
     __syncthreads();
-
-    const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4, warp = threadIdx.x >> 5;
-    const uint2 key = philox_key(P.seed);
-    const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
-
+    const int warp = threadIdx.x >> 5;
     for (int round = 0; round < G.rounds; ++round) {
         const int pair = pair_lo + round * G.warps + warp;
         if (pair >= pair_hi) break;                       // uniform across the warp
-        const int w = 2 * pair + half;
-        const bool active = w < P.n_walkers;
-        const int wr = active ? w : 2 * pair;             // a valid walker to read from
-        float *b = G.stage_b ? sB + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+        run_pair<C2>(P, S, n0, n1, pair, sm, G.stage_b ? sB : nullptr, walker_lo);
+    }
+}
 
-        float R[2 * C2], M[2 * C2];
-#pragma unroll
-        for (int c = 0; c < C2; ++c) {
-            const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + 32 * c + 2 * hl);
-            const float2 f2 = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
-            R[2 * c] = r2.x;
-            R[2 * c + 1] = r2.y;
-            M[2 * c] = f2.x - r2.x;
-            M[2 * c + 1] = f2.y - r2.y;
+// Many inversions in one persistent launch: blocks take (problem, pair range) items from a
+// queue, load the item's problem tables when the problem changes, and run one pair per warp.
+// The per-walker arithmetic is that of sweep_fp32_kernel, so a walker's trajectory does not
+// depend on which block, or which other problems, share the launch.
+__global__ void __launch_bounds__(kThreads) sweep_batch_kernel(const BatchProblem *probs, const BatchItem *items,
+                                                               int n_items, int *counter) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    __shared__ int s_item, s_loaded;
+    if (threadIdx.x == 0) s_loaded = -1;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();                       // the previous item is finished with the tables
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const BatchItem I = items[it];
+        const BatchProblem &BP = probs[I.prob];
+        if (I.prob != s_loaded) {
+            load_tables(BP.P, sm);
+            __syncthreads();
+            if (threadIdx.x == 0) s_loaded = I.prob;
         }
-        float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
-        double chi2 = S.chi2[wr];
-        int accp = S.acc_prev[wr];
-        unsigned long long nacc = 0, npos = 0;
-
-        for (int n = n0; n < n1; ++n) {
-            const float invT = (float)(1.0 / P.Tsweep[n]);
-            const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
-            int acc = 0, pos = 0;
-            float dchi = 0.0f;
-            uint4 batch = make_uint4(0u, 0u, 0u, 0u);
-            for (int mv = 0; mv < NO; ++mv) {
-                const int src = mv & 15;
-                if (src == 0)
-                    batch = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
-                const uint32_t w0 = __shfl_sync(kFull, batch.x, src, 16);
-                const uint32_t w1 = __shfl_sync(kFull, batch.y, src, 16);
-                const uint32_t w2 = __shfl_sync(kFull, batch.z, src, 16);
-                const uint32_t w3 = __shfl_sync(kFull, batch.w, src, 16);
-                int p, s;
-                move_bins(w0, w1, NO, p, s);
-                const float eps = yd * (2.0f * unit32(w2) - 1.0f);
-                const float u = unit32(w3);
-                const float r = 1.0f - eps;
-                float dp, ds;
-                deltas(eps, p, s, sBeta, sRgap, dp, ds);
-                const float ap = fmaf(r, ghi * b[p], dp);
-                const float as = fmaf(r, ghi * b[s], ds);
-                const bool ok = active && ap >= 0.0f && as >= 0.0f;
-                pos += (active && !ok);
-                if (__any_sync(kFull, ok)) {
-                    const float *qhp = sQhi + (p >> 5) * PAD + 2 * hl;
-                    const float *qlp = sQlo + (p & 31) * PAD + 2 * hl;
-                    const float *qhs = sQhi + (s >> 5) * PAD + 2 * hl;
-                    const float *qls = sQlo + (s & 31) * PAD + 2 * hl;
-                    float d[2 * C2];
-                    float part = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < C2; ++c) {
-                        const float2 a1 = *reinterpret_cast<const float2 *>(qhp + 32 * c);
-                        const float2 a2 = *reinterpret_cast<const float2 *>(qlp + 32 * c);
-                        const float2 b1 = *reinterpret_cast<const float2 *>(qhs + 32 * c);
-                        const float2 b2 = *reinterpret_cast<const float2 *>(qls + 32 * c);
-                        d[2 * c] = fmaf(-ds, b1.x * b2.x, fmaf(-dp, a1.x * a2.x, eps * M[2 * c]));
-                        d[2 * c + 1] = fmaf(-ds, b1.y * b2.y, fmaf(-dp, a1.y * a2.y, eps * M[2 * c + 1]));
-                        part = fmaf(d[2 * c], fmaf(2.0f, R[2 * c], d[2 * c]), part);
-                        part = fmaf(d[2 * c + 1], fmaf(2.0f, R[2 * c + 1], d[2 * c + 1]), part);
-                    }
-                    const float D = half_sum(part);
-                    if (ok && (D <= 0.0f || u < __expf(-D * invT))) {
-#pragma unroll
-                        for (int c = 0; c < 2 * C2; ++c) {
-                            R[c] += d[c];
-                            M[c] -= d[c];
-                        }
-                        pair_scale(ghi, glo, r);
-                        if (hl == 0) {
-                            const float inv_g = 1.0f / ghi;
-                            b[p] = ap * inv_g;
-                            b[s] = as * inv_g;
-                        }
-                        dchi += D;
-                        ++acc;
-                    }
-                }
-                __syncwarp();
-            }
-            chi2 += (double)dchi;
-            accp = acc;
-            nacc += acc;
-            npos += pos;
-            if (active && S.acc_trace && hl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
-        }
-        if (!active) continue;
-        // fold the common scale into the spectrum and write the walker back
-        float *bg = S.b32 + (size_t)w * NO;
-        for (int j = hl; j < NO; j += 16) {
-            const float v = b[j];
-            bg[j] = fmaf(glo, v, ghi * v);
-        }
-#pragma unroll
-        for (int c = 0; c < C2; ++c)
-            *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = make_float2(R[2 * c], R[2 * c + 1]);
-        if (hl == 0) {
-            S.g2[2 * w] = 1.0f;
-            S.g2[2 * w + 1] = 0.0f;
-            S.chi2[w] = chi2;
-            S.acc_prev[w] = accp;
-            S.n_acc[w] += nacc;
-            S.n_pos[w] += npos;
+        __syncthreads();
+        const int pair = I.pair_lo + warp;
+        if (pair >= I.pair_hi || BP.n0 >= BP.n1) continue;
+        switch (BP.P.n_tau_pad / 32) {
+            case 1: run_pair<1>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 2: run_pair<2>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 3: run_pair<3>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 4: run_pair<4>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 5: run_pair<5>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 6: run_pair<6>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 7: run_pair<7>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 8: run_pair<8>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 9: run_pair<9>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 10: run_pair<10>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 11: run_pair<11>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 12: run_pair<12>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 13: run_pair<13>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 14: run_pair<14>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 15: run_pair<15>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            case 16: run_pair<16>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
+            default: break;
         }
     }
 }
@@ -347,6 +414,26 @@ cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *byt
 }
 
 size_t sweep_fp32_table_bytes(const DevProblem &P) { return table_bytes(P); }
+
+cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                               size_t smem, int warps, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    // one block per SM, or two when two blocks' tables fit in one SM's shared memory
+    int per_sm = 1;
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (2 * (smem + 2048) <= (size_t)smem_sm && warps <= 8) per_sm = 2;
+    const int blocks = n_items < sms * per_sm ? n_items : sms * per_sm;
+    sweep_batch_kernel<<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st) {
     int dev = 0, sms = 0;
