@@ -266,6 +266,32 @@ int sail_batch_tuning(sail_batch_t b, int *item_pairs, double *ns_per_move, long
 
 int sail_batch_destroy(sail_batch_t b);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of inversion requests (no counterpart in the paper, which inverts one
+ * data set at a time; the requests are the independent k-vectors of Sec. 2.1).  Requests queue
+ * in submission order; sail_server_step admits the head of the queue while a slot is free, the
+ * resident walkers stay within max_walkers and the request's workspace fits a free region of
+ * d_workspace (first fit: the buffer size is the HBM admission cap), runs one block for every
+ * resident problem through the batched sweep, and retires problems that reached their
+ * target_chi2 (checked each block on the averaged spectrum) or their last sweep, keeping the
+ * averaged spectrum on the host.  A request's result does not depend on which others share
+ * the device (see the batch above). */
+typedef struct sail_server_ctx *sail_server_t;
+
+int sail_server_create(sail_server_t *out, int max_resident, long long max_walkers, int sweeps_per_block,
+                       int resync_every, void *d_workspace, size_t ws_bytes, void *stream);
+/* Copies the request (host arrays and parameters; FP32, the server's periods); *id for its result. */
+int sail_server_submit(sail_server_t s, const sail_problem *req, int *id);
+/* Admission, one block, retirement.  completed[max_completed] receives the ids retired in this
+ * step (*n_completed of them); *n_active / *n_queued: resident and waiting requests after it. */
+int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
+                     int *n_queued);
+/* Result of a completed request: averaged spectrum and its standard error (host arrays of
+ * n_omega, may be NULL), chi2 of the average, whether the target was reached, sweeps run. */
+int sail_server_result(sail_server_t s, int id, double *S_mean, double *S_err, double *chi2_of_mean, int *converged,
+                       int *sweeps_done);
+int sail_server_destroy(sail_server_t s);
+
 /* Frees the host side of the handle; the workspace stays the caller's. */
 int sail_destroy(sail_t h);
 

@@ -5,4 +5,4 @@ include/sail.h); this package is its ctypes binding.  There is no CPU path:
 using the binding without a CUDA device or without the built library raises.
 """
 from ._capi import (PREC_FP32, PREC_FP64, RESYNC_FP32, RESYNC_TENSOR, Batch, Params, Sail,  # noqa: F401
-                    SailError, load, philox, workspace_size)
+                    SailError, Server, load, philox, workspace_size)

@@ -36,7 +36,8 @@ EXPORTS = [
     "sail_get_info", "sail_get_state", "sail_set_state", "sail_get_trace", "sail_delta_probe",
     "sail_philox", "sail_probe_read_bandwidth", "sail_probe_smem_bandwidth", "sail_residue_noalloc",
     "sail_batch_workspace_size", "sail_batch_create", "sail_batch_anneal", "sail_batch_handle",
-    "sail_batch_tuning", "sail_batch_destroy", "sail_destroy", "sail_last_error",
+    "sail_batch_tuning", "sail_batch_destroy", "sail_server_create", "sail_server_submit", "sail_server_step",
+    "sail_server_result", "sail_server_destroy", "sail_destroy", "sail_last_error",
 ]
 
 
@@ -128,6 +129,12 @@ def load(path: str = LIB_PATH):
     L.sail_batch_handle.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
     L.sail_batch_tuning.argtypes = [vp, _ip, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.sail_batch_destroy.argtypes = [vp]
+    L.sail_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                     vp, ctypes.c_size_t, vp]
+    L.sail_server_submit.argtypes = [vp, ctypes.POINTER(CProblem), _ip]
+    L.sail_server_step.argtypes = [vp, _ip, ctypes.c_int, _ip, _ip, _ip]
+    L.sail_server_result.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp, _ip, _ip]
+    L.sail_server_destroy.argtypes = [vp]
     L.sail_destroy.argtypes = [vp]
     L.sail_last_error.argtypes = []
     L.sail_last_error.restype = ctypes.c_char_p
@@ -372,6 +379,67 @@ class Batch:
                 h._h = ctypes.c_void_p()
             self.lib.sail_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous batching of inversion requests on one device buffer of workspace_bytes."""
+
+    def __init__(self, workspace_bytes: int, max_resident: int = 512, max_walkers: int = 1 << 21,
+                 sweeps_per_block: int = 100, resync_every: int = 50, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("Server needs a CUDA device")
+        self.lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(int(workspace_bytes), dtype=torch.uint8, device="cuda")
+        self._s = ctypes.c_void_p()
+        _check(self.lib.sail_server_create(ctypes.byref(self._s), int(max_resident), int(max_walkers),
+                                           int(sweeps_per_block), int(resync_every),
+                                           ctypes.c_void_p(self.workspace.data_ptr()), int(workspace_bytes),
+                                           ctypes.c_void_p(self.stream.cuda_stream)))
+        self.n_omega = {}
+        self.max_resident = max_resident
+
+    def submit(self, tau, F, sigma, omega, params: "Params") -> int:
+        arrs = [_f64(x) for x in (tau, F, sigma, omega)]
+        cp = CProblem()
+        cp.tau, cp.F, cp.sigma = (_ptr(a) for a in arrs[:3])
+        cp.n_tau = arrs[0].size
+        cp.omega = _ptr(arrs[3])
+        cp.n_omega = arrs[3].size
+        cp.params = params.c()
+        rid = ctypes.c_int(-1)
+        _check(self.lib.sail_server_submit(self._s, ctypes.byref(cp), ctypes.byref(rid)))
+        self.n_omega[rid.value] = arrs[3].size
+        return rid.value
+
+    def step(self):
+        """One admission / block / retirement round: (completed ids, active, queued)."""
+        buf = (ctypes.c_int * self.max_resident)()
+        nc, na, nq = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.sail_server_step(self._s, buf, self.max_resident, ctypes.byref(nc), ctypes.byref(na),
+                                         ctypes.byref(nq)))
+        return [buf[i] for i in range(min(nc.value, self.max_resident))], na.value, nq.value
+
+    def result(self, rid: int):
+        n = self.n_omega[rid]
+        mean, err = np.zeros(n), np.zeros(n)
+        c2, conv, sw = ctypes.c_double(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.sail_server_result(self._s, int(rid), _ptr(mean), _ptr(err), ctypes.byref(c2),
+                                           ctypes.byref(conv), ctypes.byref(sw)))
+        return {"mean": mean, "err": err, "chi2_of_mean": c2.value, "converged": bool(conv.value),
+                "sweeps": sw.value}
+
+    def close(self):
+        if self._s:
+            self.lib.sail_server_destroy(self._s)
+            self._s = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -981,9 +982,12 @@ int sail_batch_tuning(sail_batch_t b, int *item_pairs, double *ns_per_move, long
     return SAIL_OK;
 }
 
-int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
-    if (!b) return fail(SAIL_EINVAL, "NULL batch");
-    if (max_blocks < 0) return fail(SAIL_EINVAL, "max_blocks < 0");
+}  // extern "C"
+
+namespace {
+
+// Runs up to max_blocks blocks for every live problem of b (empty slots are skipped).
+int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
     const int N = (int)b->h.size();
     cudaStream_t st = b->stream;
     std::vector<BlockPending> pend(N);
@@ -994,7 +998,7 @@ int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
     while (done < max_blocks) {
         bool any = false;
         for (int k = 0; k < N; ++k) {
-            active[k] = handle_active(b->h[k]);
+            active[k] = b->h[k] != nullptr && handle_active(b->h[k]);
             if (!active[k]) continue;
             any = true;
             pend[k] = BlockPending{};
@@ -1009,10 +1013,10 @@ int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
             long long seg_moves = 0;
             for (int k = 0; k < N; ++k) {
                 sail_ctx *h = b->h[k];
-                hp[k].P = h->P;
-                hp[k].S = h->S;
                 hp[k].n0 = hp[k].n1 = 0;
                 if (!active[k] || cur[k] >= pend[k].block_end) continue;
+                hp[k].P = h->P;
+                hp[k].S = h->S;
                 hp[k].n0 = cur[k];
                 hp[k].n1 = next_resync(h, cur[k], pend[k].block_end);
                 seg_moves += (long long)(hp[k].n1 - hp[k].n0) * h->prm.n_walkers * h->n_omega;
@@ -1108,6 +1112,243 @@ int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
         done += 1;
     }
     if (n_done) *n_done = done;
+    return SAIL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
+    if (!b) return fail(SAIL_EINVAL, "NULL batch");
+    if (max_blocks < 0) return fail(SAIL_EINVAL, "max_blocks < 0");
+    return batch_run_blocks(b, max_blocks, n_done);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- serving
+// Continuous batching: requests wait in a FIFO; at every step the head of the queue is
+// admitted while its workspace fits a free region of the server's device buffer (first fit;
+// the buffer size is the admission cap) and a slot is free, one block runs for every resident
+// problem through the batched sweep, and problems that reached their target chi2 or the end
+// of their schedule leave, their averaged spectrum kept on the host.
+struct sail_server_ctx {
+    sail_batch_ctx batch;              // slots: batch.h[k] == nullptr when free
+    std::vector<size_t> slot_off, slot_size;
+    std::vector<int> slot_id;
+    struct Region { size_t off, size; };
+    std::vector<Region> free_regions;  // sorted by offset, coalesced
+    size_t data_begin;
+    int sweeps_per_block, resync_every;
+    long long max_pairs, resident_pairs;
+    struct Request {
+        int id;
+        std::vector<double> tau, F, sigma, omega;
+        sail_params params;
+        size_t bytes;
+    };
+    std::deque<Request> queue;
+    struct Result {
+        bool done;
+        int converged, sweeps;
+        double chi2_mean;
+        int n_used;
+        std::vector<double> mean, err;
+        int n_omega;
+    };
+    std::vector<Result> results;
+};
+
+namespace {
+
+bool region_take(sail_server_ctx *s, size_t bytes, size_t *off) {
+    for (size_t r = 0; r < s->free_regions.size(); ++r) {
+        auto &R = s->free_regions[r];
+        if (R.size >= bytes) {
+            *off = R.off;
+            R.off += bytes;
+            R.size -= bytes;
+            if (R.size == 0) s->free_regions.erase(s->free_regions.begin() + (long)r);
+            return true;
+        }
+    }
+    return false;
+}
+
+void region_give(sail_server_ctx *s, size_t off, size_t bytes) {
+    auto &F = s->free_regions;
+    size_t r = 0;
+    while (r < F.size() && F[r].off < off) ++r;
+    F.insert(F.begin() + (long)r, sail_server_ctx::Region{off, bytes});
+    // coalesce with the neighbours
+    if (r + 1 < F.size() && F[r].off + F[r].size == F[r + 1].off) {
+        F[r].size += F[r + 1].size;
+        F.erase(F.begin() + (long)r + 1);
+    }
+    if (r > 0 && F[r - 1].off + F[r - 1].size == F[r].off) {
+        F[r - 1].size += F[r].size;
+        F.erase(F.begin() + (long)r);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sail_server_create(sail_server_t *out, int max_resident, long long max_walkers, int sweeps_per_block,
+                       int resync_every, void *d_workspace, size_t ws_bytes, void *stream) {
+    if (!out) return fail(SAIL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_resident < 1 || max_walkers < 2 || sweeps_per_block < 1 || resync_every < 1)
+        return fail(SAIL_EINVAL, "server needs max_resident >= 1, max_walkers >= 2 and positive periods");
+    if (!d_workspace || ((uintptr_t)d_workspace & 255)) return fail(SAIL_EINVAL, "workspace must be 256-byte aligned");
+    const long long max_pairs = max_walkers / 2 + max_resident;
+    const size_t header = align_up((size_t)max_resident * sizeof(BatchProblem)) +
+                          align_up((size_t)max_pairs * sizeof(BatchItem)) + 256;
+    if (ws_bytes <= header) return fail(SAIL_ENOMEM, "server workspace smaller than its %zu-byte header", header);
+    sail_server_ctx *s = new sail_server_ctx();
+    sail_batch_ctx &b = s->batch;
+    b.stream = (cudaStream_t)stream;
+    b.ws = (char *)d_workspace;
+    b.ws_bytes = ws_bytes;
+    b.d_probs = (BatchProblem *)b.ws;
+    b.d_items = (BatchItem *)(b.ws + align_up((size_t)max_resident * sizeof(BatchProblem)));
+    b.d_counter = (int *)(b.ws + header - 256);
+    b.max_items = (size_t)max_pairs;
+    b.h.assign(max_resident, nullptr);
+    b.autotune = 1;
+    b.item_pairs = kTuneCandidates[0];
+    b.tune_next = 0;
+    cudaEventCreate(&b.ev0);
+    cudaEventCreate(&b.ev1);
+    s->slot_off.assign(max_resident, 0);
+    s->slot_size.assign(max_resident, 0);
+    s->slot_id.assign(max_resident, -1);
+    s->data_begin = header;
+    s->free_regions.push_back(sail_server_ctx::Region{header, ws_bytes - header});
+    s->sweeps_per_block = sweeps_per_block;
+    s->resync_every = resync_every;
+    s->max_pairs = max_walkers / 2;
+    *out = s;
+    return SAIL_OK;
+}
+
+int sail_server_submit(sail_server_t s, const sail_problem *req, int *id) {
+    if (!s || !req || !id) return fail(SAIL_EINVAL, "NULL argument");
+    const sail_params &p = req->params;
+    if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "served inversions run FP32 precision");
+    if (p.sweeps_per_block != s->sweeps_per_block || p.resync_every != s->resync_every)
+        return fail(SAIL_EINVAL, "request periods differ from the server's");
+    size_t bytes = 0;
+    int rc = sail_workspace_size(req->n_tau, req->n_omega, &p, &bytes);
+    if (rc) return rc;
+    if ((p.n_walkers + 1) / 2 > s->max_pairs) return fail(SAIL_EINVAL, "request has more walkers than the server holds");
+    if (align_up(bytes) > s->batch.ws_bytes - s->data_begin) return fail(SAIL_ENOMEM, "request larger than the server");
+    sail_server_ctx::Request r;
+    r.id = (int)s->results.size();
+    *id = r.id;
+    r.tau.assign(req->tau, req->tau + req->n_tau);
+    r.F.assign(req->F, req->F + req->n_tau);
+    r.sigma.assign(req->sigma, req->sigma + req->n_tau);
+    r.omega.assign(req->omega, req->omega + req->n_omega);
+    r.params = p;
+    r.bytes = align_up(bytes);
+    s->queue.push_back(std::move(r));
+    sail_server_ctx::Result res{};
+    res.done = false;
+    res.n_omega = req->n_omega;
+    s->results.push_back(res);
+    return SAIL_OK;
+}
+
+int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
+                     int *n_queued) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    sail_batch_ctx &b = s->batch;
+    const int slots = (int)b.h.size();
+    // admission: the head of the queue while it fits (FIFO order)
+    while (!s->queue.empty()) {
+        auto &r = s->queue.front();
+        int slot = -1;
+        for (int k = 0; k < slots && slot < 0; ++k)
+            if (!b.h[k]) slot = k;
+        const long long pairs = (r.params.n_walkers + 1) / 2;
+        size_t off = 0;
+        if (slot < 0 || s->resident_pairs + pairs > s->max_pairs || !region_take(s, r.bytes, &off)) break;
+        sail_t h = nullptr;
+        const int rc = sail_create(&h, r.tau.data(), r.F.data(), r.sigma.data(), (int)r.tau.size(), r.omega.data(),
+                                   (int)r.omega.size(), &r.params, b.ws + off, r.bytes, b.stream);
+        if (rc) {
+            region_give(s, off, r.bytes);
+            return rc;
+        }
+        b.h[slot] = h;
+        b.smem = std::max(b.smem, sweep_fp32_table_bytes(h->P));
+        s->slot_off[slot] = off;
+        s->slot_size[slot] = r.bytes;
+        s->slot_id[slot] = r.id;
+        s->resident_pairs += pairs;
+        s->queue.pop_front();
+    }
+    int active = 0;
+    for (int k = 0; k < slots; ++k) active += b.h[k] != nullptr;
+    if (active > 0) {
+        const int rc = batch_run_blocks(&b, 1, nullptr);
+        if (rc) return rc;
+    }
+    // retirement
+    int nc = 0;
+    for (int k = 0; k < slots; ++k) {
+        sail_ctx *h = b.h[k];
+        if (!h || handle_active(h)) continue;
+        auto &res = s->results[s->slot_id[k]];
+        res.mean.assign(h->n_omega, 0.0);
+        res.err.assign(h->n_omega, 0.0);
+        const int rc = average_to_host(h, res.mean.data(), res.err.data(), &res.n_used, &res.chi2_mean);
+        if (rc) return rc;
+        res.converged = h->converged ? 1 : 0;
+        res.sweeps = h->sweeps_done;
+        res.done = true;
+        if (completed && nc < max_completed) completed[nc] = s->slot_id[k];
+        ++nc;
+        s->resident_pairs -= (h->prm.n_walkers + 1) / 2;
+        sail_destroy(h);
+        b.h[k] = nullptr;
+        region_give(s, s->slot_off[k], s->slot_size[k]);
+        s->slot_id[k] = -1;
+    }
+    if (n_completed) *n_completed = nc;
+    if (n_active) {
+        int a = 0;
+        for (int k = 0; k < slots; ++k) a += b.h[k] != nullptr;
+        *n_active = a;
+    }
+    if (n_queued) *n_queued = (int)s->queue.size();
+    return SAIL_OK;
+}
+
+int sail_server_result(sail_server_t s, int id, double *S_mean, double *S_err, double *chi2_of_mean, int *converged,
+                       int *sweeps_done) {
+    if (!s || id < 0 || id >= (int)s->results.size()) return fail(SAIL_EINVAL, "unknown request id");
+    const auto &r = s->results[id];
+    if (!r.done) return fail(SAIL_ESTATE, "request %d has not completed", id);
+    if (S_mean) std::memcpy(S_mean, r.mean.data(), r.mean.size() * 8);
+    if (S_err) std::memcpy(S_err, r.err.data(), r.err.size() * 8);
+    if (chi2_of_mean) *chi2_of_mean = r.chi2_mean;
+    if (converged) *converged = r.converged;
+    if (sweeps_done) *sweeps_done = r.sweeps;
+    return SAIL_OK;
+}
+
+int sail_server_destroy(sail_server_t s) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    cudaStreamSynchronize(s->batch.stream);
+    for (sail_t h : s->batch.h)
+        if (h) sail_destroy(h);
+    cudaEventDestroy(s->batch.ev0);
+    cudaEventDestroy(s->batch.ev1);
+    delete s;
     return SAIL_OK;
 }
 
