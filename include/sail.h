@@ -59,6 +59,8 @@ typedef struct sail_params {
     int resync_every;       /* full residual recomputation period, in sweeps */
     int branching;          /* 1: imprinted branching at every block end (Sec. 2.5) */
     double T_start, T_end;  /* geometric schedule, in units of the start residue chi2_0 (Sec. 3) */
+    double T_end_abs;       /* > 0: the schedule ends at this absolute temperature instead of
+                               T_end chi2_0 (reach the noise level, chi2 ~ n_tau, whatever chi2_0) */
     double branch_fraction; /* fraction of walkers given a zero multiplier (1/4) */
     double imprint_t;       /* imprint strength t (0.1) */
     double move_scale;      /* d: 1 - r is uniform on (-y d, y d); <= 0 selects 1 / n_omega */

@@ -45,7 +45,8 @@ class CParams(ctypes.Structure):
     _fields_ = [
         ("n_walkers", ctypes.c_int), ("precision", ctypes.c_int), ("n_sweeps", ctypes.c_int),
         ("sweeps_per_block", ctypes.c_int), ("resync_every", ctypes.c_int), ("branching", ctypes.c_int),
-        ("T_start", ctypes.c_double), ("T_end", ctypes.c_double), ("branch_fraction", ctypes.c_double),
+        ("T_start", ctypes.c_double), ("T_end", ctypes.c_double), ("T_end_abs", ctypes.c_double),
+        ("branch_fraction", ctypes.c_double),
         ("imprint_t", ctypes.c_double), ("move_scale", ctypes.c_double), ("y_p", ctypes.c_double),
         ("y_m", ctypes.c_double), ("y_min", ctypes.c_double), ("A", ctypes.c_double), ("B", ctypes.c_double),
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
@@ -176,6 +177,7 @@ class Params:
     branching: bool = True
     T_start: float = 10.0
     T_end: float = 1e-9
+    T_end_abs: float = 0.0
     branch_fraction: float = 0.25
     imprint_t: float = 0.1
     move_scale: float = 0.0

@@ -150,6 +150,7 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
         return fail(SAIL_EINVAL, "n_sweeps, sweeps_per_block and resync_every must be >= 1");
     if (!(p->T_start > 0) || !(p->T_end > 0) || !std::isfinite(p->T_start) || !std::isfinite(p->T_end))
         return fail(SAIL_EINVAL, "temperatures must be finite and > 0");
+    if (!(p->T_end_abs >= 0) || !std::isfinite(p->T_end_abs)) return fail(SAIL_EINVAL, "T_end_abs must be finite, >= 0");
     if (!(p->branch_fraction >= 0 && p->branch_fraction < 1)) return fail(SAIL_EINVAL, "branch_fraction must be in [0, 1)");
     if (!(p->imprint_t >= 0 && p->imprint_t <= 1)) return fail(SAIL_EINVAL, "imprint_t must be in [0, 1]");
     if (!(p->y_p > 0 && p->y_p <= 1) || !(p->y_m >= 1) || !(p->y_min > 0 && p->y_min <= 1))
@@ -385,9 +386,10 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     }
     // geometric temperature schedule in units of chi2_0
     std::vector<double> T(p->n_sweeps);
+    const double T_end_rel = p->T_end_abs > 0 ? p->T_end_abs / chi2_0 : p->T_end;
     for (int n = 0; n < p->n_sweeps; ++n) {
         const double t = p->n_sweeps > 1 ? (double)n / (double)(p->n_sweeps - 1) : 0.0;
-        T[n] = chi2_0 * (p->T_start * std::pow(p->T_end / p->T_start, t));
+        T[n] = chi2_0 * (p->T_start * std::pow(T_end_rel / p->T_start, t));
     }
 
     sail_ctx *h = new sail_ctx();

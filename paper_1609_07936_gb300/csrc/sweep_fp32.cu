@@ -84,9 +84,42 @@ __device__ void load_tables(const DevProblem &P, float *sm) {
     }
 }
 
+// Packed pairs of floats: Blackwell executes mul/fma.rn.f32x2 as one instruction for two
+// independent round-to-nearest operations, so each element pair of the move costs half the
+// instructions of two scalar streams and rounds exactly as they would.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up(f2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
+
 // Sweeps [n0, n1) for the two walkers 2 pair, 2 pair + 1 of one problem on one warp (half-warp
 // per walker).  sm holds the problem's tables; b_stage, if not null, the staged spectra of
-// walkers walker_lo.. .
+// walkers walker_lo.. .  Every 16 moves each lane of a half-warp draws the random words of one
+// move and works out that move's bins, amplitude eps, acceptance uniform u and delta_p,
+// delta_s (Eqs. update-delta-p/s); the move loop then takes them by shuffle.
 template <int C2>
 __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1, int pair, const float *sm,
                          float *b_stage, int walker_lo) {
@@ -104,42 +137,45 @@ __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1,
     const int wr = active ? w : 2 * pair;             // a valid walker to read from
     float *b = b_stage ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
 
-    float R[2 * C2], M[2 * C2];
+    f2 R[C2], M[C2];
 #pragma unroll
     for (int c = 0; c < C2; ++c) {
         const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + 32 * c + 2 * hl);
-        const float2 f2 = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
-        R[2 * c] = r2.x;
-        R[2 * c + 1] = r2.y;
-        M[2 * c] = f2.x - r2.x;
-        M[2 * c + 1] = f2.y - r2.y;
+        const float2 f2v = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
+        R[c] = pk(r2.x, r2.y);
+        M[c] = pk(f2v.x - r2.x, f2v.y - r2.y);
     }
     float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
     double chi2 = S.chi2[wr];
     int accp = S.acc_prev[wr];
     unsigned long long nacc = 0, npos = 0;
+    const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
 
     for (int n = n0; n < n1; ++n) {
         const float invT = (float)(1.0 / P.Tsweep[n]);
         const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
         int acc = 0, pos = 0;
         float dchi = 0.0f;
-        uint4 batch = make_uint4(0u, 0u, 0u, 0u);
+        int my_ps = 0;
+        float my_eps = 0.0f, my_u = 0.0f, my_dp = 0.0f, my_ds = 0.0f;
         for (int mv = 0; mv < NO; ++mv) {
             const int src = mv & 15;
-            if (src == 0)
-                batch = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
-            const uint32_t w0 = __shfl_sync(kFull, batch.x, src, 16);
-            const uint32_t w1 = __shfl_sync(kFull, batch.y, src, 16);
-            const uint32_t w2 = __shfl_sync(kFull, batch.z, src, 16);
-            const uint32_t w3 = __shfl_sync(kFull, batch.w, src, 16);
-            int p, s;
-            move_bins(w0, w1, NO, p, s);
-            const float eps = yd * (2.0f * unit32(w2) - 1.0f);
-            const float u = unit32(w3);
+            if (src == 0) {
+                const uint4 rnd = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
+                int p, s;
+                move_bins(rnd.x, rnd.y, NO, p, s);
+                my_ps = p | (s << 16);
+                my_eps = yd * (2.0f * unit32(rnd.z) - 1.0f);
+                my_u = unit32(rnd.w);
+                deltas(my_eps, p, s, sBeta, sRgap, my_dp, my_ds);
+            }
+            const int ps = __shfl_sync(kFull, my_ps, src, 16);
+            const float eps = __shfl_sync(kFull, my_eps, src, 16);
+            const float u = __shfl_sync(kFull, my_u, src, 16);
+            const float dp = __shfl_sync(kFull, my_dp, src, 16);
+            const float ds = __shfl_sync(kFull, my_ds, src, 16);
+            const int p = ps & 0xFFFF, s = ps >> 16;
             const float r = 1.0f - eps;
-            float dp, ds;
-            deltas(eps, p, s, sBeta, sRgap, dp, ds);
             const float ap = fmaf(r, ghi * b[p], dp);
             const float as = fmaf(r, ghi * b[s], ds);
             const bool ok = active && ap >= 0.0f && as >= 0.0f;
@@ -149,25 +185,23 @@ __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1,
                 const float *qlp = sQlo + (p & 31) * PAD + 2 * hl;
                 const float *qhs = sQhi + (s >> 5) * PAD + 2 * hl;
                 const float *qls = sQlo + (s & 31) * PAD + 2 * hl;
-                float d[2 * C2];
-                float part = 0.0f;
+                const f2 e2 = pk(eps, eps), mdp = pk(-dp, -dp), mds = pk(-ds, -ds);
+                f2 d[C2];
+                f2 part = pk(0.0f, 0.0f);
 #pragma unroll
                 for (int c = 0; c < C2; ++c) {
-                    const float2 a1 = *reinterpret_cast<const float2 *>(qhp + 32 * c);
-                    const float2 a2 = *reinterpret_cast<const float2 *>(qlp + 32 * c);
-                    const float2 b1 = *reinterpret_cast<const float2 *>(qhs + 32 * c);
-                    const float2 b2 = *reinterpret_cast<const float2 *>(qls + 32 * c);
-                    d[2 * c] = fmaf(-ds, b1.x * b2.x, fmaf(-dp, a1.x * a2.x, eps * M[2 * c]));
-                    d[2 * c + 1] = fmaf(-ds, b1.y * b2.y, fmaf(-dp, a1.y * a2.y, eps * M[2 * c + 1]));
-                    part = fmaf(d[2 * c], fmaf(2.0f, R[2 * c], d[2 * c]), part);
-                    part = fmaf(d[2 * c + 1], fmaf(2.0f, R[2 * c + 1], d[2 * c + 1]), part);
+                    const f2 Kp = mul2(lds2(qhp + 32 * c), lds2(qlp + 32 * c));
+                    const f2 Ks = mul2(lds2(qhs + 32 * c), lds2(qls + 32 * c));
+                    d[c] = fma2(mds, Ks, fma2(mdp, Kp, mul2(e2, M[c])));
+                    part = fma2(d[c], fma2(two, R[c], d[c]), part);
                 }
-                const float D = half_sum(part);
+                const float2 pp = up(part);
+                const float D = half_sum(pp.x + pp.y);
                 if (ok && (D <= 0.0f || u < __expf(-D * invT))) {
 #pragma unroll
-                    for (int c = 0; c < 2 * C2; ++c) {
-                        R[c] += d[c];
-                        M[c] -= d[c];
+                    for (int c = 0; c < C2; ++c) {
+                        R[c] = add2(R[c], d[c]);
+                        M[c] = fma2(minus_one, d[c], M[c]);
                     }
                     pair_scale(ghi, glo, r);
                     if (hl == 0) {
@@ -196,7 +230,7 @@ __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1,
     }
 #pragma unroll
     for (int c = 0; c < C2; ++c)
-        *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = make_float2(R[2 * c], R[2 * c + 1]);
+        *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = up(R[c]);
     if (hl == 0) {
         S.g2[2 * w] = 1.0f;
         S.g2[2 * w + 1] = 0.0f;
