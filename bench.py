@@ -295,6 +295,115 @@ def cpu_baseline(n_walkers: int):
                       f"branching) of the paper-scale workload, {moves:.3g} moves in {dt:.1f} s"}
 
 
+# ---------------------------------------------------------------- uneven batch and serving
+def run_batch(args):
+    """256 independent inversions (n_tau U{50..500}, n_omega U{200..2000}, walkers U{256..4096},
+    noise log-uniform [1e-5, 1e-3], 1-4 random peaks) annealed together: one persistent sweep
+    launch per segment, tensor-core resync, branching every 100 sweeps, autotuned mapping."""
+    import torch
+    import paper_1609_07936_gb300 as sail
+    from workloads import random_batch_problem
+    sail.load()
+    probs = [random_batch_problem(i, seed=0) for i in range(args.batch_size)]
+    items = []
+    for i, P in enumerate(probs):
+        prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
+                          sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
+                          T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=i, resync_kind=args.resync_kind)
+        items.append((P.tau, P.F, P.sigma, P.omega, prm))
+    t0 = time.perf_counter()
+    batch = sail.Batch(items, autotune=True)
+    t_create = time.perf_counter() - t0
+    batch.anneal(args.warmup)
+    moves0 = sum(h.info()["moves"] for h in batch.handles)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = batch.stream
+    e0.record(st)
+    batch.anneal(args.steps)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    moves = sum(h.info()["moves"] for h in batch.handles) - moves0
+    per_inv = float(np.mean([N_SWEEPS * P.n_walkers * P.n_omega for P in probs]))
+    value = moves / (ms * 1e-3)
+    out = {"metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"uneven batch: {len(probs)} inversions, n_tau U{{50..500}}, n_omega U{{200..2000}}, "
+                                  f"walkers U{{256..4096}} (total {sum(P.n_walkers for P in probs)}), noise log-U[1e-5,1e-3], "
+                                  f"one persistent sweep launch per {RESYNC_EVERY}-sweep segment",
+                      "step": f"one block ({SWEEPS_PER_BLOCK} sweeps) of every inversion"},
+           "inversions_per_s": value / per_inv, "moves_per_inversion": per_inv,
+           "tuning": batch.tuning(), "create_s": t_create}
+    print(json.dumps(out), flush=True)
+    batch.close()
+
+
+def run_serve(args):
+    """Poisson arrivals of inversion requests (sizes as the uneven batch), each run until the
+    averaged spectrum reaches chi2 <= 1.2 n_tau or its sweep budget ends; continuous batching on
+    one device buffer (admission cap)."""
+    import torch
+    import paper_1609_07936_gb300 as sail
+    from workloads import random_batch_problem
+    sail.load()
+    rng = np.random.default_rng(12345)
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / args.rate)
+        if t > args.duration:
+            break
+        arrivals.append(t)
+    free, _ = torch.cuda.mem_get_info()
+    cap = int(min(150e9, free - (4 << 30)))
+    server = sail.Server(workspace_bytes=cap, max_resident=1024, max_walkers=1 << 22,
+                         sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY)
+    reqs = {}
+    done = {}
+    t_start = time.perf_counter()
+    nxt = 0
+    moves = 0
+    while nxt < len(arrivals) or len(done) < len(arrivals):
+        now = time.perf_counter() - t_start
+        while nxt < len(arrivals) and arrivals[nxt] <= now:
+            P = random_batch_problem(nxt, seed=99)
+            prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=args.serve_sweeps,
+                              sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
+                              T_start=1e-2, T_end_abs=0.3, A=P.A, B=P.B, seed=nxt, target_chi2=1.2 * P.n_tau,
+                              resync_kind=args.resync_kind)
+            rid = server.submit(P.tau, P.F, P.sigma, P.omega, prm)
+            reqs[rid] = (arrivals[nxt], P)
+            nxt += 1
+        if len(done) + 0 < nxt:
+            completed, active, queued = server.step()
+            tnow = time.perf_counter() - t_start
+            for rid in completed:
+                r = server.result(rid)
+                t_arr, P = reqs[rid]
+                done[rid] = (tnow - t_arr, r["converged"], r["sweeps"], r["chi2_of_mean"], P)
+                moves += r["sweeps"] * P.n_walkers * P.n_omega
+        else:
+            time.sleep(0.001)
+    wall = time.perf_counter() - t_start
+    lat = np.array([v[0] for v in done.values()])
+    conv = np.array([v[1] for v in done.values()])
+    ttt = lat[conv] if conv.any() else np.array([np.nan])
+    out = {"metric": "inversions/sec (served)", "value": len(done) / wall, "unit": "inversions/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"served: Poisson arrivals {args.rate}/s for {args.duration} s ({len(arrivals)} requests), "
+                                  f"sizes as the uneven batch, target chi2 <= 1.2 n_tau, budget {args.serve_sweeps} sweeps, "
+                                  f"T 1e-2 chi2_0 -> 0.3 absolute, admission cap {cap / 1e9:.0f} GB",
+                      "resync": "tensor" if args.resync_kind == 1 else "fp32-fma"},
+           "wall_s": wall, "walker_moves_per_s": moves / wall,
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "converged_fraction": float(conv.mean()),
+           "time_to_target_p50_s": float(np.nanpercentile(ttt, 50)), "time_to_target_p99_s": float(np.nanpercentile(ttt, 99))}
+    print(json.dumps(out), flush=True)
+    server.close()
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -313,12 +422,17 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-walkers", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve"])
+    ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
     ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1],
                     help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,
@@ -331,6 +445,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args, rank, world, local_rank)
 
