@@ -103,6 +103,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- ranks
+def aggregate(ms: float, moves: float, dist=None, device="cpu"):
+    """Whole-job figures over the ranks: the slowest rank's time, the sum of every rank's
+    walker-moves, and their ratio (walker-moves per second)."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    m = torch.tensor([moves], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(m, op=dist.ReduceOp.SUM)
+    ms_max, total = float(t.item()), float(m.item())
+    return ms_max, total, total / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------- GPU arm
 def measure_read_bandwidth(torch, sail, nbytes: int, reps: int) -> float:
     buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
@@ -200,12 +214,7 @@ def run_gpu(args, rank, world, local_rank):
         barrier()
     ms = e0.elapsed_time(e1)
     info1 = g.info()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    moves = (info1["moves"] - info0["moves"]) * world
-    value = moves / (ms_max * 1e-3)
+    ms_max, moves, value = aggregate(ms, info1["moves"] - info0["moves"], dist, "cuda")
     sweep_ms = info1["sweep_ms"] - info0["sweep_ms"]
     sweep_n = info1["sweep_launches"] - info0["sweep_launches"]
     launches = info1["kernel_launches"] - info0["kernel_launches"] + args.steps  # + one flush per step

@@ -75,7 +75,10 @@ typedef struct sail_params {
                                totals appear in sail_info */
     int resync_kind;        /* FP32 state: 0 = FP32-FMA GEMM with FP64 chunk sums, 1 = tensor
                                cores (tcgen05 TF32, three-term split) */
-    int reserved[5];
+    int wait_test;          /* test hook, 0 in use: 1 makes the tensor-core resync withhold its
+                               first commit so its bounded wait runs out (sail_anneal then
+                               returns SAIL_ETIMEOUT) */
+    int reserved[4];
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */

@@ -51,7 +51,7 @@ class CParams(ctypes.Structure):
         ("y_m", ctypes.c_double), ("y_min", ctypes.c_double), ("A", ctypes.c_double), ("B", ctypes.c_double),
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
-        ("reserved", ctypes.c_int * 5),
+        ("wait_test", ctypes.c_int), ("reserved", ctypes.c_int * 4),
     ]
 
 
@@ -192,6 +192,7 @@ class Params:
     trace: bool = False
     timing: bool = False
     resync_kind: int = 0
+    wait_test: int = 0
 
     def c(self) -> CParams:
         p = CParams()

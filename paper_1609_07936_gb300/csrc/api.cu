@@ -435,6 +435,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.Khi32 = (const float *)(ws + L.Khi32);
     P.Klo32 = (const float *)(ws + L.Klo32);
     P.n_omega_pad = NOP;
+    P.wait_test = p->wait_test;
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;

@@ -85,8 +85,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
 }
 
 // Bounded wait on an mbarrier phase; false on time-out.
-__device__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    for (long long it = 0; it < kSpinLimit; ++it)
+__device__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
 }
@@ -143,6 +143,9 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
     const uint32_t tmem = *tmem_slot;
     const uint32_t mbar_a = smem_u32(mbar);
     const uint32_t idesc = instr_desc(kM, NC);
+    // wait_test: the first tile's MMAs and commit are withheld, so its wait runs out (test hook
+    // for the time-out path; nothing is in flight when the block gives up)
+    const long long spin = P.wait_test ? 1024 : kSpinLimit;
 
     float acc_hi[CS], acc_lo[CS];
 #pragma unroll
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (*abort_flag) break;
-        if (tid == 0) {
+        if (tid == 0 && !(P.wait_test && t == 0)) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             for (int ks = 0; ks < kKT / 8; ++ks) {
                 const uint32_t koff = (uint32_t)ks * 2 * kLBO;   // 8 TF32 = two core matrices along K
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
             mma_commit(mbar_a);
         }
         // all threads wait until the MMAs have read the tiles and written the accumulators
-        if (!mbar_wait(mbar_a, phase)) {
+        if (!mbar_wait(mbar_a, phase, spin)) {
             if (tid == 0) atomicExch(status, 1);
             *abort_flag = 1;   // benign race: every writer stores 1
         }
@@ -195,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
         __syncthreads();
         if (*abort_flag) {
             // give the MMAs in flight one more bounded wait before the tensor memory is freed
-            if (tid == 0) mbar_wait(mbar_a, phase ^ 1u);
+            if (tid == 0) mbar_wait(mbar_a, phase ^ 1u, spin);
             __syncthreads();
             break;
         }

@@ -45,6 +45,7 @@ struct DevProblem {
     const float *Klo32;    // [n_tau_pad][n_omega_pad] Khat - Khi
     int n_omega_pad;       // n_omega rounded up to 32
     int tc_cols;           // tau columns per tensor-core resync block (0: the widest that fits)
+    int wait_test;         // test hook: the tensor-core resync withholds its first commit
     const double *Tsweep;
 };
 

@@ -1,0 +1,84 @@
+"""Planted mistakes: each mutated copy of the oracle source (compiled here, never committed)
+must fail at least one pin, so a plausible slip in the oracle cannot pass unnoticed."""
+import ctypes
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+SRC = os.path.join(os.path.dirname(O.__file__), "sail_oracle.c")
+
+MUTATIONS = {
+    # delta_s with the wrong sign of the gap
+    "delta_s_sign": ("double ds = eps * (B - A * x[p]) / (x[s] - x[p]);",
+                     "double ds = eps * (B - A * x[p]) / (x[p] - x[s]);"),
+    # Delta chi2 without the d^2 term
+    "drop_d2": ("D += di * (2.0 * R[i] + di);", "D += di * (2.0 * R[i]);"),
+    # kernel without the 1/tau factor
+    "kernel_tau": ("/ (2.0 * OR_PI * tau[i]);", "/ (2.0 * OR_PI);"),
+    # a Philox multiplier swapped for the other one
+    "philox_const": ("uint64_t p0 = (uint64_t)0xD2511F53u * x[0];", "uint64_t p0 = (uint64_t)0xCD9E8D57u * x[0];"),
+    # break points ln(k + xi) instead of ln(k - xi)
+    "branch_sign": ("heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) - xi[top.l]);",
+                    "heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) + xi[top.l]);"),
+}
+
+
+def _build(name):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert old in src, name
+    td = tempfile.mkdtemp()
+    c = os.path.join(td, "m.c")
+    open(c, "w").write(src.replace(old, new))
+    so = os.path.join(td, "m.so")
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC", "-o", so, c, "-lm"])
+    return so
+
+
+def _with_lib(so):
+    """Re-type a mutated library with the oracle's own signatures."""
+    saved = O._lib
+    O._lib = None
+    O._LIB_saved = O._LIB
+    O._LIB = so
+    orig_build = O.build
+    O.build = lambda force=False: so
+    try:
+        return O.lib()
+    finally:
+        O.build = orig_build
+        O._LIB = O._LIB_saved
+        O._lib = saved
+
+
+def _pins_pass(L):
+    saved = O._lib
+    O._lib = L
+    try:
+        from tests import test_oracle_model as M, test_oracle_moves as V, test_oracle_branching as B
+        checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
+                  V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
+                  lambda: B.test_multipliers_match_enumeration(0)]
+        for c in checks:
+            try:
+                c()
+            except AssertionError:
+                return False
+        return True
+    finally:
+        O._lib = saved
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    L = _with_lib(_build(name))
+    assert not _pins_pass(L), f"mutation {name} passed every pin"
+
+
+def test_unmutated_oracle_passes_the_same_checks():
+    assert _pins_pass(O.lib())
