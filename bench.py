@@ -41,13 +41,14 @@ MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 RESYNC_KIND = 1    # residual recomputation on the tensor cores (tcgen05, TF32 x3)
 
 
-def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND):
+def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
+               sweep_lanes: int = 0):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
-                      resync_kind=resync_kind)
+                      resync_kind=resync_kind, sweep_lanes=sweep_lanes)
     return P, prm
 
 
@@ -189,13 +190,15 @@ def run_gpu(args, rank, world, local_rank):
     l2_gbs = measure_read_bandwidth(torch, sail, 32 << 20, 400)
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
-    P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind)
+    P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
+                        sweep_lanes=args.sweep_lanes)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
     del warm
 
-    P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind)
+    P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
+                        sweep_lanes=args.sweep_lanes)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -220,9 +223,12 @@ def run_gpu(args, rank, world, local_rank):
     launches = info1["kernel_launches"] - info0["kernel_launches"] + args.steps  # + one flush per step
     own_launches = info1["kernel_launches"] - info0["kernel_launches"]
     moves_per_launch = (info1["moves"] - info0["moves"]) / max(sweep_n, 1)
-    # algorithmic shared-memory bytes per walker-move: two kernel columns, each the product
-    # of two FP32 factor rows of N_tau entries, plus b_p and b_s
-    bytes_per_move = 4 * N_TAU * 4 + 8
+    # algorithmic shared-memory bytes of a walker-move: b_p and b_s (8 B); then, unless the
+    # move fails the positivity test (Sec. 2.2: checked before delta chi2), two kernel columns,
+    # each the product of two FP32 factor rows of N_tau entries (4 N_tau 4 B)
+    col_bytes = 4 * N_TAU * 4
+    pos_frac = sum(b["positivity_rejected"] for b in stats) / max(len(stats), 1)
+    bytes_per_move = 8 + (1.0 - pos_frac) * col_bytes
     achieved = moves_per_launch * bytes_per_move / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9
     clk = clocks.summary(local_rank)
 
@@ -230,7 +236,8 @@ def run_gpu(args, rank, world, local_rank):
     # K blocks (per-block statistics D2H), average (D2H of the spectrum and errors)
     e2e = None
     if not args.no_e2e:
-        P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind)
+        P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
+                              sweep_lanes=args.sweep_lanes)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -272,6 +279,8 @@ def run_gpu(args, rank, world, local_rank):
                                         "threads per SM",
                          "l2_read_gbs_measured": l2_gbs,
                          "algorithmic_bytes_per_move": bytes_per_move,
+                         "bytes_per_move_rule": f"8 + (1 - positivity-rejected fraction {pos_frac:.4f}) x {col_bytes}",
+                         "sweep_lanes_per_walker": g.info().get("sweep_lanes"),
                          "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
                          "sweep_share_of_step": sweep_ms / ms},
             "kernel_ms": {"sweep": sweep_ms, "resync": info1["resync_ms"] - info0["resync_ms"],
@@ -444,6 +453,8 @@ def main():
     ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
     ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1],
                     help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05)")
+    ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
+                    help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,
                     help="sweeps per sweep-kernel launch; smaller values give short launches for profiling")
     args = ap.parse_args()

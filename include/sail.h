@@ -78,7 +78,10 @@ typedef struct sail_params {
     int wait_test;          /* test hook, 0 in use: 1 makes the tensor-core resync withhold its
                                first commit so its bounded wait runs out (sail_anneal then
                                returns SAIL_ETIMEOUT) */
-    int reserved[4];
+    int sweep_lanes;        /* FP32 moves: GPU lanes per walker, 0 = choose (8 when n_tau <= 256,
+                               else 16), 8 (n_tau <= 256 only) or 16.  The choice sets the order
+                               of the FP32 delta-chi2 sum, so trajectories depend on it */
+    int reserved[3];
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */
@@ -107,6 +110,8 @@ typedef struct sail_info {
     double sweep_ms, resync_ms, branch_ms;
     long long sweep_launches, resync_launches, branch_launches;
     long long moves;           /* walker-moves proposed so far */
+    int sweep_lanes;           /* FP32 sweep: GPU lanes per walker in use (0 for FP64) */
+    int reserved;
 } sail_info;
 
 /* Fills *p with the defaults listed above (n_walkers 1024, FP32, 20000 sweeps,

@@ -51,7 +51,7 @@ class CParams(ctypes.Structure):
         ("y_m", ctypes.c_double), ("y_min", ctypes.c_double), ("A", ctypes.c_double), ("B", ctypes.c_double),
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
-        ("wait_test", ctypes.c_int), ("reserved", ctypes.c_int * 4),
+        ("wait_test", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("reserved", ctypes.c_int * 3),
     ]
 
 
@@ -82,7 +82,7 @@ class CInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t), ("sweep_ms", ctypes.c_double), ("resync_ms", ctypes.c_double),
         ("branch_ms", ctypes.c_double), ("sweep_launches", ctypes.c_longlong),
         ("resync_launches", ctypes.c_longlong), ("branch_launches", ctypes.c_longlong),
-        ("moves", ctypes.c_longlong),
+        ("moves", ctypes.c_longlong), ("sweep_lanes", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
 
 
@@ -193,6 +193,7 @@ class Params:
     timing: bool = False
     resync_kind: int = 0
     wait_test: int = 0
+    sweep_lanes: int = 0
 
     def c(self) -> CParams:
         p = CParams()

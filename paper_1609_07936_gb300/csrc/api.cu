@@ -159,6 +159,9 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!std::isfinite(p->B)) return fail(SAIL_EINVAL, "B must be given (Sec. 2.2)");
     if (!(p->avg_chi2_factor >= 1)) return fail(SAIL_EINVAL, "avg_chi2_factor must be >= 1");
     if (p->resync_kind != 0 && p->resync_kind != 1) return fail(SAIL_EINVAL, "resync_kind must be 0 or 1");
+    if (p->sweep_lanes != 0 && p->sweep_lanes != 8 && p->sweep_lanes != 16)
+        return fail(SAIL_EINVAL, "sweep_lanes must be 0, 8 or 16");
+    if (p->sweep_lanes == 8 && n_tau > 256) return fail(SAIL_EINVAL, "sweep_lanes = 8 needs n_tau <= 256");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -436,6 +439,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.Klo32 = (const float *)(ws + L.Klo32);
     P.n_omega_pad = NOP;
     P.wait_test = p->wait_test;
+    P.lanes = p->sweep_lanes != 0 ? p->sweep_lanes : (PAD <= 256 ? 8 : 16);
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;
@@ -535,6 +539,7 @@ int sail_get_info(sail_t h, sail_info *info) {
     info->resync_launches = h->n_kind[kResync];
     info->branch_launches = h->n_kind[kBranch];
     info->moves = h->moves;
+    info->sweep_lanes = h->prm.precision == SAIL_PREC_FP32 ? h->P.lanes : 0;
     return SAIL_OK;
 }
 
@@ -832,7 +837,7 @@ int sail_philox(int n, const uint32_t *d_ctr, uint64_t seed, uint32_t *d_out, vo
 // ---------------------------------------------------------------- batches
 namespace {
 
-constexpr int kTuneCandidates[3] = {16, 8, 4};   // walker pairs per queue item (= warps per block)
+constexpr int kTuneCandidates[3] = {16, 8, 4};   // walker groups per queue item (= warps per block)
 
 }  // namespace
 
@@ -845,7 +850,10 @@ struct sail_batch_ctx {
     BatchItem *d_items;
     int *d_counter;
     size_t max_items;
-    size_t smem;               // shared memory of the batched sweep: the largest problem tables
+    size_t smem[2];            // shared memory of the batched sweeps (lanes 16, lanes 8): the largest
+                               // tables of the problems of each class
+    cudaStream_t aux;          // second stream: the two classes' sweeps run side by side
+    cudaEvent_t fork, join;
     int autotune;
     int item_pairs;            // chosen mapping
     int tune_next;             // next candidate to try (autotune), or 3 when done
@@ -877,6 +885,48 @@ int check_batch(int n, const sail_problem *probs) {
         if (rc) return rc;
     }
     return SAIL_OK;
+}
+
+void batch_streams_create(sail_batch_ctx *b) {
+    cudaEventCreate(&b->ev0);
+    cudaEventCreate(&b->ev1);
+    cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
+    cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+}
+
+void batch_streams_destroy(sail_batch_ctx *b) {
+    cudaEventDestroy(b->ev0);
+    cudaEventDestroy(b->ev1);
+    cudaEventDestroy(b->fork);
+    cudaEventDestroy(b->join);
+    cudaStreamDestroy(b->aux);
+}
+
+// One batched sweep segment: the items of problems with 16 lanes per walker, [0, n16), run on
+// the batch stream and those with 8 lanes, [n16, n16 + n8), on the second stream, forked from
+// and joined back into the batch stream.  d_counter[0] and d_counter[1] are their queues.
+cudaError_t batch_sweep_segment(sail_batch_ctx *b, int n16, int n8) {
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaSuccess;
+    if (n16 > 0 && n8 > 0) {
+        if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(b->aux, b->fork, 0)) != cudaSuccess) return e;
+    }
+    if (n16 > 0) {
+        e = launch_sweep_batch(b->d_probs, b->d_items, n16, b->d_counter, b->smem[0], b->item_pairs, 16, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (n8 > 0) {
+        cudaStream_t s8 = n16 > 0 ? b->aux : st;
+        e = launch_sweep_batch(b->d_probs, b->d_items + n16, n8, b->d_counter + 1, b->smem[1], b->item_pairs, 8, s8);
+        if (e != cudaSuccess) return e;
+    }
+    if (n16 > 0 && n8 > 0) {
+        if ((e = cudaEventRecord(b->join, b->aux)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -920,7 +970,7 @@ int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int a
     off += align_up(b->max_items * sizeof(BatchItem));
     b->d_counter = (int *)(b->ws + off);
     off += 256;
-    b->smem = 0;
+    b->smem[0] = b->smem[1] = 0;
     for (int k = 0; k < n; ++k) {
         size_t sub = 0;
         sail_workspace_size(probs[k].n_tau, probs[k].n_omega, &probs[k].params, &sub);
@@ -933,15 +983,15 @@ int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int a
             return rc;
         }
         b->h.push_back(h);
-        b->smem = std::max(b->smem, sweep_fp32_table_bytes(h->P));
+        size_t &sm = b->smem[h->P.lanes == 8 ? 1 : 0];
+        sm = std::max(sm, sweep_fp32_table_bytes(h->P));
         off += align_up(sub);
     }
     b->autotune = autotune;
     b->item_pairs = kTuneCandidates[0];
     b->tune_next = autotune ? 0 : 3;
     b->last_ns = 0.0;
-    cudaEventCreate(&b->ev0);
-    cudaEventCreate(&b->ev1);
+    batch_streams_create(b);
     if (autotune) {
         for (sail_t h : b->h) {
             const int pad = h->pad;
@@ -965,8 +1015,7 @@ int sail_batch_destroy(sail_batch_t b) {
     if (!b) return fail(SAIL_EINVAL, "NULL batch");
     cudaStreamSynchronize(b->stream);
     for (sail_t h : b->h) sail_destroy(h);
-    cudaEventDestroy(b->ev0);
-    cudaEventDestroy(b->ev1);
+    batch_streams_destroy(b);
     delete b;
     return SAIL_OK;
 }
@@ -996,7 +1045,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
     std::vector<BlockPending> pend(N);
     std::vector<int> cur(N), active(N);
     std::vector<BatchProblem> hp(N);
-    std::vector<BatchItem> items;
+    std::vector<BatchItem> items, items8;
     int done = 0;
     while (done < max_blocks) {
         bool any = false;
@@ -1013,6 +1062,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
         for (;;) {
             // one segment: every problem with sweeps left in this block advances to its next resync
             items.clear();
+            items8.clear();
             long long seg_moves = 0;
             for (int k = 0; k < N; ++k) {
                 sail_ctx *h = b->h[k];
@@ -1023,18 +1073,22 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 hp[k].n0 = cur[k];
                 hp[k].n1 = next_resync(h, cur[k], pend[k].block_end);
                 seg_moves += (long long)(hp[k].n1 - hp[k].n0) * h->prm.n_walkers * h->n_omega;
-                const int pairs = (h->prm.n_walkers + 1) / 2;
-                for (int lo = 0; lo < pairs; lo += b->item_pairs)
-                    items.push_back(BatchItem{k, lo, std::min(lo + b->item_pairs, pairs)});
+                const int wpw = sweep_walkers_per_warp(h->P);
+                const int groups = (h->prm.n_walkers + wpw - 1) / wpw;
+                // walker groups per item = warps per block (at most 8 with 8 lanes per walker)
+                const int per = h->P.lanes == 8 ? std::min(b->item_pairs, 8) : b->item_pairs;
+                std::vector<BatchItem> &dst = h->P.lanes == 8 ? items8 : items;
+                for (int lo = 0; lo < groups; lo += per) dst.push_back(BatchItem{k, lo, std::min(lo + per, groups)});
             }
+            const int n16 = (int)items.size(), n8 = (int)items8.size();
+            items.insert(items.end(), items8.begin(), items8.end());
             if (items.empty()) break;
             SAIL_CUDA(cudaMemcpyAsync(b->d_probs, hp.data(), (size_t)N * sizeof(BatchProblem), cudaMemcpyHostToDevice, st),
                       "batch H2D");
             SAIL_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem),
                                       cudaMemcpyHostToDevice, st), "batch H2D");
             cudaEventRecord(b->ev0, st);
-            cudaError_t e = launch_sweep_batch(b->d_probs, b->d_items, (int)items.size(), b->d_counter, b->smem,
-                                               b->item_pairs, st);
+            cudaError_t e = batch_sweep_segment(b, n16, n8);
             cudaEventRecord(b->ev1, st);
             if (e != cudaSuccess) return cuda_fail(e, "batched sweep launch");
             for (int k = 0; k < N; ++k) {
@@ -1076,7 +1130,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 if (rc) return rc;
                 cur[k] = hp[k].n1;
             }
-            b->sweep_launches += 1;
+            b->sweep_launches += (n16 > 0) + (n8 > 0);
             b->last_seg_moves = seg_moves;
             // walker-to-block mapping: time this launch, try the next candidate, keep the fastest
             if (b->tune_next < 3) {
@@ -1223,8 +1277,8 @@ int sail_server_create(sail_server_t *out, int max_resident, long long max_walke
     b.autotune = 1;
     b.item_pairs = kTuneCandidates[0];
     b.tune_next = 0;
-    cudaEventCreate(&b.ev0);
-    cudaEventCreate(&b.ev1);
+    b.smem[0] = b.smem[1] = 0;
+    batch_streams_create(&b);
     s->slot_off.assign(max_resident, 0);
     s->slot_size.assign(max_resident, 0);
     s->slot_id.assign(max_resident, -1);
@@ -1287,7 +1341,8 @@ int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_
             return rc;
         }
         b.h[slot] = h;
-        b.smem = std::max(b.smem, sweep_fp32_table_bytes(h->P));
+        size_t &sm = b.smem[h->P.lanes == 8 ? 1 : 0];
+        sm = std::max(sm, sweep_fp32_table_bytes(h->P));
         s->slot_off[slot] = off;
         s->slot_size[slot] = r.bytes;
         s->slot_id[slot] = r.id;
@@ -1349,8 +1404,7 @@ int sail_server_destroy(sail_server_t s) {
     cudaStreamSynchronize(s->batch.stream);
     for (sail_t h : s->batch.h)
         if (h) sail_destroy(h);
-    cudaEventDestroy(s->batch.ev0);
-    cudaEventDestroy(s->batch.ev1);
+    batch_streams_destroy(&s->batch);
     delete s;
     return SAIL_OK;
 }

@@ -46,6 +46,7 @@ struct DevProblem {
     int n_omega_pad;       // n_omega rounded up to 32
     int tc_cols;           // tau columns per tensor-core resync block (0: the widest that fits)
     int wait_test;         // test hook: the tensor-core resync withholds its first commit
+    int lanes;             // FP32 sweep: lanes per walker (8: 4 walkers per warp, n_tau <= 256; 16: 2)
     const double *Tsweep;
 };
 
@@ -112,6 +113,9 @@ cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, 
 cudaError_t launch_philox(int n, const uint32_t *ctr, uint64_t seed, uint32_t *out, cudaStream_t st);
 // Shared memory the FP32 sweep needs for its kernel tables (must fit one block).
 size_t sweep_fp32_table_bytes(const DevProblem &P);
+// Walkers one warp of the FP32 sweep runs (32 / P.lanes); batched launches count items in these
+// groups.
+int sweep_walkers_per_warp(const DevProblem &P);
 
 // One problem of a batched sweep launch: sweeps [n0, n1) (n0 == n1: nothing this launch).
 struct BatchProblem {
@@ -119,12 +123,13 @@ struct BatchProblem {
     DevState S;
     int n0, n1;
 };
-struct BatchItem {      // pairs [pair_lo, pair_hi) of problem prob, one pair per warp
-    int prob, pair_lo, pair_hi;
+struct BatchItem {      // walker groups [grp_lo, grp_hi) of problem prob, one group per warp
+    int prob, grp_lo, grp_hi;
 };
-// Persistent FP32 sweep over many problems: blocks of `warps` warps take items from the queue.
+// Persistent FP32 sweep over many problems whose DevProblem.lanes all equal `lanes`: blocks of
+// `warps` warps (at most 8 when lanes = 8) take items from the queue.
 cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
-                               size_t smem, int warps, cudaStream_t st);
+                               size_t smem, int warps, int lanes, cudaStream_t st);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes);
 

@@ -30,13 +30,7 @@ namespace sail {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kThreads = 512;          // at most 16 warps (32 walkers) per round
-
-__device__ __forceinline__ float half_sum(float v) {
-#pragma unroll
-    for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
+constexpr int kThreads = 512;          // at most 16 warps per round
 
 // (hi, lo) <- (hi, lo) * r with the product's rounding error carried in lo.
 __device__ __forceinline__ void pair_scale(float &hi, float &lo, float r) {
@@ -58,10 +52,10 @@ __device__ __forceinline__ void deltas(float eps, int p, int s, const float *bet
 }
 
 struct SweepGeom {
-    int pairs_total;      // ceil(n_walkers / 2)
-    int pairs_per_cta;
+    int groups_total;     // walker groups (one warp each): ceil(n_walkers / walkers per warp)
+    int groups_per_cta;
     int warps;            // warps per block
-    int rounds;           // pairs handled one after another by each warp
+    int rounds;           // groups handled one after another by each warp
     int stage_b;          // spectra staged in shared memory
 };
 
@@ -113,37 +107,181 @@ __device__ __forceinline__ f2 add2(f2 a, f2 b) {
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
-__device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
 
-// Sweeps [n0, n1) for the two walkers 2 pair, 2 pair + 1 of one problem on one warp (half-warp
-// per walker).  sm holds the problem's tables; b_stage, if not null, the staged spectra of
-// walkers walker_lo.. .  Every 16 moves each lane of a half-warp draws the random words of one
-// move and works out that move's bins, amplitude eps, acceptance uniform u and delta_p,
-// delta_s (Eqs. update-delta-p/s); the move loop then takes them by shuffle.
-template <int C2>
-__device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1, int pair, const float *sm,
-                         float *b_stage, int walker_lo) {
+// One chunk of the four factor rows a move needs (Qhi and Qlo rows of bins p and s): a lane's
+// E-float piece of each (shared-window addresses).
+__device__ __forceinline__ void ld_chunk(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, f2 (&v0)[1],
+                                         f2 (&v1)[1], f2 (&v2)[1], f2 (&v3)[1]) {
+    asm volatile("ld.shared.u64 %0, [%4];\n\tld.shared.u64 %1, [%5];\n\t"
+                 "ld.shared.u64 %2, [%6];\n\tld.shared.u64 %3, [%7];"
+                 : "=l"(v0[0]), "=l"(v1[0]), "=l"(v2[0]), "=l"(v3[0])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
+}
+__device__ __forceinline__ void ld_chunk(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, f2 (&v0)[2],
+                                         f2 (&v1)[2], f2 (&v2)[2], f2 (&v3)[2]) {
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%8];\n\tld.shared.v2.u64 {%2, %3}, [%9];\n\t"
+                 "ld.shared.v2.u64 {%4, %5}, [%10];\n\tld.shared.v2.u64 {%6, %7}, [%11];"
+                 : "=l"(v0[0]), "=l"(v0[1]), "=l"(v1[0]), "=l"(v1[1]), "=l"(v2[0]), "=l"(v2[1]), "=l"(v3[0]),
+                   "=l"(v3[1])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// The random words of one move (Philox counter (move, sweep, walker, 0)): bins p, s packed in
+// one word, amplitude eps, Metropolis threshold -T ln u (u < exp(-D / T) <=> D < -T ln u) and
+// delta_p, delta_s (Eqs. update-delta-p/s).
+struct MoveDraw {
+    int ps;
+    float eps, thr, dp, ds;
+};
+
+__device__ __forceinline__ MoveDraw draw_move(int mv, int n, int walker, uint2 key, int NO, float yd, float T,
+                                              const float *beta, const float *rgap) {
+    const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)walker, 0u), key);
+    int p, s;
+    move_bins(rnd.x, rnd.y, NO, p, s);
+    MoveDraw m;
+    m.ps = p | (s << 16);
+    m.eps = yd * (2.0f * unit32(rnd.z) - 1.0f);
+    m.thr = -logf(unit32(rnd.w)) * T;
+    deltas(m.eps, p, s, beta, rgap, m.dp, m.ds);
+    return m;
+}
+
+__device__ __forceinline__ MoveDraw take_move(const MoveDraw &mine, int src, int width) {
+    MoveDraw m;
+    m.ps = __shfl_sync(kFull, mine.ps, src, width);
+    m.eps = __shfl_sync(kFull, mine.eps, src, width);
+    m.thr = __shfl_sync(kFull, mine.thr, src, width);
+    m.dp = __shfl_sync(kFull, mine.dp, src, width);
+    m.ds = __shfl_sync(kFull, mine.ds, src, width);
+    return m;
+}
+
+// Shared-window addresses of a lane's piece of chunk 0 of the four factor rows of a move.
+struct RowAddr {
+    uint32_t hp, lp, hs, ls;
+};
+__device__ __forceinline__ RowAddr row_addr(int ps, uint32_t qhi, uint32_t qlo, int PAD) {
+    const int p = ps & 0xFFFF, s = ps >> 16;
+    RowAddr a;
+    a.hp = qhi + 4u * (uint32_t)((p >> 5) * PAD);
+    a.lp = qlo + 4u * (uint32_t)((p & 31) * PAD);
+    a.hs = qhi + 4u * (uint32_t)((s >> 5) * PAD);
+    a.ls = qlo + 4u * (uint32_t)((s & 31) * PAD);
+    return a;
+}
+
+// dpart = -delta_p Khat_p - delta_s Khat_s over the lane's elements, the columns formed from
+// the factor rows (Eq. efficient-correlation-model).
+template <int G, int C>
+__device__ __forceinline__ void columns(f2 (&dpart)[C][32 / G / 2], uint32_t qhi, uint32_t qlo, int PAD,
+                                        const MoveDraw &m) {
+    constexpr int H = 32 / G / 2;
+    const RowAddr a = row_addr(m.ps, qhi, qlo, PAD);
+    const f2 mdp = pk(-m.dp, -m.dp), mds = pk(-m.ds, -m.ds);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        f2 hp[H], lp[H], hs[H], ls[H];
+        ld_chunk(a.hp + 128u * c, a.lp + 128u * c, a.hs + 128u * c, a.ls + 128u * c, hp, lp, hs, ls);
+#pragma unroll
+        for (int h = 0; h < H; ++h) dpart[c][h] = fma2(mds, mul2(hs[h], ls[h]), mul2(mdp, mul2(hp[h], lp[h])));
+    }
+}
+
+// A lane's part of delta chi2 = sum_i d_i (2 R_i + d_i), two interleaved accumulators.
+template <int C, int H>
+__device__ __forceinline__ float delta_sum(const f2 (&d)[C][H], const f2 (&R)[C][H], f2 two) {
+    f2 part0 = 0ull, part1 = 0ull;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if ((c * H + h) & 1)
+                part1 = fma2(d[c][h], fma2(two, R[c][h], d[c][h]), part1);
+            else
+                part0 = fma2(d[c][h], fma2(two, R[c][h], d[c][h]), part0);
+        }
+    const float2 pp = up(add2(part0, part1));
+    return pp.x + pp.y;
+}
+
+// Sweeps [n0, n1) for the 32 / G walkers of group grp of one problem on one warp, G lanes per
+// walker.  Lane l of a walker's G lanes holds R_i and M_i = Fhat_i - R_i for
+// i = 32 c + E l .. 32 c + E l + E - 1 (E = 32 / G floats of every 32-tau chunk c) and reads the
+// same E-float pieces of the kernel factor rows, so the G lanes of one walker cover a chunk
+// with one 128-byte shared-memory access.  sm holds the problem's tables; b_stage, if not null,
+// the staged spectra of walkers walker_lo.. .
+//
+// Every G moves each lane draws the random words of one move; the move loop takes them by
+// shuffle.  The loop is software-pipelined: while move k's delta chi2 is reduced and tested,
+// the warp already loads move k+1's kernel columns and forms the part of its residual change
+// that does not depend on move k, dpart = -delta_p Khat_p - delta_s Khat_s; when move k+1 is
+// evaluated, d = eps M + dpart (for n_tau > 256 the columns are loaded when the move is
+// evaluated: the pipeline's registers do not fit).  Columns are loaded for every walker, also
+// those whose move then fails the positivity test: with few warps per SM the sweep is bound by
+// the latency of each warp's instruction stream more than by shared-memory bandwidth.
+template <int G, int C, bool STAGED>
+__device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
+                                          const float *sm,
+                          float *b_stage, int walker_lo) {
+    constexpr int E = 32 / G;          // floats of a 32-tau chunk per lane
+    constexpr int H = E / 2;           // float pairs of a chunk per lane
+    constexpr int WPW = 32 / G;        // walkers per warp
+    // the pipelined loop holds four arrays of C H float pairs (R, M, d and the next move's
+    // dpart); past 8 chunks that outgrows the registers, and the columns of a move are loaded
+    // when it is evaluated
+    constexpr bool PIPE = C <= 8;
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
     const float *sQhi = sm;
     const float *sQlo = sQhi + (size_t)NH * PAD;
     const float *sBeta = sQlo + (size_t)32 * PAD;
     const float *sRgap = sBeta + NO;
-    const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), sub = lane / G;
+    const uint32_t qhi = (uint32_t)__cvta_generic_to_shared(sQhi) + 4u * E * gl;
+    const uint32_t qlo = (uint32_t)__cvta_generic_to_shared(sQlo) + 4u * E * gl;
     const uint2 key = philox_key(P.seed);
     const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
 
-    const int w = 2 * pair + half;
+    const int w = WPW * grp + sub;
     const bool active = w < P.n_walkers;
-    const int wr = active ? w : 2 * pair;             // a valid walker to read from
-    float *b = b_stage ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+    const int wr = active ? w : WPW * grp;            // a valid walker to read from
+    float *b = STAGED ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+    // the walker's spectrum b: shared memory when staged, else global memory
+    const uint32_t bsh = STAGED ? (uint32_t)__cvta_generic_to_shared(b) : 0u;
+    auto bget = [&](int j) -> float {
+        if constexpr (STAGED) {
+            float v;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(bsh + 4u * (uint32_t)j));
+            return v;
+        } else {
+            return b[j];
+        }
+    };
+    auto bset = [&](int j, float v) {
+        if constexpr (STAGED)
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(bsh + 4u * (uint32_t)j), "f"(v) : "memory");
+        else
+            b[j] = v;
+    };
 
-    f2 R[C2], M[C2];
+    f2 R[C][H], M[C][H];
 #pragma unroll
-    for (int c = 0; c < C2; ++c) {
-        const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + 32 * c + 2 * hl);
-        const float2 f2v = *reinterpret_cast<const float2 *>(P.Fhat32 + 32 * c + 2 * hl);
-        R[c] = pk(r2.x, r2.y);
-        M[c] = pk(f2v.x - r2.x, f2v.y - r2.y);
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int i = 32 * c + E * gl + 2 * h;
+            const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + i);
+            const float2 f2v = *reinterpret_cast<const float2 *>(P.Fhat32 + i);
+            R[c][h] = pk(r2.x, r2.y);
+            M[c][h] = pk(f2v.x - r2.x, f2v.y - r2.y);
+        }
     }
     float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
     double chi2 = S.chi2[wr];
@@ -152,86 +290,86 @@ __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1,
     const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
 
     for (int n = n0; n < n1; ++n) {
-        const float invT = (float)(1.0 / P.Tsweep[n]);
+        const float T = (float)P.Tsweep[n];
         const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
         int acc = 0, pos = 0;
         float dchi = 0.0f;
-        int my_ps = 0;
-        float my_eps = 0.0f, my_u = 0.0f, my_dp = 0.0f, my_ds = 0.0f;
+        MoveDraw mine = draw_move(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        MoveDraw cur = take_move(mine, 0, G);
+        f2 dcur[PIPE ? C : 1][H];
+        if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
         for (int mv = 0; mv < NO; ++mv) {
-            const int src = mv & 15;
-            if (src == 0) {
-                const uint4 rnd = philox4x32_10(make_uint4((uint32_t)(mv + hl), (uint32_t)n, (uint32_t)wr, 0u), key);
-                int p, s;
-                move_bins(rnd.x, rnd.y, NO, p, s);
-                my_ps = p | (s << 16);
-                my_eps = yd * (2.0f * unit32(rnd.z) - 1.0f);
-                my_u = unit32(rnd.w);
-                deltas(my_eps, p, s, sBeta, sRgap, my_dp, my_ds);
-            }
-            const int ps = __shfl_sync(kFull, my_ps, src, 16);
-            const float eps = __shfl_sync(kFull, my_eps, src, 16);
-            const float u = __shfl_sync(kFull, my_u, src, 16);
-            const float dp = __shfl_sync(kFull, my_dp, src, 16);
-            const float ds = __shfl_sync(kFull, my_ds, src, 16);
-            const int p = ps & 0xFFFF, s = ps >> 16;
-            const float r = 1.0f - eps;
-            const float ap = fmaf(r, ghi * b[p], dp);
-            const float as = fmaf(r, ghi * b[s], ds);
+            // move k: positivity (Eq. probability-density) on the spectrum as it is now
+            const int p = cur.ps & 0xFFFF, s = cur.ps >> 16;
+            const float r = 1.0f - cur.eps;
+            const float ap = fmaf(r, ghi * bget(p), cur.dp);
+            const float as = fmaf(r, ghi * bget(s), cur.ds);
             const bool ok = active && ap >= 0.0f && as >= 0.0f;
             pos += (active && !ok);
-            if (__any_sync(kFull, ok)) {
-                const float *qhp = sQhi + (p >> 5) * PAD + 2 * hl;
-                const float *qlp = sQlo + (p & 31) * PAD + 2 * hl;
-                const float *qhs = sQhi + (s >> 5) * PAD + 2 * hl;
-                const float *qls = sQlo + (s & 31) * PAD + 2 * hl;
-                const f2 e2 = pk(eps, eps), mdp = pk(-dp, -dp), mds = pk(-ds, -ds);
-                f2 d[C2];
-                f2 part = pk(0.0f, 0.0f);
+            // move k: residual change d = eps M + dpart
+            const f2 e2 = pk(cur.eps, cur.eps);
+            f2 d[C][H];
+            if constexpr (PIPE) {
 #pragma unroll
-                for (int c = 0; c < C2; ++c) {
-                    const f2 Kp = mul2(lds2(qhp + 32 * c), lds2(qlp + 32 * c));
-                    const f2 Ks = mul2(lds2(qhs + 32 * c), lds2(qls + 32 * c));
-                    d[c] = fma2(mds, Ks, fma2(mdp, Kp, mul2(e2, M[c])));
-                    part = fma2(d[c], fma2(two, R[c], d[c]), part);
-                }
-                const float2 pp = up(part);
-                const float D = half_sum(pp.x + pp.y);
-                if (ok && (D <= 0.0f || u < __expf(-D * invT))) {
+                for (int c = 0; c < C; ++c)
 #pragma unroll
-                    for (int c = 0; c < C2; ++c) {
-                        R[c] = add2(R[c], d[c]);
-                        M[c] = fma2(minus_one, d[c], M[c]);
+                    for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], dcur[c][h]);
+            } else {
+                columns<G, C>(d, qhi, qlo, PAD, cur);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], d[c][h]);
+            }
+            // move k+1: its words and (pipelined) its columns, into dcur, now free; neither
+            // depends on move k's outcome
+            const MoveDraw nxt = take_move(mine, (mv + 1) & (G - 1), G);
+            if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
+            // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
+            const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
+            if (ok && (D <= 0.0f || D < cur.thr)) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        R[c][h] = add2(R[c][h], d[c][h]);
+                        M[c][h] = fma2(minus_one, d[c][h], M[c][h]);
                     }
-                    pair_scale(ghi, glo, r);
-                    if (hl == 0) {
-                        const float inv_g = 1.0f / ghi;
-                        b[p] = ap * inv_g;
-                        b[s] = as * inv_g;
-                    }
-                    dchi += D;
-                    ++acc;
                 }
+                pair_scale(ghi, glo, r);
+                if (gl == 0) {
+                    const float inv_g = 1.0f / ghi;
+                    bset(p, ap * inv_g);
+                    bset(s, as * inv_g);
+                }
+                dchi += D;
+                ++acc;
             }
             __syncwarp();
+            cur = nxt;
+            // the next batch of G moves, one per lane, before its first move is taken
+            if (((mv + 2) & (G - 1)) == 0 && mv + 2 < NO)
+                mine = draw_move(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
         }
         chi2 += (double)dchi;
         accp = acc;
         nacc += acc;
         npos += pos;
-        if (active && S.acc_trace && hl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+        if (active && S.acc_trace && gl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
     }
     if (!active) return;
     // fold the common scale into the spectrum and write the walker back
     float *bg = S.b32 + (size_t)w * NO;
-    for (int j = hl; j < NO; j += 16) {
+    for (int j = gl; j < NO; j += G) {
         const float v = b[j];
         bg[j] = fmaf(glo, v, ghi * v);
     }
 #pragma unroll
-    for (int c = 0; c < C2; ++c)
-        *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + 2 * hl) = up(R[c]);
-    if (hl == 0) {
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + E * gl + 2 * h) = up(R[c][h]);
+    if (gl == 0) {
         S.g2[2 * w] = 1.0f;
         S.g2[2 * w + 1] = 0.0f;
         S.chi2[w] = chi2;
@@ -241,38 +379,80 @@ __device__ void run_pair(const DevProblem &P, const DevState &S, int n0, int n1,
     }
 }
 
-template <int C2>
-__global__ void __launch_bounds__(kThreads) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
-                                                              SweepGeom G) {
+// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker (128 registers a
+// thread), 8 warps with 8 lanes per walker (whose 4 walkers a warp hold twice the residual
+// elements per lane).
+template <int G>
+constexpr int sweep_threads() { return G == 8 ? 256 : kThreads; }
+
+template <int G, int C>
+__global__ void __launch_bounds__(sweep_threads<G>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
+                                                              SweepGeom Gm) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
+    constexpr int WPW = 32 / G;
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
-    float *sB = sm + (size_t)(NH + 32) * PAD + 2 * NO;   // staged spectra [2 * pairs_per_cta][NO]
+    float *sB = sm + (size_t)(NH + 32) * PAD + 2 * NO;   // staged spectra [WPW * groups_per_cta][NO]
     load_tables(P, sm);
-    const int pair_lo = blockIdx.x * G.pairs_per_cta;
-    const int pair_hi = min(pair_lo + G.pairs_per_cta, G.pairs_total);
-    const int walker_lo = 2 * pair_lo;
-    const int walker_hi = min(2 * pair_hi, P.n_walkers);
-    if (G.stage_b) {
+    const int grp_lo = blockIdx.x * Gm.groups_per_cta;
+    const int grp_hi = min(grp_lo + Gm.groups_per_cta, Gm.groups_total);
+    const int walker_lo = WPW * grp_lo;
+    const int walker_hi = min(WPW * grp_hi, P.n_walkers);
+    if (Gm.stage_b) {
         const size_t n = (size_t)(walker_hi - walker_lo) * NO;
         const float *src = S.b32 + (size_t)walker_lo * NO;
         for (size_t q = threadIdx.x; q < n; q += blockDim.x) sB[q] = src[q];
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
-    for (int round = 0; round < G.rounds; ++round) {
-        const int pair = pair_lo + round * G.warps + warp;
-        if (pair >= pair_hi) break;                       // uniform across the warp
-        run_pair<C2>(P, S, n0, n1, pair, sm, G.stage_b ? sB : nullptr, walker_lo);
+    for (int round = 0; round < Gm.rounds; ++round) {
+        const int grp = grp_lo + round * Gm.warps + warp;
+        if (grp >= grp_hi) break;                         // uniform across the warp
+        if (Gm.stage_b)
+            run_group<G, C, true>(P, S, n0, n1, grp, sm, sB, walker_lo);
+        else
+            run_group<G, C, false>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
     }
 }
 
-// Many inversions in one persistent launch: blocks take (problem, pair range) items from a
-// queue, load the item's problem tables when the problem changes, and run one pair per warp.
-// The per-walker arithmetic is that of sweep_fp32_kernel, so a walker's trajectory does not
+template <int G>
+__device__ __forceinline__ void run_group_c(const BatchProblem &BP, int grp, const float *sm) {
+    switch (BP.P.n_tau_pad / 32) {
+        case 1: run_group<G, 1, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 2: run_group<G, 2, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 3: run_group<G, 3, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 4: run_group<G, 4, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 5: run_group<G, 5, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 6: run_group<G, 6, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 7: run_group<G, 7, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 8: run_group<G, 8, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        default:
+            if constexpr (G == 16) {
+                switch (BP.P.n_tau_pad / 32) {
+                    case 9: run_group<16, 9, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 10: run_group<16, 10, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 11: run_group<16, 11, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 12: run_group<16, 12, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 13: run_group<16, 13, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 14: run_group<16, 14, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 15: run_group<16, 15, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 16: run_group<16, 16, false>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    default: break;
+                }
+            }
+            break;
+    }
+}
+
+// Many inversions in one persistent launch: blocks take (problem, group range) items from a
+// queue, load the item's problem tables when the problem changes, and run one walker group per
+// warp.  One launch serves the problems of one lane count G (its register budget differs);
+// the per-walker arithmetic is that of sweep_fp32_kernel, so a walker's trajectory does not
 // depend on which block, or which other problems, share the launch.
-__global__ void __launch_bounds__(kThreads) sweep_batch_kernel(const BatchProblem *probs, const BatchItem *items,
-                                                               int n_items, int *counter) {
+template <int G>
+__global__ void __launch_bounds__(sweep_threads<G>()) sweep_batch_kernel(const BatchProblem *probs,
+                                                                        const BatchItem *items, int n_items,
+                                                                        int *counter) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
     __shared__ int s_item, s_loaded;
@@ -292,27 +472,9 @@ __global__ void __launch_bounds__(kThreads) sweep_batch_kernel(const BatchProble
             if (threadIdx.x == 0) s_loaded = I.prob;
         }
         __syncthreads();
-        const int pair = I.pair_lo + warp;
-        if (pair >= I.pair_hi || BP.n0 >= BP.n1) continue;
-        switch (BP.P.n_tau_pad / 32) {
-            case 1: run_pair<1>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 2: run_pair<2>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 3: run_pair<3>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 4: run_pair<4>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 5: run_pair<5>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 6: run_pair<6>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 7: run_pair<7>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 8: run_pair<8>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 9: run_pair<9>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 10: run_pair<10>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 11: run_pair<11>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 12: run_pair<12>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 13: run_pair<13>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 14: run_pair<14>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 15: run_pair<15>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            case 16: run_pair<16>(BP.P, BP.S, BP.n0, BP.n1, pair, sm, nullptr, 0); break;
-            default: break;
-        }
+        const int grp = I.grp_lo + warp;
+        if (grp >= I.grp_hi || BP.n0 >= BP.n1) continue;
+        run_group_c<G>(BP, grp, sm);
     }
 }
 
@@ -321,28 +483,29 @@ size_t table_bytes(const DevProblem &P) {
     return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
 }
 
-template <int C2>
+template <int G, int C>
 cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    SweepGeom G;
-    G.pairs_total = (P.n_walkers + 1) / 2;
-    const int ctas = G.pairs_total < sms ? G.pairs_total : sms;
-    G.pairs_per_cta = (G.pairs_total + ctas - 1) / ctas;
-    const int max_warps = kThreads / 32;
-    G.rounds = (G.pairs_per_cta + max_warps - 1) / max_warps;
-    G.warps = (G.pairs_per_cta + G.rounds - 1) / G.rounds;
+    constexpr int WPW = 32 / G;
+    SweepGeom Gm;
+    Gm.groups_total = (P.n_walkers + WPW - 1) / WPW;
+    const int ctas = Gm.groups_total < sms ? Gm.groups_total : sms;
+    Gm.groups_per_cta = (Gm.groups_total + ctas - 1) / ctas;
+    const int max_warps = sweep_threads<G>() / 32;
+    Gm.rounds = (Gm.groups_per_cta + max_warps - 1) / max_warps;
+    Gm.warps = (Gm.groups_per_cta + Gm.rounds - 1) / Gm.rounds;
     const size_t tb = table_bytes(P);
-    const size_t staged = (size_t)2 * G.pairs_per_cta * P.n_omega * 4;
+    const size_t staged = (size_t)WPW * Gm.groups_per_cta * P.n_omega * 4;
     if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
-    G.stage_b = tb + staged <= (size_t)smem_max;
-    const size_t smem = tb + (G.stage_b ? staged : 0);
-    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<C2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    Gm.stage_b = tb + staged <= (size_t)smem_max;
+    const size_t smem = tb + (Gm.stage_b ? staged : 0);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int n_ctas = (G.pairs_total + G.pairs_per_cta - 1) / G.pairs_per_cta;
-    sweep_fp32_kernel<C2><<<n_ctas, G.warps * 32, smem, st>>>(P, S, n0, n1, G);
+    const int n_ctas = (Gm.groups_total + Gm.groups_per_cta - 1) / Gm.groups_per_cta;
+    sweep_fp32_kernel<G, C><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
     return cudaGetLastError();
 }
 
@@ -449,24 +612,32 @@ cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *byt
 
 size_t sweep_fp32_table_bytes(const DevProblem &P) { return table_bytes(P); }
 
-cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
-                               size_t smem, int warps, cudaStream_t st) {
-    if (n_items <= 0) return cudaSuccess;
+template <int G>
+cudaError_t launch_batch_g(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                           size_t smem, int warps, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (warps > sweep_threads<G>() / 32) warps = sweep_threads<G>() / 32;
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    // one block per SM, or two when two blocks' tables fit in one SM's shared memory
+    // persistent: as many blocks as fit on the SMs at once
     int per_sm = 1;
-    int smem_sm = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    if (2 * (smem + 2048) <= (size_t)smem_sm && warps <= 8) per_sm = 2;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_kernel<G>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = n_items < sms * per_sm ? n_items : sms * per_sm;
-    sweep_batch_kernel<<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
+    sweep_batch_kernel<G><<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
     return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                               size_t smem, int warps, int lanes, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    return lanes == 8 ? launch_batch_g<8>(d_probs, d_items, n_items, d_counter, smem, warps, st)
+                      : launch_batch_g<16>(d_probs, d_items, n_items, d_counter, smem, warps, st);
 }
 
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st) {
@@ -477,24 +648,39 @@ cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sin
     return cudaGetLastError();
 }
 
+int sweep_walkers_per_warp(const DevProblem &P) { return P.lanes == 8 ? 4 : 2; }
+
 cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    if (P.lanes == 8) {
+        switch (P.n_tau_pad / 32) {
+            case 1: return launch_c<8, 1>(P, S, n0, n1, st);
+            case 2: return launch_c<8, 2>(P, S, n0, n1, st);
+            case 3: return launch_c<8, 3>(P, S, n0, n1, st);
+            case 4: return launch_c<8, 4>(P, S, n0, n1, st);
+            case 5: return launch_c<8, 5>(P, S, n0, n1, st);
+            case 6: return launch_c<8, 6>(P, S, n0, n1, st);
+            case 7: return launch_c<8, 7>(P, S, n0, n1, st);
+            case 8: return launch_c<8, 8>(P, S, n0, n1, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (P.n_tau_pad / 32) {
-        case 1: return launch_c<1>(P, S, n0, n1, st);
-        case 2: return launch_c<2>(P, S, n0, n1, st);
-        case 3: return launch_c<3>(P, S, n0, n1, st);
-        case 4: return launch_c<4>(P, S, n0, n1, st);
-        case 5: return launch_c<5>(P, S, n0, n1, st);
-        case 6: return launch_c<6>(P, S, n0, n1, st);
-        case 7: return launch_c<7>(P, S, n0, n1, st);
-        case 8: return launch_c<8>(P, S, n0, n1, st);
-        case 9: return launch_c<9>(P, S, n0, n1, st);
-        case 10: return launch_c<10>(P, S, n0, n1, st);
-        case 11: return launch_c<11>(P, S, n0, n1, st);
-        case 12: return launch_c<12>(P, S, n0, n1, st);
-        case 13: return launch_c<13>(P, S, n0, n1, st);
-        case 14: return launch_c<14>(P, S, n0, n1, st);
-        case 15: return launch_c<15>(P, S, n0, n1, st);
-        case 16: return launch_c<16>(P, S, n0, n1, st);
+        case 1: return launch_c<16, 1>(P, S, n0, n1, st);
+        case 2: return launch_c<16, 2>(P, S, n0, n1, st);
+        case 3: return launch_c<16, 3>(P, S, n0, n1, st);
+        case 4: return launch_c<16, 4>(P, S, n0, n1, st);
+        case 5: return launch_c<16, 5>(P, S, n0, n1, st);
+        case 6: return launch_c<16, 6>(P, S, n0, n1, st);
+        case 7: return launch_c<16, 7>(P, S, n0, n1, st);
+        case 8: return launch_c<16, 8>(P, S, n0, n1, st);
+        case 9: return launch_c<16, 9>(P, S, n0, n1, st);
+        case 10: return launch_c<16, 10>(P, S, n0, n1, st);
+        case 11: return launch_c<16, 11>(P, S, n0, n1, st);
+        case 12: return launch_c<16, 12>(P, S, n0, n1, st);
+        case 13: return launch_c<16, 13>(P, S, n0, n1, st);
+        case 14: return launch_c<16, 14>(P, S, n0, n1, st);
+        case 15: return launch_c<16, 15>(P, S, n0, n1, st);
+        case 16: return launch_c<16, 16>(P, S, n0, n1, st);
         default: return cudaErrorInvalidValue;
     }
 }
