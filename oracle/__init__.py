@@ -53,6 +53,20 @@ class OrParams(ctypes.Structure):
         ("y_m", ctypes.c_double),
         ("y_min", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("schedule_kind", ctypes.c_int),
+        ("adaptive", ctypes.c_int),
+        ("cool_begin", ctypes.c_double),
+        ("freeze_begin", ctypes.c_double),
+        ("smooth_s", ctypes.c_double),
+    ]
+
+
+class OrState(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.POINTER(ctypes.c_double)),
+        ("acc_ref", ctypes.c_double),
+        ("T_freeze", ctypes.c_double),
+        ("acc_before", ctypes.c_int64),
     ]
 
 
@@ -85,8 +99,19 @@ def lib():
         L.or_temperature.restype = ctypes.c_double
         L.or_anneal.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                 ctypes.c_double, ctypes.c_double, ctypes.POINTER(OrParams),
-                                ctypes.c_double, _dp, _dp, _dp, _ip, _u64p, _i64p, _i64p,
+                                ctypes.POINTER(OrState), _dp, _dp, _dp, _ip, _u64p, _i64p, _i64p,
                                 ctypes.c_int, ctypes.c_int, _ip, _ip, _dp]
+        L.or_init_temperatures.argtypes = [ctypes.POINTER(OrParams), ctypes.c_double, _dp]
+        L.or_init_temperatures.restype = None
+        L.or_cooling_blocks.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip, _ip]
+        L.or_cooling_blocks.restype = None
+        L.or_self_cooling.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, _dp]
+        L.or_self_cooling.restype = ctypes.c_double
+        L.or_adaptive_scale.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_adaptive_scale.restype = ctypes.c_double
+        L.or_smooth.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        L.or_smooth.restype = None
         L.or_anneal.restype = ctypes.c_int
         L.or_average.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_average.restype = ctypes.c_int
@@ -187,6 +212,37 @@ def average(a, chi2, factor):
     return mean, err, used
 
 
+def smooth(x, B: float, s: float, a) -> np.ndarray:
+    """One spectrum smoothed by the three-point stencil of strength s and renormalised to
+    the second sum rule B (Sec. smoothing)."""
+    x = _f64(x)
+    out = _f64(a).copy()
+    lib().or_smooth(x.size, _p(x), float(B), float(s), _p(out))
+    return out
+
+
+def cooling_blocks(n_blocks: int, cool_begin: float, freeze_begin: float):
+    """First cooling block and first freeze-out block of a self-cooling schedule."""
+    bc = np.zeros(1, dtype=np.int32)
+    bf = np.zeros(1, dtype=np.int32)
+    lib().or_cooling_blocks(int(n_blocks), float(cool_begin), float(freeze_begin), _p(bc, _ip), _p(bf, _ip))
+    return int(bc[0]), int(bf[0])
+
+
+def self_cooling(b: int, n_blocks: int, b_cool: int, b_freeze: int, cbar: float, cmin: float,
+                 T_freeze: float = -1.0):
+    """Temperature of block b >= 1 from the previous block's mean and smallest residues;
+    returns (T, T_freeze after the call)."""
+    tf = np.array([T_freeze], dtype=np.float64)
+    T = lib().or_self_cooling(int(b), int(n_blocks), int(b_cool), int(b_freeze), float(cbar), float(cmin), _p(tf))
+    return T, float(tf[0])
+
+
+def adaptive_scale(acc: float, acc_ref: float) -> float:
+    """Factor on the branching fraction and imprint strength at acceptance acc."""
+    return lib().or_adaptive_scale(float(acc), float(acc_ref))
+
+
 def xi_for_block(seed: int, block: int, n_walkers: int) -> np.ndarray:
     """The branching draws xi_l of one block, Philox counter (l, block, 0, 1)."""
     key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
@@ -214,11 +270,18 @@ class Schedule:
     y_m: float = 2.0
     y_min: float = 1e-4
     seed: int = 0
+    schedule_kind: int = 0       # 0 geometric, 1 self-cooling
+    adaptive: bool = False       # acceptance-adaptive branching fraction and imprint strength
+    cool_begin: float = 0.1
+    freeze_begin: float = 0.5
+    smooth_s: float = 0.0
 
     def c(self) -> OrParams:
         return OrParams(self.n_sweeps, self.sweeps_per_block, self.resync_every, int(self.branching),
                         self.T_start, self.T_end, self.branch_fraction, self.imprint_t,
-                        self.move_scale, self.y_p, self.y_m, self.y_min, self.seed)
+                        self.move_scale, self.y_p, self.y_m, self.y_min, self.seed,
+                        int(self.schedule_kind), int(self.adaptive), self.cool_begin, self.freeze_begin,
+                        self.smooth_s)
 
 
 class Anneal:
@@ -242,9 +305,13 @@ class Anneal:
         self.n_acc = np.zeros(n_walkers, dtype=np.int64)
         self.n_pos = np.zeros(n_walkers, dtype=np.int64)
         self.sweep = 0
+        # the temperature of every sweep (self-cooling fills each block's entries as it gets there)
+        self.T = np.zeros(max(schedule.n_sweeps, 1))
+        lib().or_init_temperatures(ctypes.byref(self._c), self.chi2_0, _p(self.T))
+        self._st = OrState(_p(self.T), -1.0, -1.0, 0)
 
     def temperature(self, n: int) -> float:
-        return lib().or_temperature(ctypes.byref(self._c), int(n), self.chi2_0)
+        return float(self.T[n])
 
     def run(self, n_sweeps: Optional[int] = None, trace: bool = False):
         """Advance n sweeps (default: to the end of the schedule).  With trace,
@@ -257,7 +324,7 @@ class Anneal:
         m_tr = np.zeros((n_ev, self.n_walkers), dtype=np.int32)
         d_tr = np.zeros(n_ev)
         ev = lib().or_anneal(n_tau, n_omega, self.n_walkers, _p(self.K), _p(self.Fh), _p(self.x),
-                             self.A, self.B, ctypes.byref(self._c), self.chi2_0,
+                             self.A, self.B, ctypes.byref(self._c), ctypes.byref(self._st),
                              _p(self.a), _p(self.R), _p(self.chi2), _p(self.acc_prev, _ip),
                              _p(self.hash, _u64p), _p(self.n_acc, _i64p), _p(self.n_pos, _i64p),
                              self.sweep, end,

@@ -28,7 +28,15 @@
  *     formula applies the weight to P(chi2), read as chi2);
  *   - random numbers come from Philox4x32-10 (Salmon et al., SC'11), counter
  *     (move, sweep, walker, 0) for a move and (walker, block, 0, 1) for the
- *     branching draw xi, key = the 64-bit seed.
+ *     branching draw xi, key = the 64-bit seed;
+ *   - self-cooling (Sec. self-cooling): T constant per block; boil at the
+ *     population's mean residue, a geometric ramp to its smallest residue, then
+ *     a freeze-out linear in the blocks left (or_self_cooling);
+ *   - adaptive branching (Sec. 2.5): fraction and imprint strength times
+ *     min(1, acceptance / first block's acceptance);
+ *   - smoothing (Sec. smoothing) after branching, its second-sum-rule
+ *     renormalisation a multiplicative linear tilt (or_smooth), followed by a
+ *     full residual recomputation.
  *
  * Parity status: every function below is pinned by the CPU tests except the
  * Philox stream, whose CPU pins are statistical and whose value pin is the
@@ -313,12 +321,112 @@ typedef struct {
     double move_scale;     /* d: eps is uniform on (-y d, y d) */
     double y_p, y_m, y_min;
     uint64_t seed;
+    int schedule_kind;     /* 0: geometric T_start -> T_end; 1: self-cooling (Sec. self-cooling) */
+    int adaptive;          /* 1: branching fraction and imprint strength follow the acceptance (Sec. 2.5) */
+    double cool_begin;     /* self-cooling: fraction of the blocks boiled before the ramp */
+    double freeze_begin;   /* self-cooling: fraction of the blocks after which the freeze-out starts */
+    double smooth_s;       /* smoothing strength s (Sec. smoothing); 0: no smoothing */
 } or_params;
+
+/* What the anneal carries from block to block besides the walkers. */
+typedef struct {
+    double *T;             /* [n_sweeps] absolute temperature of every sweep */
+    double acc_ref;        /* acceptance of the first block (adaptive branching); < 0 until known */
+    double T_freeze;       /* self-cooling: chi2_min when the freeze-out began; < 0 until then */
+    int64_t acc_before;    /* accepted moves of all walkers before the current block */
+} or_state;
 
 /* T for sweep n: geometric from T_start to T_end over the schedule, times chi2_0. */
 double or_temperature(const or_params *prm, int n, double chi2_0) {
     double t = prm->n_sweeps > 1 ? (double)n / (double)(prm->n_sweeps - 1) : 0.0;
     return chi2_0 * (prm->T_start * pow(prm->T_end / prm->T_start, t));
+}
+
+/* Self-cooling, Sec. self-cooling.  Reading: the schedule is cut into n_blocks
+ * blocks of k sweeps; T is constant within a block.  Block 0 runs at the start
+ * residue chi2_0 (the population's mean residue then).  Block b >= 1 takes the
+ * mean residue cbar and the smallest residue cmin of the population at the end
+ * of block b - 1 (after its residual recomputation, before branching):
+ *   boiling,    b < b_cool:            T = cbar;
+ *   cooling,    b_cool <= b < b_freeze: T = cbar^(1 - x) cmin^x,
+ *               x = (b - b_cool + 1) / (b_freeze - b_cool), reaching cmin;
+ *   freeze-out, b >= b_freeze:         T = T_F (n_blocks - b) / (n_blocks - b_freeze + 1),
+ *               T_F = cmin at the first freeze-out block: below the smallest
+ *               residue and lowered in proportion to the steps taken. */
+void or_cooling_blocks(int n_blocks, double cool_begin, double freeze_begin, int *b_cool, int *b_freeze) {
+    int bc = (int)floor(cool_begin * (double)n_blocks + 0.5);
+    int bf = (int)floor(freeze_begin * (double)n_blocks + 0.5);
+    if (bc < 0) bc = 0;
+    if (bc > n_blocks) bc = n_blocks;
+    if (bf < bc) bf = bc;
+    if (bf > n_blocks) bf = n_blocks;
+    *b_cool = bc;
+    *b_freeze = bf;
+}
+
+double or_self_cooling(int b, int n_blocks, int b_cool, int b_freeze, double cbar, double cmin, double *T_freeze) {
+    if (b < b_cool) return cbar;
+    if (b < b_freeze) {
+        double x = (double)(b - b_cool + 1) / (double)(b_freeze - b_cool);
+        return pow(cbar, 1.0 - x) * pow(cmin, x);
+    }
+    if (*T_freeze < 0.0) *T_freeze = cmin;
+    return *T_freeze * (double)(n_blocks - b) / (double)(n_blocks - b_freeze + 1);
+}
+
+/* Fills the temperature table: the whole geometric schedule, or block 0 of the
+ * self-cooling one (the other blocks are set as the anneal reaches them). */
+void or_init_temperatures(const or_params *prm, double chi2_0, double *T) {
+    for (int n = 0; n < prm->n_sweeps; ++n) {
+        if (prm->schedule_kind == 1)
+            T[n] = n < prm->sweeps_per_block ? chi2_0 : NAN;
+        else
+            T[n] = or_temperature(prm, n, chi2_0);
+    }
+}
+
+/* Adaptive branching, Sec. 2.5: the branching fraction and the imprint strength
+ * are reduced as the acceptance drops.  Reading: both are multiplied by
+ * min(1, acc / acc_ref), acc the block's acceptance rate and acc_ref that of the
+ * first block. */
+double or_adaptive_scale(double acc, double acc_ref) {
+    return (acc_ref > 0.0 && acc < acc_ref) ? acc / acc_ref : 1.0;
+}
+
+/* Smoothing, Sec. smoothing: three-point stencil of strength s,
+ *   a_j <- s a_{j-1} + (1 - 2s) a_j + s a_{j+1}  (0 < j < N-1),
+ *   a_0 <- (1 - s) a_0 + s a_1,   a_{N-1} <- (1 - s) a_{N-1} + s a_{N-2},
+ * all from the old values.  It keeps sum_j a_j; the second sum rule moves by
+ * s dw (a_0 - a_{N-1}).  Renormalisation (reading): the tilt
+ * a_j <- a_j (1 + beta (x_j - m)), m = B'/A', beta = (B - B') / sum_j a_j (x_j - m)^2,
+ * which keeps sum_j a_j and restores sum_j a_j x_j = B (skipped when the tilt
+ * could make a factor negative: |beta| max_j |x_j - m| >= 1/2). */
+void or_smooth(int n_omega, const double *x, double B, double s, double *a) {
+    int N = n_omega;
+    double c = 1.0 - 2.0 * s, e = 1.0 - s;
+    double prev = a[0];
+    a[0] = e * a[0] + s * a[1];
+    for (int j = 1; j < N - 1; ++j) {
+        double cur = a[j];
+        a[j] = s * prev + c * cur + s * a[j + 1];
+        prev = cur;
+    }
+    a[N - 1] = e * a[N - 1] + s * prev;
+    double A1 = 0.0, B1 = 0.0;
+    for (int j = 0; j < N; ++j) {
+        A1 += a[j];
+        B1 += a[j] * x[j];
+    }
+    if (!(A1 > 0.0)) return;
+    double m = B1 / A1, V = 0.0;
+    for (int j = 0; j < N; ++j) {
+        double d = x[j] - m;
+        V += a[j] * d * d;
+    }
+    double beta = V > 0.0 ? (B - B1) / V : 0.0;
+    double span = fabs(x[0] - m) > fabs(x[N - 1] - m) ? fabs(x[0] - m) : fabs(x[N - 1] - m);
+    if (!(fabs(beta) * span < 0.5)) beta = 0.0;
+    for (int j = 0; j < N; ++j) a[j] = a[j] * (1.0 + beta * (x[j] - m));
 }
 
 static uint64_t fnv_step(uint64_t h, unsigned code) {
@@ -376,13 +484,13 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
  * accepted-move count of every walker in every sweep run ([sweep][walker]);
  * m_trace, if given, the multipliers of every branching ([event][walker]). */
 int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const double *Fhat,
-              const double *x, double A, double B, const or_params *prm, double chi2_0,
+              const double *x, double A, double B, const or_params *prm, or_state *st,
               double *a, double *R, double *chi2, int *acc_prev, uint64_t *hash,
               int64_t *n_acc, int64_t *n_pos, int sweep_begin, int sweep_end,
               int *acc_trace, int *m_trace, double *delta_trace) {
     int events = 0;
     for (int n = sweep_begin; n < sweep_end; ++n) {
-        double T = or_temperature(prm, n, chi2_0);
+        double T = st->T[n];
 #pragma omp parallel for schedule(static)
         for (int w = 0; w < n_walkers; ++w) {
             double *d = (double *)malloc(sizeof(double) * (n_tau > 0 ? n_tau : 1));
@@ -402,6 +510,26 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
                 chi2[w] = or_residual(n_tau, n_omega, Khat, Fhat, a + (size_t)w * n_omega,
                                       R + (size_t)w * n_tau);
         }
+        /* End of block b: its acceptance and residue statistics (after the
+         * recomputation above, before branching), then branching (Sec. 2.5),
+         * smoothing (Sec. smoothing) and the next block's temperature
+         * (Sec. self-cooling). */
+        double scale = 1.0, cbar = 0.0, cmin = chi2[0];
+        if (block_end && (prm->schedule_kind == 1 || prm->adaptive)) {
+            int64_t acc_total = 0;
+            for (int w = 0; w < n_walkers; ++w) acc_total += n_acc[w];
+            double acc = (double)(acc_total - st->acc_before) / ((double)k * (double)n_walkers * (double)n_omega);
+            st->acc_before = acc_total;
+            if (prm->adaptive) {
+                if (st->acc_ref < 0.0) st->acc_ref = acc;
+                scale = or_adaptive_scale(acc, st->acc_ref);
+            }
+            for (int w = 0; w < n_walkers; ++w) {
+                cbar += chi2[w];
+                if (chi2[w] < cmin) cmin = chi2[w];
+            }
+            cbar /= (double)n_walkers;
+        }
         if (block_end && prm->branching && n_walkers > 1) {
             int b = (n + 1) / k - 1;
             double *xi = (double *)malloc(sizeof(double) * n_walkers);
@@ -413,11 +541,11 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
                 draw(prm->seed, (uint32_t)l, (uint32_t)b, 0u, 1u, rnd);
                 xi[l] = unit(rnd[0]);
             }
-            double Delta = or_branch_multipliers(n_walkers, chi2, xi, prm->branch_fraction, m);
+            double Delta = or_branch_multipliers(n_walkers, chi2, xi, prm->branch_fraction * scale, m);
             int np = or_pairs(n_walkers, m, zl, dl);
             /* Imprinting, Sec. 2.5: a^(l1) <- t a^(l2) + (1 - t) a^(l1); by
              * linearity the residual mixes the same way. */
-            double t = prm->imprint_t, omt = 1.0 - prm->imprint_t;
+            double t = prm->imprint_t * scale, omt = 1.0 - t;
             for (int q = 0; q < np; ++q) {
                 double *a1 = a + (size_t)zl[q] * n_omega;
                 const double *a2 = a + (size_t)dl[q] * n_omega;
@@ -435,6 +563,21 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
             if (delta_trace) delta_trace[events] = Delta;
             events += 1;
             free(xi); free(m); free(zl); free(dl);
+        }
+        if (block_end && prm->smooth_s > 0.0) {
+#pragma omp parallel for schedule(static)
+            for (int w = 0; w < n_walkers; ++w) {
+                or_smooth(n_omega, x, B, prm->smooth_s, a + (size_t)w * n_omega);
+                chi2[w] = or_residual(n_tau, n_omega, Khat, Fhat, a + (size_t)w * n_omega,
+                                      R + (size_t)w * n_tau);
+            }
+        }
+        if (block_end && prm->schedule_kind == 1 && n + 1 < prm->n_sweeps) {
+            int n_blocks = (prm->n_sweeps + k - 1) / k, bc, bf;
+            or_cooling_blocks(n_blocks, prm->cool_begin, prm->freeze_begin, &bc, &bf);
+            int b_next = (n + 1) / k;
+            double Tn = or_self_cooling(b_next, n_blocks, bc, bf, cbar, cmin, &st->T_freeze);
+            for (int q = n + 1; q < n + 1 + k && q < prm->n_sweeps; ++q) st->T[q] = Tn;
         }
     }
     return events;

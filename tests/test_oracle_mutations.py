@@ -25,6 +25,15 @@ MUTATIONS = {
     # break points ln(k + xi) instead of ln(k - xi)
     "branch_sign": ("heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) - xi[top.l]);",
                     "heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) + xi[top.l]);"),
+    # adaptive branching that forgets to scale the imprint strength
+    "imprint_unscaled": ("double t = prm->imprint_t * scale, omt = 1.0 - t;",
+                         "double t = prm->imprint_t, omt = 1.0 - t;"),
+    # smoothing stencil with the end weight in the interior
+    "stencil_weight": ("double c = 1.0 - 2.0 * s, e = 1.0 - s;", "double c = 1.0 - s, e = 1.0 - s;"),
+    # self-cooling ramp running from the minimum to the mean
+    "cooling_reversed": ("return pow(cbar, 1.0 - x) * pow(cmin, x);", "return pow(cbar, x) * pow(cmin, 1.0 - x);"),
+    # smoothing renormalisation tilting the wrong way
+    "renorm_sign": ("double beta = V > 0.0 ? (B - B1) / V : 0.0;", "double beta = V > 0.0 ? (B1 - B) / V : 0.0;"),
 }
 
 
@@ -61,9 +70,12 @@ def _pins_pass(L):
     O._lib = L
     try:
         from tests import test_oracle_model as M, test_oracle_moves as V, test_oracle_branching as B
+        from tests import test_oracle_protocol as Q
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
-                  lambda: B.test_multipliers_match_enumeration(0)]
+                  lambda: B.test_multipliers_match_enumeration(0),
+                  Q.test_smoothing_worked_example, Q.test_smoothing_keeps_both_sum_rules,
+                  Q.test_self_cooling_phases, Q.test_adaptive_branching_scales_fraction_and_imprint]
         for c in checks:
             try:
                 c()
