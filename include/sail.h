@@ -45,6 +45,10 @@ extern "C" {
 #define SAIL_PREC_FP32 1   /* production path: FP32 state and residual, lazy common scale,
                               FP64 residual recomputation and chi2 */
 
+/* Temperature schedules. */
+#define SAIL_SCHEDULE_GEOMETRIC 0
+#define SAIL_SCHEDULE_SELF_COOLING 1
+
 typedef struct sail_ctx *sail_t;
 
 /* Run parameters.  sail_default_params() fills the paper's choices (Sec. 3):
@@ -81,7 +85,28 @@ typedef struct sail_params {
     int sweep_lanes;        /* FP32 moves: GPU lanes per walker, 0 = choose (8 when n_tau <= 256,
                                else 16), 8 (n_tau <= 256 only) or 16.  The choice sets the order
                                of the FP32 delta-chi2 sum, so trajectories depend on it */
-    int reserved[3];
+    /* The paper's protocol against the sawtooth instability (Sec. self-cooling, Sec. 2.5,
+     * Sec. smoothing).  All three act at the end of every full block of k sweeps, in this
+     * order: block statistics (acceptance; mean and smallest residue after the block's
+     * residual recomputation), branching, smoothing, next block's temperature. */
+    int schedule_kind;      /* SAIL_SCHEDULE_GEOMETRIC (T_start -> T_end) or SAIL_SCHEDULE_SELF_COOLING:
+                               T constant per block; block 0 at chi2_0; block b >= 1 from
+                               block b-1's mean residue cbar and smallest residue cmin:
+                               boiling (b < b_cool) T = cbar; cooling (b < b_freeze)
+                               T = cbar^(1-x) cmin^x, x = (b - b_cool + 1) / (b_freeze - b_cool);
+                               freeze-out T = T_F (T_fin / T_F)^y, y = (b - b_freeze + 1) /
+                               (n_blocks - b_freeze), T_F = cmin at its start, T_fin the end
+                               temperature (T_end_abs, else T_end chi2_0; T held at T_F if
+                               T_F <= T_fin); T_start is not used */
+    int adaptive_branching; /* 1: branching fraction and imprint strength times
+                               min(1, block acceptance / first block's acceptance) */
+    double cool_begin;      /* self-cooling: b_cool = round(cool_begin n_blocks) (0.1) */
+    double freeze_begin;    /* self-cooling: b_freeze = round(freeze_begin n_blocks) (0.5) */
+    double smooth_s;        /* 0 <= s < 0.5: three-point smoothing of every spectrum after branching,
+                               s a_{j-1} + (1-2s) a_j + s a_{j+1} (ends (1-s) a_0 + s a_1), then the
+                               tilt a_j (1 + beta (x_j - m)) restoring the second sum rule, then a
+                               full residual recomputation; 0 = off (the paper's runs use 1e-2) */
+    int reserved[2];
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */

@@ -64,6 +64,7 @@ class OrParams(ctypes.Structure):
 class OrState(ctypes.Structure):
     _fields_ = [
         ("T", ctypes.POINTER(ctypes.c_double)),
+        ("T_final", ctypes.c_double),
         ("acc_ref", ctypes.c_double),
         ("T_freeze", ctypes.c_double),
         ("acc_before", ctypes.c_int64),
@@ -106,7 +107,7 @@ def lib():
         L.or_cooling_blocks.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _ip, _ip]
         L.or_cooling_blocks.restype = None
         L.or_self_cooling.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                      ctypes.c_double, _dp]
+                                      ctypes.c_double, ctypes.c_double, _dp]
         L.or_self_cooling.restype = ctypes.c_double
         L.or_adaptive_scale.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_adaptive_scale.restype = ctypes.c_double
@@ -230,11 +231,12 @@ def cooling_blocks(n_blocks: int, cool_begin: float, freeze_begin: float):
 
 
 def self_cooling(b: int, n_blocks: int, b_cool: int, b_freeze: int, cbar: float, cmin: float,
-                 T_freeze: float = -1.0):
-    """Temperature of block b >= 1 from the previous block's mean and smallest residues;
-    returns (T, T_freeze after the call)."""
+                 T_final: float, T_freeze: float = -1.0):
+    """Temperature of block b >= 1 from the previous block's mean and smallest residues and
+    the schedule's end temperature; returns (T, T_freeze after the call)."""
     tf = np.array([T_freeze], dtype=np.float64)
-    T = lib().or_self_cooling(int(b), int(n_blocks), int(b_cool), int(b_freeze), float(cbar), float(cmin), _p(tf))
+    T = lib().or_self_cooling(int(b), int(n_blocks), int(b_cool), int(b_freeze), float(cbar), float(cmin),
+                              float(T_final), _p(tf))
     return T, float(tf[0])
 
 
@@ -308,7 +310,7 @@ class Anneal:
         # the temperature of every sweep (self-cooling fills each block's entries as it gets there)
         self.T = np.zeros(max(schedule.n_sweeps, 1))
         lib().or_init_temperatures(ctypes.byref(self._c), self.chi2_0, _p(self.T))
-        self._st = OrState(_p(self.T), -1.0, -1.0, 0)
+        self._st = OrState(_p(self.T), self.chi2_0 * schedule.T_end, -1.0, -1.0, 0)
 
     def temperature(self, n: int) -> float:
         return float(self.T[n])

@@ -31,7 +31,8 @@
  *     branching draw xi, key = the 64-bit seed;
  *   - self-cooling (Sec. self-cooling): T constant per block; boil at the
  *     population's mean residue, a geometric ramp to its smallest residue, then
- *     a freeze-out linear in the blocks left (or_self_cooling);
+ *     a freeze-out lowering T by a constant proportion per block to the
+ *     schedule's end temperature (or_self_cooling);
  *   - adaptive branching (Sec. 2.5): fraction and imprint strength times
  *     min(1, acceptance / first block's acceptance);
  *   - smoothing (Sec. smoothing) after branching, its second-sum-rule
@@ -331,6 +332,7 @@ typedef struct {
 /* What the anneal carries from block to block besides the walkers. */
 typedef struct {
     double *T;             /* [n_sweeps] absolute temperature of every sweep */
+    double T_final;        /* self-cooling: temperature the freeze-out ends at, T_end chi2_0 */
     double acc_ref;        /* acceptance of the first block (adaptive branching); < 0 until known */
     double T_freeze;       /* self-cooling: chi2_min when the freeze-out began; < 0 until then */
     int64_t acc_before;    /* accepted moves of all walkers before the current block */
@@ -350,9 +352,11 @@ double or_temperature(const or_params *prm, int n, double chi2_0) {
  *   boiling,    b < b_cool:            T = cbar;
  *   cooling,    b_cool <= b < b_freeze: T = cbar^(1 - x) cmin^x,
  *               x = (b - b_cool + 1) / (b_freeze - b_cool), reaching cmin;
- *   freeze-out, b >= b_freeze:         T = T_F (n_blocks - b) / (n_blocks - b_freeze + 1),
- *               T_F = cmin at the first freeze-out block: below the smallest
- *               residue and lowered in proportion to the steps taken. */
+ *   freeze-out, b >= b_freeze:         T = T_F (T_final / T_F)^y,
+ *               y = (b - b_freeze + 1) / (n_blocks - b_freeze): from below
+ *               T_F = cmin at the first freeze-out block, lowered by the same
+ *               proportion every block, to the schedule's end temperature
+ *               T_final at the last block (held at T_F if T_F <= T_final). */
 void or_cooling_blocks(int n_blocks, double cool_begin, double freeze_begin, int *b_cool, int *b_freeze) {
     int bc = (int)floor(cool_begin * (double)n_blocks + 0.5);
     int bf = (int)floor(freeze_begin * (double)n_blocks + 0.5);
@@ -364,14 +368,17 @@ void or_cooling_blocks(int n_blocks, double cool_begin, double freeze_begin, int
     *b_freeze = bf;
 }
 
-double or_self_cooling(int b, int n_blocks, int b_cool, int b_freeze, double cbar, double cmin, double *T_freeze) {
+double or_self_cooling(int b, int n_blocks, int b_cool, int b_freeze, double cbar, double cmin, double T_final,
+                       double *T_freeze) {
     if (b < b_cool) return cbar;
     if (b < b_freeze) {
         double x = (double)(b - b_cool + 1) / (double)(b_freeze - b_cool);
         return pow(cbar, 1.0 - x) * pow(cmin, x);
     }
     if (*T_freeze < 0.0) *T_freeze = cmin;
-    return *T_freeze * (double)(n_blocks - b) / (double)(n_blocks - b_freeze + 1);
+    if (!(*T_freeze > T_final)) return *T_freeze;
+    double y = (double)(b - b_freeze + 1) / (double)(n_blocks - b_freeze);
+    return *T_freeze * pow(T_final / *T_freeze, y);
 }
 
 /* Fills the temperature table: the whole geometric schedule, or block 0 of the
@@ -576,7 +583,7 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
             int n_blocks = (prm->n_sweeps + k - 1) / k, bc, bf;
             or_cooling_blocks(n_blocks, prm->cool_begin, prm->freeze_begin, &bc, &bf);
             int b_next = (n + 1) / k;
-            double Tn = or_self_cooling(b_next, n_blocks, bc, bf, cbar, cmin, &st->T_freeze);
+            double Tn = or_self_cooling(b_next, n_blocks, bc, bf, cbar, cmin, st->T_final, &st->T_freeze);
             for (int q = n + 1; q < n + 1 + k && q < prm->n_sweeps; ++q) st->T[q] = Tn;
         }
     }

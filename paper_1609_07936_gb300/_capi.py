@@ -27,6 +27,8 @@ SAIL_ESTATE = -4
 SAIL_ETIMEOUT = -5
 RESYNC_FP32 = 0
 RESYNC_TENSOR = 1
+SCHEDULE_GEOMETRIC = 0
+SCHEDULE_SELF_COOLING = 1
 PREC_FP64 = 0
 PREC_FP32 = 1
 
@@ -51,7 +53,9 @@ class CParams(ctypes.Structure):
         ("y_m", ctypes.c_double), ("y_min", ctypes.c_double), ("A", ctypes.c_double), ("B", ctypes.c_double),
         ("avg_chi2_factor", ctypes.c_double), ("target_chi2", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
-        ("wait_test", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("reserved", ctypes.c_int * 3),
+        ("wait_test", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("schedule_kind", ctypes.c_int),
+        ("adaptive_branching", ctypes.c_int), ("cool_begin", ctypes.c_double), ("freeze_begin", ctypes.c_double),
+        ("smooth_s", ctypes.c_double), ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -194,6 +198,11 @@ class Params:
     resync_kind: int = 0
     wait_test: int = 0
     sweep_lanes: int = 0
+    schedule_kind: int = 0
+    adaptive_branching: bool = False
+    cool_begin: float = 0.1
+    freeze_begin: float = 0.5
+    smooth_s: float = 0.0
 
     def c(self) -> CParams:
         p = CParams()

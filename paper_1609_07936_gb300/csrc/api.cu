@@ -162,6 +162,12 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (p->sweep_lanes != 0 && p->sweep_lanes != 8 && p->sweep_lanes != 16)
         return fail(SAIL_EINVAL, "sweep_lanes must be 0, 8 or 16");
     if (p->sweep_lanes == 8 && n_tau > 256) return fail(SAIL_EINVAL, "sweep_lanes = 8 needs n_tau <= 256");
+    if (p->schedule_kind != SAIL_SCHEDULE_GEOMETRIC && p->schedule_kind != SAIL_SCHEDULE_SELF_COOLING)
+        return fail(SAIL_EINVAL, "unknown schedule_kind %d", p->schedule_kind);
+    if (p->adaptive_branching != 0 && p->adaptive_branching != 1) return fail(SAIL_EINVAL, "adaptive_branching must be 0 or 1");
+    if (!std::isfinite(p->cool_begin) || !std::isfinite(p->freeze_begin))
+        return fail(SAIL_EINVAL, "cool_begin and freeze_begin must be finite");
+    if (!(p->smooth_s >= 0.0 && p->smooth_s < 0.5)) return fail(SAIL_EINVAL, "smooth_s must be in [0, 0.5)");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -184,6 +190,11 @@ struct sail_ctx {
     int sweeps_done, blocks_done, events;
     long long launches, moves;
     unsigned long long acc_seen, pos_seen;
+    // protocol against the sawtooth instability (self-cooling, adaptive branching)
+    unsigned long long acc_before;  // accepted moves of all walkers before the current block
+    double acc_ref;          // acceptance of the first block (< 0 until known)
+    double T_freeze;         // smallest residue when the freeze-out began (< 0 until then)
+    std::vector<double> chi2_host;
     int *status;             // device status word: nonzero after a timed-out device wait
     bool converged;          // chi2 of the averaged spectrum reached target_chi2
     double chi2_of_mean;
@@ -256,6 +267,11 @@ void sail_default_params(sail_params *p) {
     p->target_chi2 = 0.0;
     p->seed = 0;
     p->trace = 0;
+    p->schedule_kind = SAIL_SCHEDULE_GEOMETRIC;
+    p->adaptive_branching = 0;
+    p->cool_begin = 0.1;
+    p->freeze_begin = 0.5;
+    p->smooth_s = 0.0;
 }
 
 const char *sail_last_error(void) { return g_err.c_str(); }
@@ -387,10 +403,15 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         R0[i] = F64[i] - model;
         chi2_0 += R0[i] * R0[i];
     }
-    // geometric temperature schedule in units of chi2_0
+    // temperature of every sweep: the geometric schedule in units of chi2_0, or block 0 of the
+    // self-cooling one at chi2_0 (later blocks are set as the anneal reaches them)
     std::vector<double> T(p->n_sweeps);
     const double T_end_rel = p->T_end_abs > 0 ? p->T_end_abs / chi2_0 : p->T_end;
     for (int n = 0; n < p->n_sweeps; ++n) {
+        if (p->schedule_kind == SAIL_SCHEDULE_SELF_COOLING) {
+            T[n] = n < p->sweeps_per_block ? chi2_0 : NAN;
+            continue;
+        }
         const double t = p->n_sweeps > 1 ? (double)n / (double)(p->n_sweeps - 1) : 0.0;
         T[n] = chi2_0 * (p->T_start * std::pow(T_end_rel / p->T_start, t));
     }
@@ -411,6 +432,9 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     h->ws_bytes = ws_bytes;
     h->L = L;
     h->T = T;
+    h->acc_before = 0;
+    h->acc_ref = -1.0;
+    h->T_freeze = -1.0;
     char *ws = h->ws;
     DevProblem &P = h->P;
     P.n_tau = n_tau;
@@ -608,6 +632,30 @@ int segment_done(sail_ctx *h, int n, int next) {
 }
 
 // branching and statistics at the block end; the read-backs are queued, not waited for
+// Self-cooling schedule (Sec. self-cooling): T of block b >= 1 from block b-1's mean residue
+// cbar and smallest residue cmin (sail_params.schedule_kind documents the phases).
+double self_cooling_T(int b, int n_blocks, int b_cool, int b_freeze, double cbar, double cmin, double T_final,
+                      double *T_freeze) {
+    if (b < b_cool) return cbar;
+    if (b < b_freeze) {
+        const double x = (double)(b - b_cool + 1) / (double)(b_freeze - b_cool);
+        return std::pow(cbar, 1.0 - x) * std::pow(cmin, x);
+    }
+    if (*T_freeze < 0.0) *T_freeze = cmin;
+    if (!(*T_freeze > T_final)) return *T_freeze;
+    const double y = (double)(b - b_freeze + 1) / (double)(n_blocks - b_freeze);
+    return *T_freeze * std::pow(T_final / *T_freeze, y);
+}
+
+void cooling_blocks(int n_blocks, double cool_begin, double freeze_begin, int *b_cool, int *b_freeze) {
+    int bc = (int)std::floor(cool_begin * (double)n_blocks + 0.5);
+    int bf = (int)std::floor(freeze_begin * (double)n_blocks + 0.5);
+    bc = std::min(std::max(bc, 0), n_blocks);
+    bf = std::min(std::max(bf, bc), n_blocks);
+    *b_cool = bc;
+    *b_freeze = bf;
+}
+
 int block_tail(sail_ctx *h, BlockPending &b) {
     const sail_params &p = h->prm;
     const int k = p.sweeps_per_block;
@@ -616,16 +664,71 @@ int block_tail(sail_ctx *h, BlockPending &b) {
     b.delta = 0.0;
     b.zeros = 0;
     b.dev_status = 0;
-    b.branched = p.branching && p.n_walkers > 1 && (b.block_end % k) == 0;
+    const bool full = (b.block_end % k) == 0;
+    b.branched = p.branching && p.n_walkers > 1 && full;
+    // the protocol against the sawtooth instability: the finished block's acceptance and
+    // residue statistics (after its residual recomputation, before branching)
+    const bool cooling = p.schedule_kind == SAIL_SCHEDULE_SELF_COOLING;
+    double scale = 1.0, cbar = 0.0, cmin = 0.0;
+    if (full && (cooling || p.adaptive_branching)) {
+        BlockCounters bc{};
+        cudaError_t e = launch_block_stats(h->P, h->S, (BlockCounters *)(h->ws + h->L.counters), st);
+        h->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(e, "stats launch");
+        SAIL_CUDA(cudaMemcpyAsync(&bc, h->ws + h->L.counters, sizeof bc, cudaMemcpyDeviceToHost, st), "stats D2H");
+        if (cooling) {
+            h->chi2_host.resize(p.n_walkers);
+            SAIL_CUDA(cudaMemcpyAsync(h->chi2_host.data(), h->S.chi2, (size_t)p.n_walkers * 8, cudaMemcpyDeviceToHost, st),
+                      "chi2 D2H");
+        }
+        SAIL_CUDA(cudaStreamSynchronize(st), "block statistics");
+        const double acc = (double)(bc.acc - h->acc_before) / ((double)k * (double)p.n_walkers * (double)h->n_omega);
+        h->acc_before = bc.acc;
+        if (p.adaptive_branching) {
+            if (h->acc_ref < 0.0) h->acc_ref = acc;
+            scale = (h->acc_ref > 0.0 && acc < h->acc_ref) ? acc / h->acc_ref : 1.0;
+        }
+        if (cooling) {
+            cmin = h->chi2_host[0];
+            for (int w = 0; w < p.n_walkers; ++w) {
+                cbar += h->chi2_host[w];
+                if (h->chi2_host[w] < cmin) cmin = h->chi2_host[w];
+            }
+            cbar /= (double)p.n_walkers;
+        }
+    }
     if (b.branched) {
         int l = 0;
         const int tk = timed_begin(h);
-        const cudaError_t e = launch_branch(h->P, h->S, h->Bs, p.precision, b.block_end / k - 1, p.branch_fraction,
-                                            p.imprint_t, h->events, st, &l);
+        const cudaError_t e = launch_branch(h->P, h->S, h->Bs, p.precision, b.block_end / k - 1,
+                                            p.branch_fraction * scale, p.imprint_t * scale, h->events, st, &l);
         timed_end(h, tk, kBranch);
         h->launches += l;
         if (e != cudaSuccess) return cuda_fail(e, "branch launch");
         h->events += 1;
+    }
+    if (full && p.smooth_s > 0.0) {
+        // smoothing (Sec. smoothing), then every walker's residual and chi2 anew
+        int l = 0;
+        const int tk = timed_begin(h);
+        cudaError_t e = launch_smooth(h->P, h->S, p.precision, p.smooth_s, st);
+        if (e == cudaSuccess)
+            e = launch_resync(h->P, h->S, p.precision, p.precision == SAIL_PREC_FP32 ? 1 : 0, p.resync_kind, h->status,
+                              st, &l);
+        timed_end(h, tk, kBranch);
+        h->launches += 1 + l;
+        if (e != cudaSuccess) return cuda_fail(e, "smoothing launch");
+    }
+    if (full && cooling && b.block_end < p.n_sweeps) {
+        const int n_blocks = (p.n_sweeps + k - 1) / k;
+        int bcool = 0, bfreeze = 0;
+        cooling_blocks(n_blocks, p.cool_begin, p.freeze_begin, &bcool, &bfreeze);
+        const double T_final = p.T_end_abs > 0 ? p.T_end_abs : p.T_end * h->chi2_0;
+        const double Tn = self_cooling_T(b.block_end / k, n_blocks, bcool, bfreeze, cbar, cmin, T_final, &h->T_freeze);
+        const int q1 = std::min(b.block_end + k, p.n_sweeps);
+        for (int q = b.block_end; q < q1; ++q) h->T[q] = Tn;
+        SAIL_CUDA(cudaMemcpyAsync(h->ws + h->L.Tsweep + (size_t)b.block_end * 8, h->T.data() + b.block_end,
+                                  (size_t)(q1 - b.block_end) * 8, cudaMemcpyHostToDevice, st), "temperature H2D");
     }
     const cudaError_t e = launch_block_stats(h->P, h->S, (BlockCounters *)(h->ws + h->L.counters), st);
     h->launches += 1;

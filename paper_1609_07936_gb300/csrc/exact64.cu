@@ -755,6 +755,52 @@ cudaError_t launch_sweep64_c(const DevProblem &P, const DevState &S, int n0, int
     return cudaGetLastError();
 }
 
+
+// Smoothing of one spectrum (Sec. smoothing), in the oracle's order of operations: the
+// three-point stencil of strength s from the old values, ends (1 - s) a_0 + s a_1 and
+// (1 - s) a_{N-1} + s a_{N-2}; then sums in bin order and the tilt a_j (1 + beta (x_j - m)),
+// m = B'/A', beta = (B - B') / sum_j a_j (x_j - m)^2, which restores sum_j a_j x_j = B and
+// keeps sum_j a_j (skipped when |beta| max_j |x_j - m| >= 1/2).  FP64 arithmetic; E is the
+// element type of the state.
+template <typename E>
+__device__ void smooth_one(E *a, int N, const double *x, double B, double s) {
+    const double c = 1.0 - 2.0 * s, e = 1.0 - s;
+    double prev = (double)a[0];
+    a[0] = (E)(e * (double)a[0] + s * (double)a[1]);
+    for (int j = 1; j < N - 1; ++j) {
+        const double cur = (double)a[j];
+        a[j] = (E)(s * prev + c * cur + s * (double)a[j + 1]);
+        prev = cur;
+    }
+    a[N - 1] = (E)(e * (double)a[N - 1] + s * prev);
+    double A1 = 0.0, B1 = 0.0;
+    for (int j = 0; j < N; ++j) {
+        const double v = (double)a[j];
+        A1 += v;
+        B1 += v * x[j];
+    }
+    if (!(A1 > 0.0)) return;
+    const double m = B1 / A1;
+    double V = 0.0;
+    for (int j = 0; j < N; ++j) {
+        const double d = x[j] - m;
+        V += (double)a[j] * d * d;
+    }
+    double beta = V > 0.0 ? (B - B1) / V : 0.0;
+    const double span = fabs(x[0] - m) > fabs(x[N - 1] - m) ? fabs(x[0] - m) : fabs(x[N - 1] - m);
+    if (!(fabs(beta) * span < 0.5)) beta = 0.0;
+    for (int j = 0; j < N; ++j) a[j] = (E)((double)a[j] * (1.0 + beta * (x[j] - m)));
+}
+
+__global__ void __launch_bounds__(128) smooth_kernel(DevProblem P, DevState S, int precision, double s) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= P.n_walkers) return;
+    if (precision == 0)
+        smooth_one(S.a64 + (size_t)w * P.n_omega, P.n_omega, P.x64, P.B, s);
+    else
+        smooth_one(S.b32 + (size_t)w * P.n_omega, P.n_omega, P.x64, P.B, s);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -813,6 +859,11 @@ cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchSc
     if (e != cudaSuccess) return e;
     imprint_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, B, precision, imprint_t);
     *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_smooth(const DevProblem &P, const DevState &S, int precision, double s, cudaStream_t st) {
+    smooth_kernel<<<(P.n_walkers + 127) / 128, 128, 0, st>>>(P, S, precision, s);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,10 @@ cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);
+// Smoothing (Sec. smoothing) of every walker's spectrum with strength s and the tilt that
+// restores the second sum rule; one thread per walker, sums in bin order (FP64 arithmetic for
+// either state precision).  The residuals are stale afterwards.
+cudaError_t launch_smooth(const DevProblem &P, const DevState &S, int precision, double s, cudaStream_t st);
 cudaError_t launch_block_stats(const DevProblem &P, const DevState &S, BlockCounters *out,
                                cudaStream_t st);
 cudaError_t launch_average(const DevProblem &P, const DevState &S, int precision, double factor,

@@ -37,10 +37,30 @@ def test_defaults_are_the_papers():
     assert math.isnan(p.A) and math.isnan(p.B)
 
 
-def test_struct_sizes_match_the_header():
-    # sail_params: 6 ints, 13 doubles, one uint64, 8 ints
-    assert ctypes.sizeof(_capi.CParams) == 6 * 4 + 13 * 8 + 8 + 8 * 4
-    assert ctypes.sizeof(_capi.CBlockStats) == 8 + 6 * 8 + 8
+def _c_layout(struct, fields):
+    """sizeof and field offsets of a header struct, as the C compiler lays it out."""
+    import subprocess
+    import tempfile
+    td = tempfile.mkdtemp()
+    src = os.path.join(td, "layout.c")
+    body = "".join(f'    printf("%zu\\n", offsetof({struct}, {f}));\n' for f in fields)
+    open(src, "w").write('#include <stddef.h>\n#include <stdio.h>\n#include "sail.h"\n'
+                         f'int main(void) {{\n    printf("%zu\\n", sizeof({struct}));\n{body}    return 0;\n}}\n')
+    exe = os.path.join(td, "layout")
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", exe, src])
+    out = [int(v) for v in subprocess.check_output([exe]).split()]
+    return out[0], out[1:]
+
+
+@pytest.mark.parametrize("struct,cls", [("sail_params", "CParams"), ("sail_block_stats", "CBlockStats"),
+                                        ("sail_info", "CInfo"), ("sail_problem", "CProblem")])
+def test_struct_layouts_match_the_header(struct, cls):
+    """Every ctypes mirror has the C compiler's size and field offsets."""
+    C = getattr(_capi, cls)
+    names = [f[0] for f in C._fields_]
+    size, offs = _c_layout(struct, names)
+    assert ctypes.sizeof(C) == size
+    assert [getattr(C, n).offset for n in names] == offs
 
 
 def test_workspace_size_and_refusals():

@@ -76,20 +76,25 @@ def test_cooling_block_split():
 
 def test_self_cooling_phases():
     nb, bc, bf = 20, 4, 10
-    cbar, cmin = 900.0, 100.0
+    cbar, cmin, Tf = 900.0, 100.0, 1e-3
     # boiling: the population's mean residue
     for b in range(1, bc):
-        assert O.self_cooling(b, nb, bc, bf, cbar, cmin)[0] == cbar
+        assert O.self_cooling(b, nb, bc, bf, cbar, cmin, Tf)[0] == cbar
     # cooling: geometric from the mean towards the minimum; x = 1/2 at b = bc + 2
-    assert O.self_cooling(bc + 2, nb, bc, bf, cbar, cmin)[0] == pytest.approx(np.sqrt(cbar * cmin), rel=1e-14)
-    assert O.self_cooling(bf - 1, nb, bc, bf, cbar, cmin)[0] == cmin
-    Ts = [O.self_cooling(b, nb, bc, bf, cbar, cmin)[0] for b in range(bc, bf)]
+    assert O.self_cooling(bc + 2, nb, bc, bf, cbar, cmin, Tf)[0] == pytest.approx(np.sqrt(cbar * cmin), rel=1e-14)
+    assert O.self_cooling(bf - 1, nb, bc, bf, cbar, cmin, Tf)[0] == cmin
+    Ts = [O.self_cooling(b, nb, bc, bf, cbar, cmin, Tf)[0] for b in range(bc, bf)]
     assert all(t1 > t2 for t1, t2 in zip(Ts, Ts[1:]))
-    # freeze-out: below the minimum at its start, then linear in the blocks left
-    T, tf = O.self_cooling(bf, nb, bc, bf, cbar, cmin)
-    assert tf == cmin and T == pytest.approx(cmin * (nb - bf) / (nb - bf + 1), rel=1e-15)
-    T_last, tf2 = O.self_cooling(nb - 1, nb, bc, bf, cbar, 1.0, tf)   # later minima do not move T_F
-    assert tf2 == cmin and T_last == pytest.approx(cmin / (nb - bf + 1), rel=1e-15)
+    # freeze-out: from the minimum down by a constant factor per block to T_final at the end
+    T, tf = O.self_cooling(bf, nb, bc, bf, cbar, cmin, Tf)
+    ratio = (Tf / cmin) ** (1.0 / (nb - bf))
+    assert tf == cmin and T == pytest.approx(cmin * ratio, rel=1e-13)
+    Tz = [O.self_cooling(b, nb, bc, bf, cbar, 5.0, Tf, tf)[0] for b in range(bf, nb)]  # later minima do not move T_F
+    np.testing.assert_allclose(np.array(Tz[1:]) / np.array(Tz[:-1]), ratio, rtol=1e-12)
+    assert Tz[-1] == pytest.approx(Tf, rel=1e-13)
+    # a population already colder than the end temperature is held where it is
+    assert O.self_cooling(bf, nb, bc, bf, cbar, 1e-4, Tf)[0] == 1e-4
+    assert O.self_cooling(bf, nb, bc, bf, cbar, 0.0, Tf)[0] == 0.0
 
 
 def test_self_cooling_anneal_follows_population_statistics():
@@ -110,7 +115,7 @@ def test_self_cooling_anneal_follows_population_statistics():
         for c in an.chi2:
             cbar += float(c)
         cbar /= len(an.chi2)
-        T, tf = O.self_cooling(b + 1, nblocks, bc, bf, cbar, float(an.chi2.min()), tf)
+        T, tf = O.self_cooling(b + 1, nblocks, bc, bf, cbar, float(an.chi2.min()), an.chi2_0 * s.T_end, tf)
         assert np.all(an.T[(b + 1) * k:(b + 2) * k] == T)
     an.run()
     assert an.T[-1] < an.T[bf * k - 1]
