@@ -58,6 +58,8 @@ class OrParams(ctypes.Structure):
         ("cool_begin", ctypes.c_double),
         ("freeze_begin", ctypes.c_double),
         ("smooth_s", ctypes.c_double),
+        ("walk_len", ctypes.c_int),
+        ("walk_uniform", ctypes.c_double),
     ]
 
 
@@ -113,6 +115,9 @@ def lib():
         L.or_adaptive_scale.restype = ctypes.c_double
         L.or_smooth.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
         L.or_smooth.restype = None
+        L.or_move_bins.argtypes = [ctypes.POINTER(OrParams), ctypes.c_int, _dp, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip]
+        L.or_move_bins.restype = None
         L.or_anneal.restype = ctypes.c_int
         L.or_average.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_average.restype = ctypes.c_int
@@ -245,6 +250,20 @@ def adaptive_scale(acc: float, acc_ref: float) -> float:
     return lib().or_adaptive_scale(float(acc), float(acc_ref))
 
 
+def move_bins(a, w0: int, w1: int, mv: int, n: int, w: int, walk_len: int = 0, walk_uniform: float = 0.0,
+              seed: int = 0):
+    """Bins (p, s) of move mv of sweep n of walker w with spectrum a: the start words w0, w1
+    and, for walk_len > 0, the index walk of Sec. 2.3."""
+    a = _f64(a)
+    sched = Schedule(walk_len=walk_len, walk_uniform=walk_uniform, seed=seed)
+    c = sched.c()
+    p = np.zeros(1, dtype=np.int32)
+    s = np.zeros(1, dtype=np.int32)
+    lib().or_move_bins(ctypes.byref(c), a.size, _p(a), int(w0), int(w1), int(mv), int(n), int(w), _p(p, _ip),
+                       _p(s, _ip))
+    return int(p[0]), int(s[0])
+
+
 def xi_for_block(seed: int, block: int, n_walkers: int) -> np.ndarray:
     """The branching draws xi_l of one block, Philox counter (l, block, 0, 1)."""
     key = np.array([seed & 0xFFFFFFFF, seed >> 32], dtype=np.uint32)
@@ -277,13 +296,15 @@ class Schedule:
     cool_begin: float = 0.1
     freeze_begin: float = 0.5
     smooth_s: float = 0.0
+    walk_len: int = 0            # steps of the index walk (Sec. 2.3)
+    walk_uniform: float = 0.0    # probability an index skips its walk
 
     def c(self) -> OrParams:
         return OrParams(self.n_sweeps, self.sweeps_per_block, self.resync_every, int(self.branching),
                         self.T_start, self.T_end, self.branch_fraction, self.imprint_t,
                         self.move_scale, self.y_p, self.y_m, self.y_min, self.seed,
                         int(self.schedule_kind), int(self.adaptive), self.cool_begin, self.freeze_begin,
-                        self.smooth_s)
+                        self.smooth_s, int(self.walk_len), self.walk_uniform)
 
 
 class Anneal:

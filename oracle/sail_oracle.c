@@ -23,7 +23,8 @@
  *     rules, a_j proportional to exp(-lambda x_j);
  *   - the move amplitude eps = 1 - r is uniform on (-y d, y d);
  *   - p is uniform on the bins and s uniform on the other bins (zero-length
- *     index walk, Sec. 2.3);
+ *     index walk, Sec. 2.3); an index walk of L > 0 steps is an independence
+ *     walk with law a_j / A, s walking on the bins other than p (or_move_bins);
  *   - the branching weight is w = exp[-Delta (chi2 - P_r)] (the printed
  *     formula applies the weight to P(chi2), read as chi2);
  *   - random numbers come from Philox4x32-10 (Salmon et al., SC'11), counter
@@ -327,6 +328,8 @@ typedef struct {
     double cool_begin;     /* self-cooling: fraction of the blocks boiled before the ramp */
     double freeze_begin;   /* self-cooling: fraction of the blocks after which the freeze-out starts */
     double smooth_s;       /* smoothing strength s (Sec. smoothing); 0: no smoothing */
+    int walk_len;          /* L: steps of the index walk (Sec. 2.3); 0: uniform bins */
+    double walk_uniform;   /* rho: probability that an index skips its walk (uniform admixture) */
 } or_params;
 
 /* What the anneal carries from block to block besides the walkers. */
@@ -442,6 +445,47 @@ static uint64_t fnv_step(uint64_t h, unsigned code) {
     return h;
 }
 
+/* Bin choice of a move, Sec. 2.3 (selection of update frequencies).  With a
+ * zero-length walk p is uniform on the bins and s uniform on the others.
+ * Reading for L > 0: each index takes L steps of an independence walk whose
+ * stationary law is a_j / A: from the current bin j, propose j' uniform and move
+ * there when u a_j <= a_j' (probability min(1, a_j'/a_j)).  p walks first from
+ * its uniform start; s then starts uniform on the bins other than the final p
+ * and walks with proposals drawn on those bins.  Each index skips its walk with
+ * probability rho (the uniform admixture).  Words: starts from words 0 and 1 of
+ * the move's counter (mv, n, w, 0); step t = 1..L from counter (mv, n, w, 1 + t)
+ * as (proposal of p, acceptance of p, proposal of s, acceptance of s); the two
+ * admixture uniforms from words 0 and 1 of counter (mv, n, w, 2 + L). */
+void or_move_bins(const or_params *prm, int n_omega, const double *a, uint32_t w0, uint32_t w1, int mv, int n, int w,
+                  int *p_out, int *s_out) {
+    int L = prm->walk_len;
+    int p = (int)(((uint64_t)w0 * (uint64_t)n_omega) >> 32);
+    int walk_p = 0, walk_s = 0;
+    if (L > 0) {
+        uint32_t mix[4];
+        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(2 + L), mix);
+        walk_p = !(unit(mix[0]) < prm->walk_uniform);
+        walk_s = !(unit(mix[1]) < prm->walk_uniform);
+    }
+    for (int t = 1; t <= L && walk_p; ++t) {
+        uint32_t r[4];
+        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(1 + t), r);
+        int j = (int)(((uint64_t)r[0] * (uint64_t)n_omega) >> 32);
+        if (unit(r[1]) * a[p] <= a[j]) p = j;
+    }
+    int s = (int)(((uint64_t)w1 * (uint64_t)(n_omega - 1)) >> 32);
+    if (s >= p) s += 1;
+    for (int t = 1; t <= L && walk_s; ++t) {
+        uint32_t r[4];
+        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(1 + t), r);
+        int j = (int)(((uint64_t)r[2] * (uint64_t)(n_omega - 1)) >> 32);
+        if (j >= p) j += 1;
+        if (unit(r[3]) * a[s] <= a[j]) s = j;
+    }
+    *p_out = p;
+    *s_out = s;
+}
+
 /* One sweep (N_omega proposals) of walker w at sweep index n. */
 static void sweep_walker(int n_tau, int n_omega, const double *Khat, const double *Fhat,
                          const double *x, double A, double B, const or_params *prm, double T,
@@ -453,10 +497,8 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
     for (int mv = 0; mv < n_omega; ++mv) {
         uint32_t rnd[4];
         draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u, rnd);
-        /* Sec. 2.3 with a zero-length walk: p uniform, s uniform on the others. */
-        int p = (int)(((uint64_t)rnd[0] * (uint64_t)n_omega) >> 32);
-        int s = (int)(((uint64_t)rnd[1] * (uint64_t)(n_omega - 1)) >> 32);
-        if (s >= p) s += 1;
+        int p, s;
+        or_move_bins(prm, n_omega, a, rnd[0], rnd[1], mv, n, w, &p, &s);
         double eps = (y * dmove) * (2.0 * unit(rnd[2]) - 1.0);
         double u = unit(rnd[3]);
         double D, ap, as;

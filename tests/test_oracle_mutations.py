@@ -34,6 +34,10 @@ MUTATIONS = {
     "cooling_reversed": ("return pow(cbar, 1.0 - x) * pow(cmin, x);", "return pow(cbar, x) * pow(cmin, 1.0 - x);"),
     # smoothing renormalisation tilting the wrong way
     "renorm_sign": ("double beta = V > 0.0 ? (B - B1) / V : 0.0;", "double beta = V > 0.0 ? (B1 - B) / V : 0.0;"),
+    # index walk accepting by the inverse ratio (law a_j^-1 instead of a_j)
+    "walk_ratio": ("if (unit(r[1]) * a[p] <= a[j]) p = j;", "if (unit(r[1]) * a[j] <= a[p]) p = j;"),
+    # s walk whose proposals may land on p
+    "walk_skip": ("        if (j >= p) j += 1;\n        if (unit(r[3])", "        if (unit(r[3])"),
 }
 
 
@@ -71,11 +75,13 @@ def _pins_pass(L):
     try:
         from tests import test_oracle_model as M, test_oracle_moves as V, test_oracle_branching as B
         from tests import test_oracle_protocol as Q
+        from tests import test_oracle_walk as Wk
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
                   lambda: B.test_multipliers_match_enumeration(0),
                   Q.test_smoothing_worked_example, Q.test_smoothing_keeps_both_sum_rules,
-                  Q.test_self_cooling_phases, Q.test_adaptive_branching_scales_fraction_and_imprint]
+                  Q.test_self_cooling_phases, Q.test_adaptive_branching_scales_fraction_and_imprint,
+                  lambda: Wk.test_walk_law_matches_the_matrix_power(3, 0.0)]
         for c in checks:
             try:
                 c()
