@@ -42,13 +42,13 @@ RESYNC_KIND = 1    # residual recomputation on the tensor cores (tcgen05, TF32 x
 
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
-               sweep_lanes: int = 0):
+               sweep_lanes: int = 0, index_walk: int = 0):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
-                      resync_kind=resync_kind, sweep_lanes=sweep_lanes)
+                      resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk)
     return P, prm
 
 
@@ -191,14 +191,14 @@ def run_gpu(args, rank, world, local_rank):
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
     P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
-                        sweep_lanes=args.sweep_lanes)
+                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
     del warm
 
     P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
-                        sweep_lanes=args.sweep_lanes)
+                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -237,7 +237,7 @@ def run_gpu(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
-                              sweep_lanes=args.sweep_lanes)
+                              sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -269,7 +269,7 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
+            "config": {"workload": WORKLOAD + (f", index walk of {args.index_walk} steps" if args.index_walk else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
             "roofline": {"kernel": "sweep_fp32", "bound": "smem", "achieved": achieved,
@@ -453,6 +453,8 @@ def main():
     ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
     ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1],
                     help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05)")
+    ap.add_argument("--index-walk", type=int, default=0, choices=range(8),
+                    help="steps of the index walk choosing a move's bins (0: uniform bins, the paper's runs)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
                     help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,

@@ -106,6 +106,14 @@ typedef struct sail_params {
                                s a_{j-1} + (1-2s) a_j + s a_{j+1} (ends (1-s) a_0 + s a_1), then the
                                tilt a_j (1 + beta (x_j - m)) restoring the second sum rule, then a
                                full residual recomputation; 0 = off (the paper's runs use 1e-2) */
+    int index_walk_len;     /* L in [0, 7]: steps of the index walk choosing p and s (Sec. 2.3);
+                               0 = p uniform, s uniform on the other bins.  L > 0: each index
+                               walks from that start, proposing a uniform bin j' and moving
+                               when u a_j <= a_j' (stationary law a_j / A); s walks on the bins
+                               other than the final p.  Words: step t from Philox counter
+                               (move, sweep, walker, 1 + t), admixture from (.., 2 + L) */
+    int reserved0;
+    double walk_uniform;    /* probability that an index skips its walk (uniform admixture) */
     int reserved[2];
 } sail_params;
 

@@ -22,6 +22,8 @@ UNITS = {
     "api.cu": [],
     "exact64.cu": ["-fmad=false"],
     "sweep_fp32.cu": [],
+    "sweep_walk.cu": [],
+    "sweep_batch.cu": [],
     "resync_fp32.cu": [],
     "resync_tc.cu": [],
     "noalloc.cu": ["-fmad=false"],

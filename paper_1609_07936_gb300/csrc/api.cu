@@ -168,6 +168,8 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!std::isfinite(p->cool_begin) || !std::isfinite(p->freeze_begin))
         return fail(SAIL_EINVAL, "cool_begin and freeze_begin must be finite");
     if (!(p->smooth_s >= 0.0 && p->smooth_s < 0.5)) return fail(SAIL_EINVAL, "smooth_s must be in [0, 0.5)");
+    if (p->index_walk_len < 0 || p->index_walk_len > 7) return fail(SAIL_EINVAL, "index_walk_len must be in [0, 7]");
+    if (!(p->walk_uniform >= 0.0 && p->walk_uniform <= 1.0)) return fail(SAIL_EINVAL, "walk_uniform must be in [0, 1]");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -464,6 +466,8 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.n_omega_pad = NOP;
     P.wait_test = p->wait_test;
     P.lanes = p->sweep_lanes != 0 ? p->sweep_lanes : (PAD <= 256 ? 8 : 16);
+    P.walk_len = p->index_walk_len;
+    P.walk_rho = p->walk_uniform;
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;

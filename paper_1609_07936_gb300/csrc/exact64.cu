@@ -53,6 +53,38 @@ __global__ void init_state_kernel(DevProblem P, DevState S, int precision, const
 //   Delta chi2 = sum_i d_i (2 R_i + d_i), summed over i ascending,
 // accepted with probability min(1, exp(-Delta chi2 / T)) (Eq. probability-density); an
 // accepted move rescales every bin by r, writes a_p', a_s' and adds d to R.
+// Bins of a move (Sec. 2.3) in the oracle's order: p from word w0, then its index walk of
+// L = P.walk_len steps (step t: Philox counter (mv, n, w, 1 + t), proposal word x, acceptance
+// word y; move when u a_p <= a_j); s from word w1 on the bins other than the final p, then its
+// walk (words z, w; proposals on the bins other than p).  Each walk is skipped with
+// probability walk_rho (words x, y of counter (mv, n, w, 2 + L)).
+__device__ void walk_bins64(const DevProblem &P, const double *a, uint32_t w0, uint32_t w1, int mv, int n, int w,
+                            uint2 key, int &p_out, int &s_out) {
+    const int NO = P.n_omega, L = P.walk_len;
+    int p = (int)(((uint64_t)w0 * (uint64_t)NO) >> 32);
+    bool walk_p = false, walk_s = false;
+    if (L > 0) {
+        const uint4 mix = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(2 + L)), key);
+        walk_p = !(unit64(mix.x) < P.walk_rho);
+        walk_s = !(unit64(mix.y) < P.walk_rho);
+    }
+    for (int t = 1; t <= L && walk_p; ++t) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(1 + t)), key);
+        const int j = (int)(((uint64_t)r.x * (uint64_t)NO) >> 32);
+        if (unit64(r.y) * a[p] <= a[j]) p = j;
+    }
+    int s = (int)(((uint64_t)w1 * (uint64_t)(NO - 1)) >> 32);
+    s += (s >= p);
+    for (int t = 1; t <= L && walk_s; ++t) {
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, (uint32_t)(1 + t)), key);
+        int j = (int)(((uint64_t)r.z * (uint64_t)(NO - 1)) >> 32);
+        j += (j >= p);
+        if (unit64(r.w) * a[s] <= a[j]) s = j;
+    }
+    p_out = p;
+    s_out = s;
+}
+
 template <int C>
 __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState S, int n0, int n1) {
     const int lane = threadIdx.x & 31;
@@ -79,7 +111,7 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
         for (int mv = 0; mv < NO; ++mv) {
             const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u), key);
             int p, s;
-            move_bins(rnd.x, rnd.y, NO, p, s);
+            walk_bins64(P, a, rnd.x, rnd.y, mv, n, w, key, p, s);
             const double eps = (y * dmove) * (2.0 * unit64(rnd.z) - 1.0);
             const double u = unit64(rnd.w);
             const double r = 1.0 - eps;

@@ -47,6 +47,8 @@ struct DevProblem {
     int tc_cols;           // tau columns per tensor-core resync block (0: the widest that fits)
     int wait_test;         // test hook: the tensor-core resync withholds its first commit
     int lanes;             // FP32 sweep: lanes per walker (8: 4 walkers per warp, n_tau <= 256; 16: 2)
+    int walk_len;          // steps of the index walk (0: uniform bins)
+    double walk_rho;       // probability that an index skips its walk
     const double *Tsweep;
 };
 
@@ -91,6 +93,9 @@ cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int sweep_
                               int sweep_end, cudaStream_t st);
 cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_begin,
                               int sweep_end, cudaStream_t st);
+// The FP32 sweep of a problem with an index walk (P.walk_len > 0); launch_sweep_fp32 calls it.
+cudaError_t launch_sweep_walk(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
+                              cudaStream_t st);
 // FP64 state: sequential FP64 recomputation.  FP32 state: optional sum-rule restoration
 // (restore != 0), then the tiled GEMM of resync_fp32.cu.
 cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,

@@ -1,0 +1,105 @@
+// Batched FP32 sweep: many inversions in one persistent launch per lane count (the move
+// loop of sweep_group.cuh).
+#include "sweep_group.cuh"
+
+namespace sail {
+
+namespace {
+
+template <int G, bool WALK>
+__device__ __forceinline__ void run_group_c(const BatchProblem &BP, int grp, const float *sm) {
+    switch (BP.P.n_tau_pad / 32) {
+        case 1: run_group<G, 1, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 2: run_group<G, 2, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 3: run_group<G, 3, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 4: run_group<G, 4, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 5: run_group<G, 5, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 6: run_group<G, 6, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 7: run_group<G, 7, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 8: run_group<G, 8, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        default:
+            if constexpr (G == 16) {
+                switch (BP.P.n_tau_pad / 32) {
+                    case 9: run_group<16, 9, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 10: run_group<16, 10, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 11: run_group<16, 11, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 12: run_group<16, 12, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 13: run_group<16, 13, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 14: run_group<16, 14, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 15: run_group<16, 15, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 16: run_group<16, 16, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    default: break;
+                }
+            }
+            break;
+    }
+}
+
+// Many inversions in one persistent launch: blocks take (problem, group range) items from a
+// queue, load the item's problem tables when the problem changes, and run one walker group per
+// warp.  One launch serves the problems of one lane count G (its register budget differs);
+// the per-walker arithmetic is that of sweep_fp32_kernel, so a walker's trajectory does not
+// depend on which block, or which other problems, share the launch.
+template <int G>
+__global__ void __launch_bounds__(sweep_threads<G>()) sweep_batch_kernel(const BatchProblem *probs,
+                                                                        const BatchItem *items, int n_items,
+                                                                        int *counter) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    __shared__ int s_item, s_loaded;
+    if (threadIdx.x == 0) s_loaded = -1;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        __syncthreads();                       // the previous item is finished with the tables
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const BatchItem I = items[it];
+        const BatchProblem &BP = probs[I.prob];
+        if (I.prob != s_loaded) {
+            load_tables(BP.P, sm);
+            __syncthreads();
+            if (threadIdx.x == 0) s_loaded = I.prob;
+        }
+        __syncthreads();
+        const int grp = I.grp_lo + warp;
+        if (grp >= I.grp_hi || BP.n0 >= BP.n1) continue;
+        if (BP.P.walk_len > 0)
+            run_group_c<G, true>(BP, grp, sm);
+        else
+            run_group_c<G, false>(BP, grp, sm);
+    }
+}
+
+}  // namespace
+
+template <int G>
+cudaError_t launch_batch_g(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                           size_t smem, int warps, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (warps > sweep_threads<G>() / 32) warps = sweep_threads<G>() / 32;
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    // persistent: as many blocks as fit on the SMs at once
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_kernel<G>, warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const int blocks = n_items < sms * per_sm ? n_items : sms * per_sm;
+    sweep_batch_kernel<G><<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                               size_t smem, int warps, int lanes, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    return lanes == 8 ? launch_batch_g<8>(d_probs, d_items, n_items, d_counter, smem, warps, st)
+                      : launch_batch_g<16>(d_probs, d_items, n_items, d_counter, smem, warps, st);
+}
+
+}  // namespace sail

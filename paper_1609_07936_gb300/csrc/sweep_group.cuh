@@ -1,0 +1,532 @@
+// The FP32 production sweep (Sec. 2.2 moves, Eq. probability-density acceptance): the device
+// code shared by the sweep translation units (sweep_fp32.cu: single-problem kernels and
+// probes; sweep_walk.cu: the kernels with an index walk; sweep_batch.cu: batched kernels).
+//
+// Kernel columns from two small tables.  Eq. (efficient-correlation-model) writes the bin
+// kernel as c_i q_i^j with q_i = e^{-dw tau_i}; so with j = 32 h + l,
+//     Khat_ij = Khat_{i,32h} * q_i^l = Qhi[h][i] * Qlo[l][i],
+// and the two tables ((N_omega/32 + 32) rows of n_tau_pad floats, 57 KB at 200 x 1000) sit in
+// shared memory.  A move reads its two columns from there: no L2 traffic, no L2 latency.
+//
+// Walker layout.  One persistent block per SM; G lanes per walker (G = 8: four walkers a warp,
+// for n_tau <= 256; G = 16: two), lane l of a walker's group holding R_i and M_i = Fhat_i - R_i
+// for its 32 / G consecutive i of every 32-tau chunk.  Each lane of a group draws the random
+// words of one of G consecutive moves at once (one Philox call) and works out that move's
+// scalars; the move loop takes them by shuffle within the group.  Delta chi2 =
+// sum_i d_i (2 R_i + d_i) is reduced by an xor butterfly over the group.
+//
+// Spectrum.  a = g b: an accepted move multiplies the common scale g by r (an unevaluated
+// pair of floats, error ~1e-14 over a launch) and writes only b_p and b_s.  When the block's
+// spectra fit in shared memory next to the tables they are staged there for the launch.  The
+// scale is folded back into b when the launch ends, so residual recomputation sees a = b.
+#pragma once
+#include <cmath>
+#include <cstdint>
+
+#include "moves.cuh"
+#include "philox.cuh"
+#include "sail_internal.cuh"
+
+namespace sail {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kThreads = 512;          // at most 16 warps per round
+
+// (hi, lo) <- (hi, lo) * r with the product's rounding error carried in lo.
+__device__ __forceinline__ void pair_scale(float &hi, float &lo, float r) {
+    const float p = hi * r;
+    const float e = fmaf(hi, r, -p);
+    const float l = fmaf(lo, r, e);
+    const float s = p + l;
+    lo = l - (s - p);
+    hi = s;
+}
+
+// The FP32 move amplitudes of Eqs. (update-delta-p/s): rgap[k] = 1 / (k dw).
+__device__ __forceinline__ void deltas(float eps, int p, int s, const float *beta, const float *rgap,
+                                       float &dp, float &ds) {
+    const int k = p - s;
+    const float inv_gap = k > 0 ? rgap[k] : -rgap[-k];   // 1 / (x_p - x_s)
+    dp = (eps * beta[s]) * inv_gap;
+    ds = -(eps * beta[p]) * inv_gap;
+}
+
+struct SweepGeom {
+    int groups_total;     // walker groups (one warp each): ceil(n_walkers / walkers per warp)
+    int groups_per_cta;
+    int warps;            // warps per block
+    int rounds;           // groups handled one after another by each warp
+    int stage_b;          // spectra staged in shared memory
+};
+
+// Loads a problem's kernel factor tables, beta and the reciprocal gaps into shared memory.
+__device__ void load_tables(const DevProblem &P, float *sm) {
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    float *sQhi = sm;
+    float *sQlo = sQhi + (size_t)NH * PAD;
+    float *sBeta = sQlo + (size_t)32 * PAD;
+    float *sRgap = sBeta + NO;
+    const float4 *g4 = reinterpret_cast<const float4 *>(P.Qhi32);
+    float4 *s4 = reinterpret_cast<float4 *>(sQhi);
+    for (int q = threadIdx.x; q < NH * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+    g4 = reinterpret_cast<const float4 *>(P.Qlo32);
+    s4 = reinterpret_cast<float4 *>(sQlo);
+    for (int q = threadIdx.x; q < 32 * PAD / 4; q += blockDim.x) s4[q] = g4[q];
+    for (int q = threadIdx.x; q < NO; q += blockDim.x) {
+        sBeta[q] = P.beta32[q];
+        sRgap[q] = P.rgap32[q];
+    }
+}
+
+// Packed pairs of floats: Blackwell executes mul/fma.rn.f32x2 as one instruction for two
+// independent round-to-nearest operations, so each element pair of the move costs half the
+// instructions of two scalar streams and rounds exactly as they would.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 up(f2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// One chunk of the four factor rows a move needs (Qhi and Qlo rows of bins p and s): a lane's
+// E-float piece of each (shared-window addresses).
+__device__ __forceinline__ void ld_chunk(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, f2 (&v0)[1],
+                                         f2 (&v1)[1], f2 (&v2)[1], f2 (&v3)[1]) {
+    asm volatile("ld.shared.u64 %0, [%4];\n\tld.shared.u64 %1, [%5];\n\t"
+                 "ld.shared.u64 %2, [%6];\n\tld.shared.u64 %3, [%7];"
+                 : "=l"(v0[0]), "=l"(v1[0]), "=l"(v2[0]), "=l"(v3[0])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
+}
+__device__ __forceinline__ void ld_chunk(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, f2 (&v0)[2],
+                                         f2 (&v1)[2], f2 (&v2)[2], f2 (&v3)[2]) {
+    asm volatile("ld.shared.v2.u64 {%0, %1}, [%8];\n\tld.shared.v2.u64 {%2, %3}, [%9];\n\t"
+                 "ld.shared.v2.u64 {%4, %5}, [%10];\n\tld.shared.v2.u64 {%6, %7}, [%11];"
+                 : "=l"(v0[0]), "=l"(v0[1]), "=l"(v1[0]), "=l"(v1[1]), "=l"(v2[0]), "=l"(v2[1]), "=l"(v3[0]),
+                   "=l"(v3[1])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3));
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// The random words of one move (Philox counter (move, sweep, walker, 0)): bins p, s packed in
+// one word, amplitude eps, Metropolis threshold -T ln u (u < exp(-D / T) <=> D < -T ln u) and
+// delta_p, delta_s (Eqs. update-delta-p/s).
+struct MoveDraw {
+    int ps;
+    float eps, thr, dp, ds;
+};
+
+// With an index walk (WALK) the draw keeps p's start and s's start index on the other n - 1
+// bins (not yet shifted past p) and leaves delta_p, delta_s to the move (the walk sets p, s).
+template <bool WALK>
+__device__ __forceinline__ MoveDraw draw_move(int mv, int n, int walker, uint2 key, int NO, float yd, float T,
+                                              const float *beta, const float *rgap) {
+    const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)walker, 0u), key);
+    MoveDraw m;
+    m.eps = yd * (2.0f * unit32(rnd.z) - 1.0f);
+    m.thr = -logf(unit32(rnd.w)) * T;
+    if constexpr (WALK) {
+        m.ps = (int)(((uint64_t)rnd.x * (uint64_t)NO) >> 32) | ((int)(((uint64_t)rnd.y * (uint64_t)(NO - 1)) >> 32) << 16);
+        m.dp = m.ds = 0.0f;
+    } else {
+        int p, s;
+        move_bins(rnd.x, rnd.y, NO, p, s);
+        m.ps = p | (s << 16);
+        deltas(m.eps, p, s, beta, rgap, m.dp, m.ds);
+    }
+    return m;
+}
+
+__device__ __forceinline__ MoveDraw take_move(const MoveDraw &mine, int src, int width) {
+    MoveDraw m;
+    m.ps = __shfl_sync(kFull, mine.ps, src, width);
+    m.eps = __shfl_sync(kFull, mine.eps, src, width);
+    m.thr = __shfl_sync(kFull, mine.thr, src, width);
+    m.dp = __shfl_sync(kFull, mine.dp, src, width);
+    m.ds = __shfl_sync(kFull, mine.ds, src, width);
+    return m;
+}
+
+// Shared-window addresses of a lane's piece of chunk 0 of the four factor rows of a move.
+struct RowAddr {
+    uint32_t hp, lp, hs, ls;
+};
+__device__ __forceinline__ RowAddr row_addr(int ps, uint32_t qhi, uint32_t qlo, int PAD) {
+    const int p = ps & 0xFFFF, s = ps >> 16;
+    RowAddr a;
+    a.hp = qhi + 4u * (uint32_t)((p >> 5) * PAD);
+    a.lp = qlo + 4u * (uint32_t)((p & 31) * PAD);
+    a.hs = qhi + 4u * (uint32_t)((s >> 5) * PAD);
+    a.ls = qlo + 4u * (uint32_t)((s & 31) * PAD);
+    return a;
+}
+
+// dpart = -delta_p Khat_p - delta_s Khat_s over the lane's elements, the columns formed from
+// the factor rows (Eq. efficient-correlation-model).
+template <int G, int C>
+__device__ __forceinline__ void columns(f2 (&dpart)[C][32 / G / 2], uint32_t qhi, uint32_t qlo, int PAD,
+                                        const MoveDraw &m) {
+    constexpr int H = 32 / G / 2;
+    const RowAddr a = row_addr(m.ps, qhi, qlo, PAD);
+    const f2 mdp = pk(-m.dp, -m.dp), mds = pk(-m.ds, -m.ds);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        f2 hp[H], lp[H], hs[H], ls[H];
+        ld_chunk(a.hp + 128u * c, a.lp + 128u * c, a.hs + 128u * c, a.ls + 128u * c, hp, lp, hs, ls);
+#pragma unroll
+        for (int h = 0; h < H; ++h) dpart[c][h] = fma2(mds, mul2(hs[h], ls[h]), mul2(mdp, mul2(hp[h], lp[h])));
+    }
+}
+
+// A lane's part of delta chi2 = sum_i d_i (2 R_i + d_i), two interleaved accumulators.
+template <int C, int H>
+__device__ __forceinline__ float delta_sum(const f2 (&d)[C][H], const f2 (&R)[C][H], f2 two) {
+    f2 part0 = 0ull, part1 = 0ull;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if ((c * H + h) & 1)
+                part1 = fma2(d[c][h], fma2(two, R[c][h], d[c][h]), part1);
+            else
+                part0 = fma2(d[c][h], fma2(two, R[c][h], d[c][h]), part0);
+        }
+    const float2 pp = up(add2(part0, part1));
+    return pp.x + pp.y;
+}
+
+// Sweeps [n0, n1) for the 32 / G walkers of group grp of one problem on one warp, G lanes per
+// walker.  Lane l of a walker's G lanes holds R_i and M_i = Fhat_i - R_i for
+// i = 32 c + E l .. 32 c + E l + E - 1 (E = 32 / G floats of every 32-tau chunk c) and reads the
+// same E-float pieces of the kernel factor rows, so the G lanes of one walker cover a chunk
+// with one 128-byte shared-memory access.  sm holds the problem's tables; b_stage, if not null,
+// the staged spectra of walkers walker_lo.. .
+//
+// Every G moves each lane draws the random words of one move; the move loop takes them by
+// shuffle.  The loop is software-pipelined: while move k's delta chi2 is reduced and tested,
+// the warp already loads move k+1's kernel columns and forms the part of its residual change
+// that does not depend on move k, dpart = -delta_p Khat_p - delta_s Khat_s; when move k+1 is
+// evaluated, d = eps M + dpart (for n_tau > 256 the columns are loaded when the move is
+// evaluated: the pipeline's registers do not fit).  Columns are loaded for every walker, also
+// those whose move then fails the positivity test: with few warps per SM the sweep is bound by
+// the latency of each warp's instruction stream more than by shared-memory bandwidth.
+template <int G, int C, bool STAGED, bool WALK>
+__device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
+                                          const float *sm,
+                          float *b_stage, int walker_lo) {
+    constexpr int E = 32 / G;          // floats of a 32-tau chunk per lane
+    constexpr int H = E / 2;           // float pairs of a chunk per lane
+    constexpr int WPW = 32 / G;        // walkers per warp
+    // the pipelined loop holds four arrays of C H float pairs (R, M, d and the next move's
+    // dpart); past 8 chunks that outgrows the registers, and the columns of a move are loaded
+    // when it is evaluated
+    constexpr bool PIPE = C <= 8 && !WALK;
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    const float *sQhi = sm;
+    const float *sQlo = sQhi + (size_t)NH * PAD;
+    const float *sBeta = sQlo + (size_t)32 * PAD;
+    const float *sRgap = sBeta + NO;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), sub = lane / G;
+    const uint32_t qhi = (uint32_t)__cvta_generic_to_shared(sQhi) + 4u * E * gl;
+    const uint32_t qlo = (uint32_t)__cvta_generic_to_shared(sQlo) + 4u * E * gl;
+    const uint2 key = philox_key(P.seed);
+    const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
+    const float rho = (float)P.walk_rho;
+
+    const int w = WPW * grp + sub;
+    const bool active = w < P.n_walkers;
+    const int wr = active ? w : WPW * grp;            // a valid walker to read from
+    float *b = STAGED ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+    // the walker's spectrum b: shared memory when staged, else global memory
+    const uint32_t bsh = STAGED ? (uint32_t)__cvta_generic_to_shared(b) : 0u;
+    auto bget = [&](int j) -> float {
+        if constexpr (STAGED) {
+            float v;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(bsh + 4u * (uint32_t)j));
+            return v;
+        } else {
+            return b[j];
+        }
+    };
+    auto bset = [&](int j, float v) {
+        if constexpr (STAGED)
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(bsh + 4u * (uint32_t)j), "f"(v) : "memory");
+        else
+            b[j] = v;
+    };
+
+    f2 R[C][H], M[C][H];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int i = 32 * c + E * gl + 2 * h;
+            const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + i);
+            const float2 f2v = *reinterpret_cast<const float2 *>(P.Fhat32 + i);
+            R[c][h] = pk(r2.x, r2.y);
+            M[c][h] = pk(f2v.x - r2.x, f2v.y - r2.y);
+        }
+    }
+    float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
+    double chi2 = S.chi2[wr];
+    int accp = S.acc_prev[wr];
+    unsigned long long nacc = 0, npos = 0;
+    const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
+
+    for (int n = n0; n < n1; ++n) {
+        const float T = (float)P.Tsweep[n];
+        const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
+        int acc = 0, pos = 0;
+        float dchi = 0.0f;
+        MoveDraw mine = draw_move<WALK>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        MoveDraw cur = take_move(mine, 0, G);
+        f2 dcur[PIPE ? C : 1][H];
+        if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
+        for (int mv = 0; mv < NO; ++mv) {
+            if constexpr (WALK) {
+                // the index walk (Sec. 2.3) on the spectrum as it is now: lane t of the group
+                // draws step t + 1's words (counter (mv, n, w, 2 + t)), lane L the admixture's
+                const int L = P.walk_len;
+                const uint4 wr4 = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)wr, 2u + gl), key);
+                const bool walk_p = !(unit32(__shfl_sync(kFull, wr4.x, L, G)) < rho);
+                const bool walk_s = !(unit32(__shfl_sync(kFull, wr4.y, L, G)) < rho);
+                int wp = cur.ps & 0xFFFF;
+                float bp = bget(wp);
+                for (int t = 0; t < L; ++t) {
+                    const uint32_t xj = __shfl_sync(kFull, wr4.x, t, G), xu = __shfl_sync(kFull, wr4.y, t, G);
+                    const int j = (int)(((uint64_t)xj * (uint64_t)NO) >> 32);
+                    const float bj = bget(j);
+                    if (walk_p && unit32(xu) * bp <= bj) {
+                        wp = j;
+                        bp = bj;
+                    }
+                }
+                int ws = cur.ps >> 16;
+                ws += (ws >= wp);
+                float bs = bget(ws);
+                for (int t = 0; t < L; ++t) {
+                    const uint32_t xj = __shfl_sync(kFull, wr4.z, t, G), xu = __shfl_sync(kFull, wr4.w, t, G);
+                    int j = (int)(((uint64_t)xj * (uint64_t)(NO - 1)) >> 32);
+                    j += (j >= wp);
+                    const float bj = bget(j);
+                    if (walk_s && unit32(xu) * bs <= bj) {
+                        ws = j;
+                        bs = bj;
+                    }
+                }
+                cur.ps = wp | (ws << 16);
+                deltas(cur.eps, wp, ws, sBeta, sRgap, cur.dp, cur.ds);
+            }
+            // move k: positivity (Eq. probability-density) on the spectrum as it is now
+            const int p = cur.ps & 0xFFFF, s = cur.ps >> 16;
+            const float r = 1.0f - cur.eps;
+            const float ap = fmaf(r, ghi * bget(p), cur.dp);
+            const float as = fmaf(r, ghi * bget(s), cur.ds);
+            const bool ok = active && ap >= 0.0f && as >= 0.0f;
+            pos += (active && !ok);
+            // move k: residual change d = eps M + dpart
+            const f2 e2 = pk(cur.eps, cur.eps);
+            f2 d[C][H];
+            if constexpr (PIPE) {
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], dcur[c][h]);
+            } else {
+                columns<G, C>(d, qhi, qlo, PAD, cur);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], d[c][h]);
+            }
+            // move k+1: its words and (pipelined) its columns, into dcur, now free; neither
+            // depends on move k's outcome
+            const MoveDraw nxt = take_move(mine, (mv + 1) & (G - 1), G);
+            if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
+            // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
+            const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
+            if (ok && (D <= 0.0f || D < cur.thr)) {
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+#pragma unroll
+                    for (int h = 0; h < H; ++h) {
+                        R[c][h] = add2(R[c][h], d[c][h]);
+                        M[c][h] = fma2(minus_one, d[c][h], M[c][h]);
+                    }
+                }
+                pair_scale(ghi, glo, r);
+                if (gl == 0) {
+                    const float inv_g = 1.0f / ghi;
+                    bset(p, ap * inv_g);
+                    bset(s, as * inv_g);
+                }
+                dchi += D;
+                ++acc;
+            }
+            __syncwarp();
+            cur = nxt;
+            // the next batch of G moves, one per lane, before its first move is taken
+            if (((mv + 2) & (G - 1)) == 0 && mv + 2 < NO)
+                mine = draw_move<WALK>(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        }
+        chi2 += (double)dchi;
+        accp = acc;
+        nacc += acc;
+        npos += pos;
+        if (active && S.acc_trace && gl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+    }
+    if (!active) return;
+    // fold the common scale into the spectrum and write the walker back
+    float *bg = S.b32 + (size_t)w * NO;
+    for (int j = gl; j < NO; j += G) {
+        const float v = b[j];
+        bg[j] = fmaf(glo, v, ghi * v);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + E * gl + 2 * h) = up(R[c][h]);
+    if (gl == 0) {
+        S.g2[2 * w] = 1.0f;
+        S.g2[2 * w + 1] = 0.0f;
+        S.chi2[w] = chi2;
+        S.acc_prev[w] = accp;
+        S.n_acc[w] += nacc;
+        S.n_pos[w] += npos;
+    }
+}
+
+// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker (128 registers a
+// thread), 8 warps with 8 lanes per walker (whose 4 walkers a warp hold twice the residual
+// elements per lane).
+template <int G>
+constexpr int sweep_threads() { return G == 8 ? 256 : kThreads; }
+
+template <int G, int C, bool WALK>
+__global__ void __launch_bounds__(sweep_threads<G>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
+                                                              SweepGeom Gm) {
+    extern __shared__ float4 smem4[];
+    float *sm = reinterpret_cast<float *>(smem4);
+    constexpr int WPW = 32 / G;
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    float *sB = sm + (size_t)(NH + 32) * PAD + 2 * NO;   // staged spectra [WPW * groups_per_cta][NO]
+    load_tables(P, sm);
+    const int grp_lo = blockIdx.x * Gm.groups_per_cta;
+    const int grp_hi = min(grp_lo + Gm.groups_per_cta, Gm.groups_total);
+    const int walker_lo = WPW * grp_lo;
+    const int walker_hi = min(WPW * grp_hi, P.n_walkers);
+    if (Gm.stage_b) {
+        const size_t n = (size_t)(walker_hi - walker_lo) * NO;
+        const float *src = S.b32 + (size_t)walker_lo * NO;
+        for (size_t q = threadIdx.x; q < n; q += blockDim.x) sB[q] = src[q];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    for (int round = 0; round < Gm.rounds; ++round) {
+        const int grp = grp_lo + round * Gm.warps + warp;
+        if (grp >= grp_hi) break;                         // uniform across the warp
+        if (Gm.stage_b)
+            run_group<G, C, true, WALK>(P, S, n0, n1, grp, sm, sB, walker_lo);
+        else
+            run_group<G, C, false, WALK>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
+    }
+}
+
+size_t table_bytes(const DevProblem &P) {
+    const size_t NH = (size_t)(P.n_omega + 31) / 32;
+    return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
+}
+
+template <int G, int C, bool WALK>
+cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    int dev = 0, sms = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    constexpr int WPW = 32 / G;
+    SweepGeom Gm;
+    Gm.groups_total = (P.n_walkers + WPW - 1) / WPW;
+    const int ctas = Gm.groups_total < sms ? Gm.groups_total : sms;
+    Gm.groups_per_cta = (Gm.groups_total + ctas - 1) / ctas;
+    const int max_warps = sweep_threads<G>() / 32;
+    Gm.rounds = (Gm.groups_per_cta + max_warps - 1) / max_warps;
+    Gm.warps = (Gm.groups_per_cta + Gm.rounds - 1) / Gm.rounds;
+    const size_t tb = table_bytes(P);
+    const size_t staged = (size_t)WPW * Gm.groups_per_cta * P.n_omega * 4;
+    if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
+    Gm.stage_b = tb + staged <= (size_t)smem_max;
+    const size_t smem = tb + (Gm.stage_b ? staged : 0);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C, WALK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int n_ctas = (Gm.groups_total + Gm.groups_per_cta - 1) / Gm.groups_per_cta;
+    sweep_fp32_kernel<G, C, WALK><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
+    return cudaGetLastError();
+}
+
+template <bool WALK>
+cudaError_t launch_sweep_w(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    if (P.lanes == 8) {
+        switch (P.n_tau_pad / 32) {
+            case 1: return launch_c<8, 1, WALK>(P, S, n0, n1, st);
+            case 2: return launch_c<8, 2, WALK>(P, S, n0, n1, st);
+            case 3: return launch_c<8, 3, WALK>(P, S, n0, n1, st);
+            case 4: return launch_c<8, 4, WALK>(P, S, n0, n1, st);
+            case 5: return launch_c<8, 5, WALK>(P, S, n0, n1, st);
+            case 6: return launch_c<8, 6, WALK>(P, S, n0, n1, st);
+            case 7: return launch_c<8, 7, WALK>(P, S, n0, n1, st);
+            case 8: return launch_c<8, 8, WALK>(P, S, n0, n1, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (P.n_tau_pad / 32) {
+        case 1: return launch_c<16, 1, WALK>(P, S, n0, n1, st);
+        case 2: return launch_c<16, 2, WALK>(P, S, n0, n1, st);
+        case 3: return launch_c<16, 3, WALK>(P, S, n0, n1, st);
+        case 4: return launch_c<16, 4, WALK>(P, S, n0, n1, st);
+        case 5: return launch_c<16, 5, WALK>(P, S, n0, n1, st);
+        case 6: return launch_c<16, 6, WALK>(P, S, n0, n1, st);
+        case 7: return launch_c<16, 7, WALK>(P, S, n0, n1, st);
+        case 8: return launch_c<16, 8, WALK>(P, S, n0, n1, st);
+        case 9: return launch_c<16, 9, WALK>(P, S, n0, n1, st);
+        case 10: return launch_c<16, 10, WALK>(P, S, n0, n1, st);
+        case 11: return launch_c<16, 11, WALK>(P, S, n0, n1, st);
+        case 12: return launch_c<16, 12, WALK>(P, S, n0, n1, st);
+        case 13: return launch_c<16, 13, WALK>(P, S, n0, n1, st);
+        case 14: return launch_c<16, 14, WALK>(P, S, n0, n1, st);
+        case 15: return launch_c<16, 15, WALK>(P, S, n0, n1, st);
+        case 16: return launch_c<16, 16, WALK>(P, S, n0, n1, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+}  // namespace sail
