@@ -60,6 +60,7 @@ class OrParams(ctypes.Structure):
         ("smooth_s", ctypes.c_double),
         ("walk_len", ctypes.c_int),
         ("walk_uniform", ctypes.c_double),
+        ("hastings", ctypes.c_int),
     ]
 
 
@@ -118,6 +119,11 @@ def lib():
         L.or_move_bins.argtypes = [ctypes.POINTER(OrParams), ctypes.c_int, _dp, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _ip, _ip]
         L.or_move_bins.restype = None
+        L.or_accept.argtypes = [ctypes.POINTER(OrParams), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        L.or_accept.restype = ctypes.c_int
+        L.or_restore.argtypes = [ctypes.c_int, _dp, ctypes.c_double, ctypes.c_double, _dp]
+        L.or_restore.restype = None
         L.or_anneal.restype = ctypes.c_int
         L.or_average.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_average.restype = ctypes.c_int
@@ -227,6 +233,20 @@ def smooth(x, B: float, s: float, a) -> np.ndarray:
     return out
 
 
+def restore(x, A: float, B: float, a) -> np.ndarray:
+    """A spectrum put back on both sum rules (the Hastings chain's projection)."""
+    x = _f64(x)
+    out = _f64(a).copy()
+    lib().or_restore(x.size, _p(x), float(A), float(B), _p(out))
+    return out
+
+
+def accept(n_omega: int, yd: float, eps: float, D: float, T: float, u: float, hastings: bool = False) -> bool:
+    """The acceptance decision of a move that passed the positivity test."""
+    c = Schedule(hastings=hastings).c()
+    return bool(lib().or_accept(ctypes.byref(c), int(n_omega), float(yd), float(eps), float(D), float(T), float(u)))
+
+
 def cooling_blocks(n_blocks: int, cool_begin: float, freeze_begin: float):
     """First cooling block and first freeze-out block of a self-cooling schedule."""
     bc = np.zeros(1, dtype=np.int32)
@@ -298,13 +318,14 @@ class Schedule:
     smooth_s: float = 0.0
     walk_len: int = 0            # steps of the index walk (Sec. 2.3)
     walk_uniform: float = 0.0    # probability an index skips its walk
+    hastings: bool = False       # Metropolis-Hastings acceptance with the move's Jacobian
 
     def c(self) -> OrParams:
         return OrParams(self.n_sweeps, self.sweeps_per_block, self.resync_every, int(self.branching),
                         self.T_start, self.T_end, self.branch_fraction, self.imprint_t,
                         self.move_scale, self.y_p, self.y_m, self.y_min, self.seed,
                         int(self.schedule_kind), int(self.adaptive), self.cool_begin, self.freeze_begin,
-                        self.smooth_s, int(self.walk_len), self.walk_uniform)
+                        self.smooth_s, int(self.walk_len), self.walk_uniform, int(self.hastings))
 
 
 class Anneal:

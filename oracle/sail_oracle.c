@@ -25,6 +25,9 @@
  *   - p is uniform on the bins and s uniform on the other bins (zero-length
  *     index walk, Sec. 2.3); an index walk of L > 0 steps is an independence
  *     walk with law a_j / A, s walking on the bins other than p (or_move_bins);
+ *   - an optional Hastings acceptance with the move's Jacobian r^(N_omega-4)
+ *     (or_accept), for exact detailed balance, with the spectra put back on the
+ *     sum rules at every residual recomputation (or_restore);
  *   - the branching weight is w = exp[-Delta (chi2 - P_r)] (the printed
  *     formula applies the weight to P(chi2), read as chi2);
  *   - random numbers come from Philox4x32-10 (Salmon et al., SC'11), counter
@@ -330,6 +333,7 @@ typedef struct {
     double smooth_s;       /* smoothing strength s (Sec. smoothing); 0: no smoothing */
     int walk_len;          /* L: steps of the index walk (Sec. 2.3); 0: uniform bins */
     double walk_uniform;   /* rho: probability that an index skips its walk (uniform admixture) */
+    int hastings;          /* 1: Metropolis-Hastings acceptance with the move's Jacobian */
 } or_params;
 
 /* What the anneal carries from block to block besides the walkers. */
@@ -486,6 +490,45 @@ void or_move_bins(const or_params *prm, int n_omega, const double *a, uint32_t w
     *s_out = s;
 }
 
+/* Acceptance of a move that passed the positivity test.  Plain: the Metropolis
+ * test for density exp(-chi2 / T), Eq. (probability-density): D <= 0 or
+ * u < exp(-D / T).  Hastings (reading of the move's detailed balance; the paper
+ * claims ergodicity only): the move (a, eps) -> (r a + delta(eps), -eps / r),
+ * r = 1 - eps, is its own inverse; on the (N_omega - 2)-dimensional manifold of
+ * the two sum rules its Jacobian is r^(N_omega - 2) times |d eps'/d eps| = r^-2.
+ * The reverse move needs |eps / r| < y d to be proposable; then accept when
+ * u < exp(-D / T) r^(N_omega - 4). */
+int or_accept(const or_params *prm, int n_omega, double yd, double eps, double D, double T, double u) {
+    if (!prm->hastings) return D <= 0.0 || u < exp(-D / T);
+    double r = 1.0 - eps;
+    if (!(fabs(eps / r) < yd)) return 0;
+    return u < exp(-D / T + (double)(n_omega - 4) * log(r));
+}
+
+/* Puts a spectrum back on both sum rules: a_j <- a_j kappa (1 + lambda (x_j - c)),
+ * c = B'/A', kappa = A / A', lambda = (B/A - c) A' / sum_j a_j (x_j - c)^2 (sums in bin
+ * order; lambda = 0 when the tilt could turn a factor negative).  In exact arithmetic
+ * a no-op.  The Hastings chain needs it: a move maps the sum errors e to r e, and its
+ * accepted moves have r > 1 on average, so rounding errors grow geometrically without it. */
+void or_restore(int n_omega, const double *x, double A, double B, double *a) {
+    int N = n_omega;
+    double A1 = 0.0, B1 = 0.0;
+    for (int j = 0; j < N; ++j) {
+        A1 += a[j];
+        B1 += a[j] * x[j];
+    }
+    if (!(A1 > 0.0)) return;
+    double c = B1 / A1, V = 0.0;
+    for (int j = 0; j < N; ++j) {
+        double d = x[j] - c;
+        V += a[j] * d * d;
+    }
+    double kappa = A / A1;
+    double lambda = V > 0.0 ? (B / A - c) * A1 / V : 0.0;
+    if (!(fabs(lambda * (x[N - 1] - x[0])) < 0.5)) lambda = 0.0;
+    for (int j = 0; j < N; ++j) a[j] = a[j] * (kappa * (1.0 + lambda * (x[j] - c)));
+}
+
 /* One sweep (N_omega proposals) of walker w at sweep index n. */
 static void sweep_walker(int n_tau, int n_omega, const double *Khat, const double *Fhat,
                          const double *x, double A, double B, const or_params *prm, double T,
@@ -506,8 +549,7 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
         if (!or_propose(n_tau, n_omega, Khat, Fhat, x, A, B, a, R, p, s, eps, &D, &ap, &as, d)) {
             code = 2;
             *n_pos += 1;
-        } else if (D <= 0.0 || u < exp(-D / T)) {
-            /* Metropolis with density exp(-chi2 / T), Eq. (probability-density). */
+        } else if (or_accept(prm, n_omega, y * dmove, eps, D, T, u)) {
             double r = 1.0 - eps;
             for (int j = 0; j < n_omega; ++j) a[j] = r * a[j];
             a[p] = ap;
@@ -555,9 +597,11 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
         int block_end = ((n + 1) % k) == 0;
         if (((n + 1) % prm->resync_every) == 0 || block_end || n + 1 == prm->n_sweeps) {
 #pragma omp parallel for schedule(static)
-            for (int w = 0; w < n_walkers; ++w)
+            for (int w = 0; w < n_walkers; ++w) {
+                if (prm->hastings) or_restore(n_omega, x, A, B, a + (size_t)w * n_omega);
                 chi2[w] = or_residual(n_tau, n_omega, Khat, Fhat, a + (size_t)w * n_omega,
                                       R + (size_t)w * n_tau);
+            }
         }
         /* End of block b: its acceptance and residue statistics (after the
          * recomputation above, before branching), then branching (Sec. 2.5),

@@ -38,6 +38,10 @@ MUTATIONS = {
     "walk_ratio": ("if (unit(r[1]) * a[p] <= a[j]) p = j;", "if (unit(r[1]) * a[j] <= a[p]) p = j;"),
     # s walk whose proposals may land on p
     "walk_skip": ("        if (j >= p) j += 1;\n        if (unit(r[3])", "        if (unit(r[3])"),
+    # Hastings factor with the manifold's Jacobian alone (no d eps'/d eps)
+    "hastings_exponent": ("(double)(n_omega - 4) * log(r)", "(double)(n_omega - 2) * log(r)"),
+    # Hastings acceptance without the reverse move's feasibility
+    "hastings_reverse": ("    if (!(fabs(eps / r) < yd)) return 0;\n", ""),
 }
 
 
@@ -76,12 +80,15 @@ def _pins_pass(L):
         from tests import test_oracle_model as M, test_oracle_moves as V, test_oracle_branching as B
         from tests import test_oracle_protocol as Q
         from tests import test_oracle_walk as Wk
+        from tests import test_oracle_hastings as Hs
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
                   lambda: B.test_multipliers_match_enumeration(0),
                   Q.test_smoothing_worked_example, Q.test_smoothing_keeps_both_sum_rules,
                   Q.test_self_cooling_phases, Q.test_adaptive_branching_scales_fraction_and_imprint,
-                  lambda: Wk.test_walk_law_matches_the_matrix_power(3, 0.0)]
+                  lambda: Wk.test_walk_law_matches_the_matrix_power(3, 0.0),
+                  lambda: Hs.test_jacobian_is_r_to_the_n_minus_4(0.07),
+                  Hs.test_hastings_chain_samples_the_uniform_polytope]
         for c in checks:
             try:
                 c()
