@@ -160,7 +160,8 @@ def kernel_traffic():
         return None
     try:
         rec = json.load(open(path))
-        src = open(os.path.join(ROOT, "paper_1609_07936_gb300", "csrc", "sweep_fp32.cu"), "rb").read()
+        csrc = os.path.join(ROOT, "paper_1609_07936_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("sweep_group.cuh", "sweep_fp32.cu"))
         if hashlib.sha256(src).hexdigest() != rec.get("source_sha256"):
             return None
         return rec.get("dram_bytes_per_launch")

@@ -112,7 +112,13 @@ typedef struct sail_params {
                                when u a_j <= a_j' (stationary law a_j / A); s walks on the bins
                                other than the final p.  Words: step t from Philox counter
                                (move, sweep, walker, 1 + t), admixture from (.., 2 + L) */
-    int reserved0;
+    int hastings;           /* 1: Metropolis-Hastings acceptance for exact detailed balance of the
+                               move (a, eps) -> (r a + delta, -eps/r): accept when |eps/r| < y d
+                               (the reverse move can be proposed) and u < exp(-D/T) r^(n_omega-4),
+                               r^(n_omega-4) the move's Jacobian on the sum-rule manifold; the
+                               spectra are put back on the sum rules at every residual
+                               recomputation; needs index_walk_len = 0.  0: the paper's
+                               Metropolis test */
     double walk_uniform;    /* probability that an index skips its walk (uniform admixture) */
     int reserved[2];
 } sail_params;

@@ -55,7 +55,7 @@ class CParams(ctypes.Structure):
         ("trace", ctypes.c_int), ("timing", ctypes.c_int), ("resync_kind", ctypes.c_int),
         ("wait_test", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("schedule_kind", ctypes.c_int),
         ("adaptive_branching", ctypes.c_int), ("cool_begin", ctypes.c_double), ("freeze_begin", ctypes.c_double),
-        ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("reserved0", ctypes.c_int),
+        ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("hastings", ctypes.c_int),
         ("walk_uniform", ctypes.c_double), ("reserved", ctypes.c_int * 2),
     ]
 
@@ -206,6 +206,7 @@ class Params:
     smooth_s: float = 0.0
     index_walk_len: int = 0
     walk_uniform: float = 0.0
+    hastings: bool = False
 
     def c(self) -> CParams:
         p = CParams()

@@ -23,7 +23,9 @@ UNITS = {
     "exact64.cu": ["-fmad=false"],
     "sweep_fp32.cu": [],
     "sweep_walk.cu": [],
-    "sweep_batch.cu": [],
+    "sweep_hastings.cu": [],
+    "sweep_batch8.cu": [],
+    "sweep_batch16.cu": [],
     "resync_fp32.cu": [],
     "resync_tc.cu": [],
     "noalloc.cu": ["-fmad=false"],

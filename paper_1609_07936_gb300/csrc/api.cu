@@ -170,6 +170,10 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->smooth_s >= 0.0 && p->smooth_s < 0.5)) return fail(SAIL_EINVAL, "smooth_s must be in [0, 0.5)");
     if (p->index_walk_len < 0 || p->index_walk_len > 7) return fail(SAIL_EINVAL, "index_walk_len must be in [0, 7]");
     if (!(p->walk_uniform >= 0.0 && p->walk_uniform <= 1.0)) return fail(SAIL_EINVAL, "walk_uniform must be in [0, 1]");
+    if (p->hastings != 0 && p->hastings != 1) return fail(SAIL_EINVAL, "hastings must be 0 or 1");
+    if (p->hastings && p->index_walk_len > 0)
+        return fail(SAIL_EINVAL, "hastings needs uniform bins (index_walk_len = 0): the walk's bin choice "
+                                 "depends on the state, and its ratio is not part of the correction");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -468,6 +472,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.lanes = p->sweep_lanes != 0 ? p->sweep_lanes : (PAD <= 256 ? 8 : 16);
     P.walk_len = p->index_walk_len;
     P.walk_rho = p->walk_uniform;
+    P.hastings = p->hastings;
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;

@@ -143,7 +143,15 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
                         if (32 * c + l < NT) D = D + v;
                     }
                 }
-                if (D <= 0.0 || u < exp(-D / T)) {
+                bool accept;
+                if (!P.hastings) {
+                    accept = D <= 0.0 || u < exp(-D / T);
+                } else {
+                    // Metropolis-Hastings with the move's Jacobian r^(N-4), the reverse amplitude
+                    // -eps/r proposable only when |eps/r| < y d (the oracle's or_accept)
+                    accept = fabs(eps / r) < y * dmove && u < exp(-D / T + (double)(NO - 4) * log(r));
+                }
+                if (accept) {
                     for (int j = lane; j < NO; j += 32) a[j] = r * a[j];
                     __syncwarp();
                     if (lane == 0) {
@@ -824,6 +832,32 @@ __device__ void smooth_one(E *a, int N, const double *x, double B, double s) {
     for (int j = 0; j < N; ++j) a[j] = (E)((double)a[j] * (1.0 + beta * (x[j] - m)));
 }
 
+// Puts each FP64 spectrum back on both sum rules in the oracle's order (or_restore): sums in
+// bin order, then a_j kappa (1 + lambda (x_j - c)).  One thread per walker.
+__global__ void __launch_bounds__(128) restore_seq_kernel(DevProblem P, DevState S) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= P.n_walkers) return;
+    const int N = P.n_omega;
+    double *a = S.a64 + (size_t)w * N;
+    const double *x = P.x64;
+    double A1 = 0.0, B1 = 0.0;
+    for (int j = 0; j < N; ++j) {
+        A1 += a[j];
+        B1 += a[j] * x[j];
+    }
+    if (!(A1 > 0.0)) return;
+    const double c = B1 / A1;
+    double V = 0.0;
+    for (int j = 0; j < N; ++j) {
+        const double d = x[j] - c;
+        V += a[j] * d * d;
+    }
+    const double kappa = P.A / A1;
+    double lambda = V > 0.0 ? (P.B / P.A - c) * A1 / V : 0.0;
+    if (!(fabs(lambda * (x[N - 1] - x[0])) < 0.5)) lambda = 0.0;
+    for (int j = 0; j < N; ++j) a[j] = a[j] * (kappa * (1.0 + lambda * (x[j] - c)));
+}
+
 __global__ void __launch_bounds__(128) smooth_kernel(DevProblem P, DevState S, int precision, double s) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= P.n_walkers) return;
@@ -867,6 +901,11 @@ cudaError_t launch_sweep_fp64(const DevProblem &P, const DevState &S, int n0, in
 cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
                           int *status, cudaStream_t st, int *launches) {
     if (precision == 0) {
+        if (P.hastings && restore) {
+            // the Hastings chain drifts off the sum rules by rounding: put it back first
+            restore_seq_kernel<<<(P.n_walkers + 127) / 128, 128, 0, st>>>(P, S);
+            *launches += 1;
+        }
         resync_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, precision);
         *launches += 1;
         return cudaGetLastError();

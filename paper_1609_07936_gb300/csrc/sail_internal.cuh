@@ -48,6 +48,7 @@ struct DevProblem {
     int wait_test;         // test hook: the tensor-core resync withholds its first commit
     int lanes;             // FP32 sweep: lanes per walker (8: 4 walkers per warp, n_tau <= 256; 16: 2)
     int walk_len;          // steps of the index walk (0: uniform bins)
+    int hastings;          // Metropolis-Hastings acceptance with the move's Jacobian
     double walk_rho;       // probability that an index skips its walk
     const double *Tsweep;
 };
@@ -96,8 +97,12 @@ cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_
 // The FP32 sweep of a problem with an index walk (P.walk_len > 0); launch_sweep_fp32 calls it.
 cudaError_t launch_sweep_walk(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                               cudaStream_t st);
-// FP64 state: sequential FP64 recomputation.  FP32 state: optional sum-rule restoration
-// (restore != 0), then the tiled GEMM of resync_fp32.cu.
+// The FP32 sweep with the Metropolis-Hastings acceptance (P.hastings, uniform bins).
+cudaError_t launch_sweep_hastings(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
+                                  cudaStream_t st);
+// FP64 state: sequential FP64 recomputation, after (restore != 0 and the Hastings acceptance)
+// putting the spectra back on the sum rules in bin order.  FP32 state: optional sum-rule
+// restoration (restore != 0), then the tiled GEMM of resync_fp32.cu or the tensor cores.
 cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
                           int *status, cudaStream_t st, int *launches);
 cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStream_t st);
@@ -139,6 +144,8 @@ struct BatchItem {      // walker groups [grp_lo, grp_hi) of problem prob, one g
 // `warps` warps (at most 8 when lanes = 8) take items from the queue.
 cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
                                size_t smem, int warps, int lanes, cudaStream_t st);
+cudaError_t launch_sweep_batch8(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
+                                size_t smem, int warps, cudaStream_t st);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes);
 

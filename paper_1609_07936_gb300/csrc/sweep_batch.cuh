@@ -1,33 +1,35 @@
-// Batched FP32 sweep: many inversions in one persistent launch per lane count (the move
-// loop of sweep_group.cuh).
+// Batched FP32 sweep: many inversions in one persistent launch per lane count (the move loop
+// of sweep_group.cuh).  sweep_batch8.cu and sweep_batch16.cu instantiate it for 8 and 16
+// lanes per walker.
+#pragma once
 #include "sweep_group.cuh"
 
 namespace sail {
 
 namespace {
 
-template <int G, bool WALK>
+template <int G, int MODE>
 __device__ __forceinline__ void run_group_c(const BatchProblem &BP, int grp, const float *sm) {
     switch (BP.P.n_tau_pad / 32) {
-        case 1: run_group<G, 1, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 2: run_group<G, 2, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 3: run_group<G, 3, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 4: run_group<G, 4, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 5: run_group<G, 5, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 6: run_group<G, 6, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 7: run_group<G, 7, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 8: run_group<G, 8, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 1: run_group<G, 1, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 2: run_group<G, 2, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 3: run_group<G, 3, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 4: run_group<G, 4, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 5: run_group<G, 5, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 6: run_group<G, 6, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 7: run_group<G, 7, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 8: run_group<G, 8, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
         default:
             if constexpr (G == 16) {
                 switch (BP.P.n_tau_pad / 32) {
-                    case 9: run_group<16, 9, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 10: run_group<16, 10, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 11: run_group<16, 11, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 12: run_group<16, 12, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 13: run_group<16, 13, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 14: run_group<16, 14, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 15: run_group<16, 15, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 16: run_group<16, 16, false, WALK>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 9: run_group<16, 9, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 10: run_group<16, 10, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 11: run_group<16, 11, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 12: run_group<16, 12, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 13: run_group<16, 13, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 14: run_group<16, 14, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 15: run_group<16, 15, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 16: run_group<16, 16, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
                     default: break;
                 }
             }
@@ -66,13 +68,13 @@ __global__ void __launch_bounds__(sweep_threads<G>()) sweep_batch_kernel(const B
         const int grp = I.grp_lo + warp;
         if (grp >= I.grp_hi || BP.n0 >= BP.n1) continue;
         if (BP.P.walk_len > 0)
-            run_group_c<G, true>(BP, grp, sm);
+            run_group_c<G, kWalk>(BP, grp, sm);
+        else if (BP.P.hastings)
+            run_group_c<G, kHastings>(BP, grp, sm);
         else
-            run_group_c<G, false>(BP, grp, sm);
+            run_group_c<G, kPlain>(BP, grp, sm);
     }
 }
-
-}  // namespace
 
 template <int G>
 cudaError_t launch_batch_g(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
@@ -95,11 +97,6 @@ cudaError_t launch_batch_g(const BatchProblem *d_probs, const BatchItem *d_items
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
-                               size_t smem, int warps, int lanes, cudaStream_t st) {
-    if (n_items <= 0) return cudaSuccess;
-    return lanes == 8 ? launch_batch_g<8>(d_probs, d_items, n_items, d_counter, smem, warps, st)
-                      : launch_batch_g<16>(d_probs, d_items, n_items, d_counter, smem, warps, st);
-}
+}  // namespace
 
 }  // namespace sail

@@ -120,7 +120,9 @@ cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sin
 int sweep_walkers_per_warp(const DevProblem &P) { return P.lanes == 8 ? 4 : 2; }
 
 cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
-    return P.walk_len > 0 ? launch_sweep_walk(P, S, n0, n1, st) : launch_sweep_w<false>(P, S, n0, n1, st);
+    if (P.walk_len > 0) return launch_sweep_walk(P, S, n0, n1, st);
+    if (P.hastings) return launch_sweep_hastings(P, S, n0, n1, st);
+    return launch_sweep_w<kPlain>(P, S, n0, n1, st);
 }
 
 cudaError_t launch_probe(const DevProblem &P, const DevState &S, int precision, int n, const int *walker,

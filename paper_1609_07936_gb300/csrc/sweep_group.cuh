@@ -34,6 +34,11 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kThreads = 512;          // at most 16 warps per round
 
+// Move-loop variants, compiled separately so the plain loop carries no code of the others.
+constexpr int kPlain = 0;              // uniform bins, Metropolis test (the paper's)
+constexpr int kWalk = 1;               // bins from the index walk (Sec. 2.3)
+constexpr int kHastings = 2;           // uniform bins, Metropolis-Hastings test with the Jacobian
+
 // (hi, lo) <- (hi, lo) * r with the product's rounding error carried in lo.
 __device__ __forceinline__ void pair_scale(float &hi, float &lo, float r) {
     const float p = hi * r;
@@ -143,15 +148,24 @@ struct MoveDraw {
     float eps, thr, dp, ds;
 };
 
-// With an index walk (WALK) the draw keeps p's start and s's start index on the other n - 1
+// With an index walk (kWalk) the draw keeps p's start and s's start index on the other n - 1
 // bins (not yet shifted past p) and leaves delta_p, delta_s to the move (the walk sets p, s).
-template <bool WALK>
+//
+// With the Hastings acceptance the threshold takes the move's Jacobian: D < -T ln u +
+// T (N - 4) ln r, and a move whose reverse amplitude -eps/r cannot be proposed
+// (|eps/r| >= y d) gets -infinity.
+template <int MODE>
 __device__ __forceinline__ MoveDraw draw_move(int mv, int n, int walker, uint2 key, int NO, float yd, float T,
                                               const float *beta, const float *rgap) {
+    constexpr bool WALK = MODE == kWalk;
     const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)walker, 0u), key);
     MoveDraw m;
     m.eps = yd * (2.0f * unit32(rnd.z) - 1.0f);
     m.thr = -logf(unit32(rnd.w)) * T;
+    if constexpr (MODE == kHastings) {
+        const float r = 1.0f - m.eps;
+        m.thr = fabsf(m.eps / r) < yd ? m.thr + T * (float)(NO - 4) * log1pf(-m.eps) : -INFINITY;
+    }
     if constexpr (WALK) {
         m.ps = (int)(((uint64_t)rnd.x * (uint64_t)NO) >> 32) | ((int)(((uint64_t)rnd.y * (uint64_t)(NO - 1)) >> 32) << 16);
         m.dp = m.ds = 0.0f;
@@ -237,7 +251,7 @@ __device__ __forceinline__ float delta_sum(const f2 (&d)[C][H], const f2 (&R)[C]
 // evaluated: the pipeline's registers do not fit).  Columns are loaded for every walker, also
 // those whose move then fails the positivity test: with few warps per SM the sweep is bound by
 // the latency of each warp's instruction stream more than by shared-memory bandwidth.
-template <int G, int C, bool STAGED, bool WALK>
+template <int G, int C, bool STAGED, int MODE>
 __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
                                           const float *sm,
                           float *b_stage, int walker_lo) {
@@ -247,6 +261,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     // the pipelined loop holds four arrays of C H float pairs (R, M, d and the next move's
     // dpart); past 8 chunks that outgrows the registers, and the columns of a move are loaded
     // when it is evaluated
+    constexpr bool WALK = MODE == kWalk;
     constexpr bool PIPE = C <= 8 && !WALK;
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
     const float *sQhi = sm;
@@ -305,7 +320,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
         const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
         int acc = 0, pos = 0;
         float dchi = 0.0f;
-        MoveDraw mine = draw_move<WALK>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        MoveDraw mine = draw_move<MODE>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
         MoveDraw cur = take_move(mine, 0, G);
         f2 dcur[PIPE ? C : 1][H];
         if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
@@ -372,7 +387,8 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
             // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
             const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
-            if (ok && (D <= 0.0f || D < cur.thr)) {
+            // the Hastings threshold may be negative: then D <= 0 does not pass by itself
+            if (ok && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr))) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
 #pragma unroll
@@ -394,7 +410,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             cur = nxt;
             // the next batch of G moves, one per lane, before its first move is taken
             if (((mv + 2) & (G - 1)) == 0 && mv + 2 < NO)
-                mine = draw_move<WALK>(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+                mine = draw_move<MODE>(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
         }
         chi2 += (double)dchi;
         accp = acc;
@@ -430,7 +446,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
 template <int G>
 constexpr int sweep_threads() { return G == 8 ? 256 : kThreads; }
 
-template <int G, int C, bool WALK>
+template <int G, int C, int MODE>
 __global__ void __launch_bounds__(sweep_threads<G>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom Gm) {
     extern __shared__ float4 smem4[];
@@ -454,9 +470,9 @@ __global__ void __launch_bounds__(sweep_threads<G>()) sweep_fp32_kernel(DevProbl
         const int grp = grp_lo + round * Gm.warps + warp;
         if (grp >= grp_hi) break;                         // uniform across the warp
         if (Gm.stage_b)
-            run_group<G, C, true, WALK>(P, S, n0, n1, grp, sm, sB, walker_lo);
+            run_group<G, C, true, MODE>(P, S, n0, n1, grp, sm, sB, walker_lo);
         else
-            run_group<G, C, false, WALK>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
+            run_group<G, C, false, MODE>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
     }
 }
 
@@ -465,7 +481,7 @@ size_t table_bytes(const DevProblem &P) {
     return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
 }
 
-template <int G, int C, bool WALK>
+template <int G, int C, int MODE>
 cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
@@ -484,45 +500,45 @@ cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cud
     if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
     Gm.stage_b = tb + staged <= (size_t)smem_max;
     const size_t smem = tb + (Gm.stage_b ? staged : 0);
-    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C, WALK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int n_ctas = (Gm.groups_total + Gm.groups_per_cta - 1) / Gm.groups_per_cta;
-    sweep_fp32_kernel<G, C, WALK><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
+    sweep_fp32_kernel<G, C, MODE><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
     return cudaGetLastError();
 }
 
-template <bool WALK>
+template <int MODE>
 cudaError_t launch_sweep_w(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
     if (P.lanes == 8) {
         switch (P.n_tau_pad / 32) {
-            case 1: return launch_c<8, 1, WALK>(P, S, n0, n1, st);
-            case 2: return launch_c<8, 2, WALK>(P, S, n0, n1, st);
-            case 3: return launch_c<8, 3, WALK>(P, S, n0, n1, st);
-            case 4: return launch_c<8, 4, WALK>(P, S, n0, n1, st);
-            case 5: return launch_c<8, 5, WALK>(P, S, n0, n1, st);
-            case 6: return launch_c<8, 6, WALK>(P, S, n0, n1, st);
-            case 7: return launch_c<8, 7, WALK>(P, S, n0, n1, st);
-            case 8: return launch_c<8, 8, WALK>(P, S, n0, n1, st);
+            case 1: return launch_c<8, 1, MODE>(P, S, n0, n1, st);
+            case 2: return launch_c<8, 2, MODE>(P, S, n0, n1, st);
+            case 3: return launch_c<8, 3, MODE>(P, S, n0, n1, st);
+            case 4: return launch_c<8, 4, MODE>(P, S, n0, n1, st);
+            case 5: return launch_c<8, 5, MODE>(P, S, n0, n1, st);
+            case 6: return launch_c<8, 6, MODE>(P, S, n0, n1, st);
+            case 7: return launch_c<8, 7, MODE>(P, S, n0, n1, st);
+            case 8: return launch_c<8, 8, MODE>(P, S, n0, n1, st);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (P.n_tau_pad / 32) {
-        case 1: return launch_c<16, 1, WALK>(P, S, n0, n1, st);
-        case 2: return launch_c<16, 2, WALK>(P, S, n0, n1, st);
-        case 3: return launch_c<16, 3, WALK>(P, S, n0, n1, st);
-        case 4: return launch_c<16, 4, WALK>(P, S, n0, n1, st);
-        case 5: return launch_c<16, 5, WALK>(P, S, n0, n1, st);
-        case 6: return launch_c<16, 6, WALK>(P, S, n0, n1, st);
-        case 7: return launch_c<16, 7, WALK>(P, S, n0, n1, st);
-        case 8: return launch_c<16, 8, WALK>(P, S, n0, n1, st);
-        case 9: return launch_c<16, 9, WALK>(P, S, n0, n1, st);
-        case 10: return launch_c<16, 10, WALK>(P, S, n0, n1, st);
-        case 11: return launch_c<16, 11, WALK>(P, S, n0, n1, st);
-        case 12: return launch_c<16, 12, WALK>(P, S, n0, n1, st);
-        case 13: return launch_c<16, 13, WALK>(P, S, n0, n1, st);
-        case 14: return launch_c<16, 14, WALK>(P, S, n0, n1, st);
-        case 15: return launch_c<16, 15, WALK>(P, S, n0, n1, st);
-        case 16: return launch_c<16, 16, WALK>(P, S, n0, n1, st);
+        case 1: return launch_c<16, 1, MODE>(P, S, n0, n1, st);
+        case 2: return launch_c<16, 2, MODE>(P, S, n0, n1, st);
+        case 3: return launch_c<16, 3, MODE>(P, S, n0, n1, st);
+        case 4: return launch_c<16, 4, MODE>(P, S, n0, n1, st);
+        case 5: return launch_c<16, 5, MODE>(P, S, n0, n1, st);
+        case 6: return launch_c<16, 6, MODE>(P, S, n0, n1, st);
+        case 7: return launch_c<16, 7, MODE>(P, S, n0, n1, st);
+        case 8: return launch_c<16, 8, MODE>(P, S, n0, n1, st);
+        case 9: return launch_c<16, 9, MODE>(P, S, n0, n1, st);
+        case 10: return launch_c<16, 10, MODE>(P, S, n0, n1, st);
+        case 11: return launch_c<16, 11, MODE>(P, S, n0, n1, st);
+        case 12: return launch_c<16, 12, MODE>(P, S, n0, n1, st);
+        case 13: return launch_c<16, 13, MODE>(P, S, n0, n1, st);
+        case 14: return launch_c<16, 14, MODE>(P, S, n0, n1, st);
+        case 15: return launch_c<16, 15, MODE>(P, S, n0, n1, st);
+        case 16: return launch_c<16, 16, MODE>(P, S, n0, n1, st);
         default: return cudaErrorInvalidValue;
     }
 }
