@@ -13,4 +13,7 @@ from .problems import (  # noqa: F401
     precision_random_peaks,
     random_batch_problem,
     random_peaks,
+    lorentzian_band,
+    lorentzian_band_peaks,
+    skew,
 )

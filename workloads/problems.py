@@ -121,3 +121,50 @@ def random_batch_problem(index: int, seed: int = 0, rng: Optional[np.random.Gene
     tau = 8.0 * np.arange(n_tau, dtype=np.float64) / (n_tau - 1)
     return make_problem(f"batch_{seed}_{index}", tau, n_omega, 20.0, peaks, level,
                         int(rng.integers(0, 2**31)), n_walkers)
+
+
+def lorentzian_band_peaks() -> List[Peak]:
+    """Eq. (lorentzian-band): two unit Lorentzians of HWHM 1 at 1 and 2, cut to [0.5, 2.5]."""
+    return [Peak("lorentz", 1.0, 1.0, 1.0), Peak("lorentz", 2.0, 1.0, 1.0)]
+
+
+LORENTZIAN_BAND = (0.5, 2.5)
+
+
+def lorentzian_band(noise_level: float, seed: int = 0, n_walkers: int = 1500, n_tau: int = 160,
+                    dtau: float = 0.05, n_omega: int = 1000, W: float = 3.5) -> Problem:
+    """The paper's example (Sec. lorentzian-model): the band spectrum on 1000 bins of [0, 3.5]
+    with correlated undersampling noise (Sec. resampling) of relative level noise_level at
+    tau = 0; noise_level = 0 gives the exact data, weighted as if its noise were at 1e-8.
+    Readings: the tau grid (unstated) is tau_i = i dtau, i < n_tau, and the sequences drawn
+    for the noise have 2 n_tau points."""
+    from .correlated import correlated_noise
+    from .spectra import laplace as _laplace
+    peaks = lorentzian_band_peaks()
+    tau = dtau * np.arange(n_tau, dtype=np.float64)
+    lags = dtau * np.arange(2 * n_tau, dtype=np.float64)
+    F_lags = _laplace(peaks, W, lags, LORENTZIAN_BAND)
+    F_exact = F_lags[:n_tau].copy()
+    rng = np.random.default_rng(seed)
+    F, sigma, M = correlated_noise(F_exact, F_lags, noise_level if noise_level > 0 else 1e-8, rng)
+    if noise_level == 0:
+        F = F_exact.copy()
+    omega = (np.arange(n_omega, dtype=np.float64) + 0.5) * (W / n_omega)
+    dw = W / n_omega
+    return Problem(name=f"lorentzian_band_{noise_level:g}", tau=tau, F=F, sigma=sigma, omega=omega,
+                   A=mass(peaks, W, LORENTZIAN_BAND) / dw, B=first_moment(peaks, W, LORENTZIAN_BAND) / dw,
+                   W=W, peaks=peaks, F_exact=F_exact, n_walkers=n_walkers,
+                   extra={"noise_level": noise_level, "seed": seed, "band": LORENTZIAN_BAND,
+                          "sequences_equivalent": M})
+
+
+def skew(a: np.ndarray, omega: np.ndarray, w_mid: float = 1.5) -> float:
+    """The paper's skew of a histogram spectrum about w_mid (Sec. annealing results):
+    |mass below - mass above| / total mass, the bin containing w_mid split at it."""
+    a = np.asarray(a, dtype=np.float64)
+    dw = omega[1] - omega[0]
+    lo_edge = omega - 0.5 * dw
+    frac_below = np.clip((w_mid - lo_edge) / dw, 0.0, 1.0)
+    below = float(np.sum(a * frac_below))
+    total = float(np.sum(a))
+    return abs(below - (total - below)) / total

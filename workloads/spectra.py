@@ -3,7 +3,7 @@
 A synthetic spectrum is a weighted sum of peaks, each cut to the frequency
 window [0, W] on which the histogram model of Eq. (spectral-model) lives:
 
-    S(w) = sum_k c_k * P_k(w) * 1[0 <= w <= W]
+    S(w) = sum_k c_k * P_k(w) * 1[0 <= w <= W]   (or 1[lo <= w <= hi], a band inside it)
 
 with P_k a unit-mass Lorentzian (centre w0, half width at half maximum G,
 as in Eq. (lorentzian-band)) or a unit-mass Gaussian (mean mu, standard
@@ -136,28 +136,47 @@ def _gauss_laplace(p: Peak, W: float, tau: np.ndarray) -> np.ndarray:
 
 # ---------------------------------------------------------------- interface
 
-def mass(peaks: Sequence[Peak], W: float) -> float:
-    """int_0^W S(w) dw."""
-    return float(sum(_lorentz_mass(p, W) if p.kind == "lorentz" else _gauss_mass(p, W) for p in peaks))
+# A spectrum may also be cut to a band [lo, hi] inside [0, W] (Eq. lorentzian-band); every
+# quantity over the band is the one over [0, hi] minus the one over [0, lo].
+
+def _band(W: float, band):
+    lo, hi = (0.0, W) if band is None else (float(band[0]), float(band[1]))
+    if not (0.0 <= lo < hi <= W):
+        raise ValueError("band must satisfy 0 <= lo < hi <= W")
+    return lo, hi
 
 
-def first_moment(peaks: Sequence[Peak], W: float) -> float:
-    """int_0^W w S(w) dw."""
-    return float(sum(_lorentz_moment(p, W) if p.kind == "lorentz" else _gauss_moment(p, W) for p in peaks))
+def mass(peaks: Sequence[Peak], W: float, band=None) -> float:
+    """int S(w) dw over [0, W] (or over the band [lo, hi])."""
+    lo, hi = _band(W, band)
+    f = lambda p, x: (_lorentz_mass(p, x) if p.kind == "lorentz" else _gauss_mass(p, x)) if x > 0 else 0.0
+    return float(sum(f(p, hi) - f(p, lo) for p in peaks))
 
 
-def laplace(peaks: Sequence[Peak], W: float, tau) -> np.ndarray:
-    """F(tau) = (1/2pi) int_0^W S(w) e^{-w tau} dw (Eq. transform, S cut at W)."""
+def first_moment(peaks: Sequence[Peak], W: float, band=None) -> float:
+    """int w S(w) dw over [0, W] (or over the band [lo, hi])."""
+    lo, hi = _band(W, band)
+    f = lambda p, x: (_lorentz_moment(p, x) if p.kind == "lorentz" else _gauss_moment(p, x)) if x > 0 else 0.0
+    return float(sum(f(p, hi) - f(p, lo) for p in peaks))
+
+
+def laplace(peaks: Sequence[Peak], W: float, tau, band=None) -> np.ndarray:
+    """F(tau) = (1/2pi) int S(w) e^{-w tau} dw (Eq. transform) over [0, W] or the band."""
+    lo, hi = _band(W, band)
     tau = np.atleast_1d(np.asarray(tau, dtype=np.float64))
     out = np.zeros(tau.shape, dtype=np.float64)
     for p in peaks:
-        out += _lorentz_laplace(p, W, tau) if p.kind == "lorentz" else _gauss_laplace(p, W, tau)
+        f = _lorentz_laplace if p.kind == "lorentz" else _gauss_laplace
+        out += f(p, hi, tau)
+        if lo > 0:
+            out -= f(p, lo, tau)
     return out
 
 
-def bin_masses(peaks: Sequence[Peak], W: float, n_omega: int) -> np.ndarray:
-    """int over bin j of S(w) dw for the n_omega equal bins of [0, W]."""
-    edges = np.linspace(0.0, W, n_omega + 1)
+def bin_masses(peaks: Sequence[Peak], W: float, n_omega: int, band=None) -> np.ndarray:
+    """int over bin j of S(w) dw for the n_omega equal bins of [0, W] (S cut to the band)."""
+    lo, hi = _band(W, band)
+    edges = np.clip(np.linspace(0.0, W, n_omega + 1), lo, hi)
     cum = np.zeros(n_omega + 1)
     for p in peaks:
         if p.kind == "lorentz":
