@@ -962,10 +962,12 @@ struct sail_batch_ctx {
     BatchItem *d_items;
     int *d_counter;
     size_t max_items;
-    size_t smem[2];            // shared memory of the batched sweeps (lanes 16, lanes 8): the largest
-                               // tables of the problems of each class
-    cudaStream_t aux;          // second stream: the two classes' sweeps run side by side
-    cudaEvent_t fork, join;
+    // a batched sweep segment launches one kernel per class of problems: lanes per walker
+    // (16 or 8) times move-loop variant (plain, walk, Hastings); class = 3 * (lanes == 8) + mode
+    static constexpr int kClasses = 6;
+    size_t smem[kClasses];     // shared memory of each class's kernel: its problems' largest tables
+    cudaStream_t aux[kClasses - 1];   // further streams: the classes' kernels run side by side
+    cudaEvent_t fork, join[kClasses - 1];
     int autotune;
     int item_pairs;            // chosen mapping
     int tune_next;             // next candidate to try (autotune), or 3 when done
@@ -999,44 +1001,55 @@ int check_batch(int n, const sail_problem *probs) {
     return SAIL_OK;
 }
 
+int batch_class(const DevProblem &P) { return 3 * (P.lanes == 8 ? 1 : 0) + sweep_mode(P); }
+
 void batch_streams_create(sail_batch_ctx *b) {
     cudaEventCreate(&b->ev0);
     cudaEventCreate(&b->ev1);
     cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-    cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming);
-    cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking);
+    for (int c = 0; c < sail_batch_ctx::kClasses - 1; ++c) {
+        cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming);
+        cudaStreamCreateWithFlags(&b->aux[c], cudaStreamNonBlocking);
+    }
 }
 
 void batch_streams_destroy(sail_batch_ctx *b) {
     cudaEventDestroy(b->ev0);
     cudaEventDestroy(b->ev1);
     cudaEventDestroy(b->fork);
-    cudaEventDestroy(b->join);
-    cudaStreamDestroy(b->aux);
+    for (int c = 0; c < sail_batch_ctx::kClasses - 1; ++c) {
+        cudaEventDestroy(b->join[c]);
+        cudaStreamDestroy(b->aux[c]);
+    }
 }
 
-// One batched sweep segment: the items of problems with 16 lanes per walker, [0, n16), run on
-// the batch stream and those with 8 lanes, [n16, n16 + n8), on the second stream, forked from
-// and joined back into the batch stream.  d_counter[0] and d_counter[1] are their queues.
-cudaError_t batch_sweep_segment(sail_batch_ctx *b, int n16, int n8) {
+// One batched sweep segment: the items of class c are count[c] consecutive items from the
+// start of the class's range in the item list (classes in order); the first non-empty class
+// runs on the batch stream, the others on further streams forked from and joined back into
+// it.  d_counter[c] is class c's queue.
+cudaError_t batch_sweep_segment(sail_batch_ctx *b, const int *count) {
     cudaStream_t st = b->stream;
     cudaError_t e = cudaSuccess;
-    if (n16 > 0 && n8 > 0) {
+    int used = 0;
+    for (int c = 0; c < sail_batch_ctx::kClasses; ++c) used += count[c] > 0;
+    if (used > 1) {
         if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(b->aux, b->fork, 0)) != cudaSuccess) return e;
+        for (int c = 0; c < used - 1; ++c)
+            if ((e = cudaStreamWaitEvent(b->aux[c], b->fork, 0)) != cudaSuccess) return e;
     }
-    if (n16 > 0) {
-        e = launch_sweep_batch(b->d_probs, b->d_items, n16, b->d_counter, b->smem[0], b->item_pairs, 16, st);
+    int offset = 0, k = 0;
+    for (int c = 0; c < sail_batch_ctx::kClasses; ++c) {
+        if (count[c] == 0) continue;
+        cudaStream_t sc = k == 0 ? st : b->aux[k - 1];
+        e = launch_sweep_batch(b->d_probs, b->d_items + offset, count[c], b->d_counter + c, b->smem[c], b->item_pairs,
+                               c >= 3 ? 8 : 16, c % 3, sc);
         if (e != cudaSuccess) return e;
+        offset += count[c];
+        ++k;
     }
-    if (n8 > 0) {
-        cudaStream_t s8 = n16 > 0 ? b->aux : st;
-        e = launch_sweep_batch(b->d_probs, b->d_items + n16, n8, b->d_counter + 1, b->smem[1], b->item_pairs, 8, s8);
-        if (e != cudaSuccess) return e;
-    }
-    if (n16 > 0 && n8 > 0) {
-        if ((e = cudaEventRecord(b->join, b->aux)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(st, b->join, 0)) != cudaSuccess) return e;
+    for (int c = 0; c < used - 1; ++c) {
+        if ((e = cudaEventRecord(b->join[c], b->aux[c])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, b->join[c], 0)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -1082,7 +1095,7 @@ int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int a
     off += align_up(b->max_items * sizeof(BatchItem));
     b->d_counter = (int *)(b->ws + off);
     off += 256;
-    b->smem[0] = b->smem[1] = 0;
+    for (size_t &m : b->smem) m = 0;
     for (int k = 0; k < n; ++k) {
         size_t sub = 0;
         sail_workspace_size(probs[k].n_tau, probs[k].n_omega, &probs[k].params, &sub);
@@ -1095,7 +1108,7 @@ int sail_batch_create(sail_batch_t *out, int n, const sail_problem *probs, int a
             return rc;
         }
         b->h.push_back(h);
-        size_t &sm = b->smem[h->P.lanes == 8 ? 1 : 0];
+        size_t &sm = b->smem[batch_class(h->P)];
         sm = std::max(sm, sweep_fp32_table_bytes(h->P));
         off += align_up(sub);
     }
@@ -1157,7 +1170,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
     std::vector<BlockPending> pend(N);
     std::vector<int> cur(N), active(N);
     std::vector<BatchProblem> hp(N);
-    std::vector<BatchItem> items, items8;
+    std::vector<BatchItem> items, cls_items[sail_batch_ctx::kClasses];
     int done = 0;
     while (done < max_blocks) {
         bool any = false;
@@ -1173,8 +1186,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
         if (!any) break;
         for (;;) {
             // one segment: every problem with sweeps left in this block advances to its next resync
-            items.clear();
-            items8.clear();
+            for (auto &v : cls_items) v.clear();
             long long seg_moves = 0;
             for (int k = 0; k < N; ++k) {
                 sail_ctx *h = b->h[k];
@@ -1187,20 +1199,25 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 seg_moves += (long long)(hp[k].n1 - hp[k].n0) * h->prm.n_walkers * h->n_omega;
                 const int wpw = sweep_walkers_per_warp(h->P);
                 const int groups = (h->prm.n_walkers + wpw - 1) / wpw;
-                // walker groups per item = warps per block (at most 8 with 8 lanes per walker)
-                const int per = h->P.lanes == 8 ? std::min(b->item_pairs, 8) : b->item_pairs;
-                std::vector<BatchItem> &dst = h->P.lanes == 8 ? items8 : items;
+                // walker groups per item = warps per block (at most 8 with 8 lanes per walker, 12
+                // with 16)
+                const int per = std::min(b->item_pairs, h->P.lanes == 8 ? 8 : 12);
+                std::vector<BatchItem> &dst = cls_items[batch_class(h->P)];
                 for (int lo = 0; lo < groups; lo += per) dst.push_back(BatchItem{k, lo, std::min(lo + per, groups)});
             }
-            const int n16 = (int)items.size(), n8 = (int)items8.size();
-            items.insert(items.end(), items8.begin(), items8.end());
+            int count[sail_batch_ctx::kClasses];
+            items.clear();
+            for (int c = 0; c < sail_batch_ctx::kClasses; ++c) {
+                count[c] = (int)cls_items[c].size();
+                items.insert(items.end(), cls_items[c].begin(), cls_items[c].end());
+            }
             if (items.empty()) break;
             SAIL_CUDA(cudaMemcpyAsync(b->d_probs, hp.data(), (size_t)N * sizeof(BatchProblem), cudaMemcpyHostToDevice, st),
                       "batch H2D");
             SAIL_CUDA(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(BatchItem),
                                       cudaMemcpyHostToDevice, st), "batch H2D");
             cudaEventRecord(b->ev0, st);
-            cudaError_t e = batch_sweep_segment(b, n16, n8);
+            cudaError_t e = batch_sweep_segment(b, count);
             cudaEventRecord(b->ev1, st);
             if (e != cudaSuccess) return cuda_fail(e, "batched sweep launch");
             for (int k = 0; k < N; ++k) {
@@ -1242,7 +1259,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 if (rc) return rc;
                 cur[k] = hp[k].n1;
             }
-            b->sweep_launches += (n16 > 0) + (n8 > 0);
+            for (int c = 0; c < sail_batch_ctx::kClasses; ++c) b->sweep_launches += count[c] > 0;
             b->last_seg_moves = seg_moves;
             // walker-to-block mapping: time this launch, try the next candidate, keep the fastest
             if (b->tune_next < 3) {
@@ -1389,7 +1406,7 @@ int sail_server_create(sail_server_t *out, int max_resident, long long max_walke
     b.autotune = 1;
     b.item_pairs = kTuneCandidates[0];
     b.tune_next = 0;
-    b.smem[0] = b.smem[1] = 0;
+    for (size_t &m : b.smem) m = 0;
     batch_streams_create(&b);
     s->slot_off.assign(max_resident, 0);
     s->slot_size.assign(max_resident, 0);
@@ -1453,7 +1470,7 @@ int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_
             return rc;
         }
         b.h[slot] = h;
-        size_t &sm = b.smem[h->P.lanes == 8 ? 1 : 0];
+        size_t &sm = b.smem[batch_class(h->P)];
         sm = std::max(sm, sweep_fp32_table_bytes(h->P));
         s->slot_off[slot] = off;
         s->slot_size[slot] = r.bytes;

@@ -140,12 +140,15 @@ struct BatchProblem {
 struct BatchItem {      // walker groups [grp_lo, grp_hi) of problem prob, one group per warp
     int prob, grp_lo, grp_hi;
 };
-// Persistent FP32 sweep over many problems whose DevProblem.lanes all equal `lanes`: blocks of
-// `warps` warps (at most 8 when lanes = 8) take items from the queue.
+// Move-loop variant of a problem's FP32 sweep: 0 plain, 1 index walk, 2 Metropolis-Hastings.
+int sweep_mode(const DevProblem &P);
+// Persistent FP32 sweep over many problems whose DevProblem.lanes all equal `lanes` and whose
+// sweep_mode all equal `mode`: blocks of `warps` warps (at most 8 when lanes = 8, 12 when 16)
+// take items from the queue.
 cudaError_t launch_sweep_batch(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
-                               size_t smem, int warps, int lanes, cudaStream_t st);
+                               size_t smem, int warps, int lanes, int mode, cudaStream_t st);
 cudaError_t launch_sweep_batch8(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
-                                size_t smem, int warps, cudaStream_t st);
+                                size_t smem, int warps, int mode, cudaStream_t st);
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st);
 cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *bytes);
 

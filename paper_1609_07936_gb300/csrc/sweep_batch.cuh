@@ -1,6 +1,6 @@
-// Batched FP32 sweep: many inversions in one persistent launch per lane count (the move loop
-// of sweep_group.cuh).  sweep_batch8.cu and sweep_batch16.cu instantiate it for 8 and 16
-// lanes per walker.
+// Batched FP32 sweep: many inversions in one persistent launch per lane count and move-loop
+// variant (the move loop of sweep_group.cuh).  sweep_batch8.cu and sweep_batch16.cu
+// instantiate it for 8 and 16 lanes per walker.
 #pragma once
 #include "sweep_group.cuh"
 
@@ -42,8 +42,8 @@ __device__ __forceinline__ void run_group_c(const BatchProblem &BP, int grp, con
 // warp.  One launch serves the problems of one lane count G (its register budget differs);
 // the per-walker arithmetic is that of sweep_fp32_kernel, so a walker's trajectory does not
 // depend on which block, or which other problems, share the launch.
-template <int G>
-__global__ void __launch_bounds__(sweep_threads<G>()) sweep_batch_kernel(const BatchProblem *probs,
+template <int G, int MODE>
+__global__ void __launch_bounds__(sweep_threads<G, G == 8 ? 8 : 16>()) sweep_batch_kernel(const BatchProblem *probs,
                                                                         const BatchItem *items, int n_items,
                                                                         int *counter) {
     extern __shared__ float4 smem4[];
@@ -67,33 +67,29 @@ __global__ void __launch_bounds__(sweep_threads<G>()) sweep_batch_kernel(const B
         __syncthreads();
         const int grp = I.grp_lo + warp;
         if (grp >= I.grp_hi || BP.n0 >= BP.n1) continue;
-        if (BP.P.walk_len > 0)
-            run_group_c<G, kWalk>(BP, grp, sm);
-        else if (BP.P.hastings)
-            run_group_c<G, kHastings>(BP, grp, sm);
-        else
-            run_group_c<G, kPlain>(BP, grp, sm);
+        run_group_c<G, MODE>(BP, grp, sm);
     }
 }
 
-template <int G>
+template <int G, int MODE>
 cudaError_t launch_batch_g(const BatchProblem *d_probs, const BatchItem *d_items, int n_items, int *d_counter,
                            size_t smem, int warps, cudaStream_t st) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (warps > sweep_threads<G>() / 32) warps = sweep_threads<G>() / 32;
-    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    constexpr int kMaxWarps = sweep_threads<G, G == 8 ? 8 : 16>() / 32;
+    if (warps > kMaxWarps) warps = kMaxWarps;
+    cudaError_t e = cudaFuncSetAttribute(sweep_batch_kernel<G, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     // persistent: as many blocks as fit on the SMs at once
     int per_sm = 1;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_kernel<G>, warps * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batch_kernel<G, MODE>, warps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int blocks = n_items < sms * per_sm ? n_items : sms * per_sm;
-    sweep_batch_kernel<G><<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
+    sweep_batch_kernel<G, MODE><<<blocks, warps * 32, smem, st>>>(d_probs, d_items, n_items, d_counter);
     return cudaGetLastError();
 }
 

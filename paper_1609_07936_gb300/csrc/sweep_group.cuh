@@ -440,14 +440,15 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     }
 }
 
-// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker (128 registers a
-// thread), 8 warps with 8 lanes per walker (whose 4 walkers a warp hold twice the residual
-// elements per lane).
-template <int G>
-constexpr int sweep_threads() { return G == 8 ? 256 : kThreads; }
+// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker and up to 9 chunks
+// (128 registers a thread); 12 warps past 9 chunks (170 registers: the residual arrays grow
+// with the chunks); 8 warps with 8 lanes per walker (whose 4 walkers a warp hold twice the
+// residual elements per lane).
+template <int G, int C>
+constexpr int sweep_threads() { return G == 8 ? 256 : (C <= 9 ? kThreads : 384); }
 
 template <int G, int C, int MODE>
-__global__ void __launch_bounds__(sweep_threads<G>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
+__global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom Gm) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
@@ -492,7 +493,7 @@ cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cud
     Gm.groups_total = (P.n_walkers + WPW - 1) / WPW;
     const int ctas = Gm.groups_total < sms ? Gm.groups_total : sms;
     Gm.groups_per_cta = (Gm.groups_total + ctas - 1) / ctas;
-    const int max_warps = sweep_threads<G>() / 32;
+    const int max_warps = sweep_threads<G, C>() / 32;
     Gm.rounds = (Gm.groups_per_cta + max_warps - 1) / max_warps;
     Gm.warps = (Gm.groups_per_cta + Gm.rounds - 1) / Gm.rounds;
     const size_t tb = table_bytes(P);
