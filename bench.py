@@ -32,13 +32,13 @@ N_TAU, N_OMEGA, N_WALKERS = 200, 1000, 4096
 SWEEPS_PER_BLOCK, RESYNC_EVERY, N_SWEEPS = 100, 50, 20000
 NOISE = 1e-4
 WORKLOAD = (f"paper_scale_double_lorentz: N_tau={N_TAU} on [0,8], N_omega={N_OMEGA} on [0,20], "
-            f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, tensor-core resync every {RESYNC_EVERY} sweeps, "
+            f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, tensor-core (BF16 x6) resync every {RESYNC_EVERY} sweeps, "
             f"branching every {SWEEPS_PER_BLOCK} sweeps (f=1/4, t=0.1), {N_SWEEPS}-sweep schedule T 10->1e-9")
 METRIC = "walker-moves/sec"
 MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 
 
-RESYNC_KIND = 1    # residual recomputation on the tensor cores (tcgen05, TF32 x3)
+RESYNC_KIND = 2    # residual recomputation on the tensor cores (tcgen05, BF16, three pieces, six products)
 
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
@@ -414,7 +414,7 @@ def run_serve(args):
            "config": {"workload": f"served: Poisson arrivals {args.rate}/s for {args.duration} s ({len(arrivals)} requests), "
                                   f"sizes as the uneven batch, target chi2 <= 1.2 n_tau, budget {args.serve_sweeps} sweeps, "
                                   f"T 1e-2 chi2_0 -> 0.3 absolute, admission cap {cap / 1e9:.0f} GB",
-                      "resync": "tensor" if args.resync_kind == 1 else "fp32-fma"},
+                      "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6"}[args.resync_kind]},
            "wall_s": wall, "walker_moves_per_s": moves / wall,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "converged_fraction": float(conv.mean()),
@@ -435,6 +435,53 @@ def run_reference(args, rank, world):
            "cpu_baseline": cpu,
            "e2e": {"value": cpu["value"], "unit": "walker-moves/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """The precision configuration: 512 tau x 2048 bins, 16384 walkers, a 1-4 peak random
+    spectrum, FP32 moves.  For each residual recomputation (FP32-FMA GEMM, tcgen05 TF32 x3,
+    tcgen05 BF16 x6): two blocks of 50 sweeps with a recomputation every 10, its time per call
+    from CUDA events, and the error of the residual it leaves against an FP64 recomputation
+    from the same spectra on 256 sampled walkers (relative to the model value sum_j K_ij a_j)."""
+    import torch
+    import oracle as O
+    import paper_1609_07936_gb300 as sail
+    from workloads import precision_random_peaks
+    sail.load()
+    P = precision_random_peaks(0)
+    K, Fh, _ = O.tables(P.tau, P.F, P.sigma, P.omega)
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(P.n_walkers, 256, replace=False))
+    kinds, moves, sweep_ms = [], 0.0, 0.0
+    for kind, name in ((0, "fp32-fma"), (1, "tcgen05-tf32x3"), (2, "tcgen05-bf16x6")):
+        prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=100, sweeps_per_block=50,
+                          resync_every=10, branching=False, T_start=10.0, T_end=1e-3, A=P.A, B=P.B, seed=3,
+                          resync_kind=kind, timing=True)
+        g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
+        g.anneal()
+        torch.cuda.synchronize()
+        inf = g.info()
+        a, R, chi2, _, _ = g.state()
+        model = a[sample] @ K.T
+        err = np.abs(R[sample] - (Fh[None, :] - model))
+        rel = err / np.maximum(model, 1e-300)
+        kinds.append({"resync": name, "ms_per_call": inf["resync_ms"] / max(inf["resync_launches"], 1),
+                      "max_err_rel_model": float(rel.max()), "rms_err_rel_model": float(np.sqrt(np.mean(rel ** 2))),
+                      "max_err_over_sigma": float(err.max())})
+        moves += inf["moves"]
+        sweep_ms += inf["sweep_ms"]
+        g.close()
+    flop = 2.0 * P.n_walkers * P.n_omega * P.n_tau
+    for k in kinds:
+        k["useful_tflops"] = flop / (k["ms_per_call"] * 1e-3) / 1e12
+    out = {"metric": METRIC, "value": moves / (sweep_ms * 1e-3), "unit": "walker-moves/s", "n_gpus": 1,
+           "steps": 3, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "precision: 512 tau x 2048 bins, 16384 walkers, random 1-4 peaks, FP32 moves, "
+                                  "residual recomputation every 10 sweeps by each method",
+                      "step": "two blocks of 50 sweeps per recomputation method"},
+           "resync": kinds}
     print(json.dumps(out), flush=True)
 
 
@@ -497,14 +544,15 @@ def main():
     ap.add_argument("--cpu-sample-walkers", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band"])
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision"])
     ap.add_argument("--band-sweeps", type=int, default=20000, help="band example: sweep budget per inversion")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
-    ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1],
-                    help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05)")
+    ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1, 2],
+                    help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05 TF32 x3), "
+                         "2 = tensor cores (tcgen05 BF16 x6)")
     ap.add_argument("--index-walk", type=int, default=0, choices=range(8),
                     help="steps of the index walk choosing a move's bins (0: uniform bins, the paper's runs)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
@@ -525,6 +573,8 @@ def main():
         run_serve(args)
     elif args.workload == "band":
         run_band(args)
+    elif args.workload == "precision":
+        run_precision(args)
     else:
         run_gpu(args, rank, world, local_rank)
 

@@ -78,7 +78,8 @@ typedef struct sail_params {
     int timing;             /* 1: time every kernel with CUDA events on the handle's stream;
                                totals appear in sail_info */
     int resync_kind;        /* FP32 state: 0 = FP32-FMA GEMM with FP64 chunk sums, 1 = tensor
-                               cores (tcgen05 TF32, three-term split) */
+                               cores (tcgen05 TF32, three-term split), 2 = tensor cores
+                               (tcgen05 BF16, three pieces per operand and six products) */
     int wait_test;          /* test hook, 0 in use: 1 makes the tensor-core resync withhold its
                                first commit so its bounded wait runs out (sail_anneal then
                                returns SAIL_ETIMEOUT) */

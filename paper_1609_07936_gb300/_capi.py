@@ -27,6 +27,7 @@ SAIL_ESTATE = -4
 SAIL_ETIMEOUT = -5
 RESYNC_FP32 = 0
 RESYNC_TENSOR = 1
+RESYNC_TENSOR_BF16 = 2
 SCHEDULE_GEOMETRIC = 0
 SCHEDULE_SELF_COOLING = 1
 PREC_FP64 = 0

@@ -158,7 +158,7 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->move_scale < 1) || std::isnan(p->move_scale)) return fail(SAIL_EINVAL, "move_scale must be < 1");
     if (!std::isfinite(p->B)) return fail(SAIL_EINVAL, "B must be given (Sec. 2.2)");
     if (!(p->avg_chi2_factor >= 1)) return fail(SAIL_EINVAL, "avg_chi2_factor must be >= 1");
-    if (p->resync_kind != 0 && p->resync_kind != 1) return fail(SAIL_EINVAL, "resync_kind must be 0 or 1");
+    if (p->resync_kind < 0 || p->resync_kind > 2) return fail(SAIL_EINVAL, "resync_kind must be 0, 1 or 2");
     if (p->sweep_lanes != 0 && p->sweep_lanes != 8 && p->sweep_lanes != 16)
         return fail(SAIL_EINVAL, "sweep_lanes must be 0, 8 or 16");
     if (p->sweep_lanes == 8 && n_tau > 256) return fail(SAIL_EINVAL, "sweep_lanes = 8 needs n_tau <= 256");
@@ -1228,7 +1228,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 sail_batch_ctx::TcTune *tt = nullptr;
                 for (auto &t : b->tc)
                     if (t.pad == h->pad) tt = &t;
-                if (tt && h->prm.resync_kind == 1) {
+                if (tt && h->prm.resync_kind >= 1) {
                     if (tt->next < tt->n_cand) {
                         h->P.tc_cols = tt->cand[tt->next];
                         cudaEventCreate(&t0);

@@ -916,8 +916,8 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    *launches += kind == 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
-    return kind == 1 ? launch_resync_tc(P, S, status, st) : launch_resync_fp32(P, S, st);
+    *launches += kind >= 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
+    return kind >= 1 ? launch_resync_tc(P, S, status, kind == 2, st) : launch_resync_fp32(P, S, st);
 }
 
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,

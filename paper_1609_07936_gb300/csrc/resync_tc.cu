@@ -15,6 +15,12 @@
 // float pair (TwoSum, round to nearest), so the bias is that of 4 MMAs per tile and the sum
 // over tiles carries ~2^-44 relative error.
 //
+// BF16 variant (resync kind 2): each operand is split into three BF16 pieces,
+// x = x1 + x2 + x3 (each the round-to-nearest BF16 of what is left), and the products kept are
+// x1 y1 (main accumulator) and x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1 (correction accumulator);
+// the dropped terms are ~2^-24 of a product.  kind::f16 with BF16 A and B (both operands of
+// one MMA the same type), K = 16 per MMA.
+//
 // Block: 128 walkers (the MMA's M) x NC tau columns (NC <= 128, a multiple of 16; n_tau_pad
 // is split over gridDim.y blocks), 16 warps: warp w reads tensor-memory lanes
 // 32 (w % 4) .. +31 (its walkers) and columns (w / 4) NC/4 .. +NC/4.  Bins are taken 32 at a
@@ -27,6 +33,8 @@
 // residual by resync_chi2_kernel.
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "sail_internal.cuh"
 
 namespace sail {
@@ -37,37 +45,79 @@ constexpr int kM = 128;            // walkers per block (MMA M)
 constexpr int kKT = 32;            // bins per shared-memory tile
 constexpr int kThreads = 512;      // 16 warps
 constexpr uint32_t kLBO = 128;     // bytes between core matrices along K
-constexpr uint32_t kSBO = 1024;    // bytes between 8-row groups (8 core matrices of one row group)
 constexpr uint32_t kCorrCol = 128; // tensor-memory column of the correction accumulator
+
+// Operand format of a resync variant: element bytes, pieces per operand, and the byte stride
+// between 8-row groups of a [rows x 32] K-major tile (its core matrices of 8 rows x 16 bytes
+// laid side by side along K).
+template <bool BF16>
+struct Fmt {
+    static constexpr int kElem = BF16 ? 2 : 4;
+    static constexpr int kPieces = BF16 ? 3 : 2;
+    static constexpr int kPerCore = 16 / kElem;             // elements of a core-matrix row
+    static constexpr uint32_t kSBO = (kKT / kPerCore) * 128;  // 512 (BF16) or 1024 (TF32)
+    static constexpr int kSteps = kKT * kElem / 32;          // MMAs of K = 32 bytes per tile
+};
 constexpr uint32_t kCols = 256;    // tensor-memory columns allocated per block
 constexpr long long kSpinLimit = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Byte offset of element (row r, k) of a [rows x 32] K-major tile in the canonical layout.
+template <bool BF16>
 __device__ __forceinline__ uint32_t tile_off(int r, int k) {
-    return (uint32_t)(((r >> 3) * 8 + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+    using F = Fmt<BF16>;
+    return (uint32_t)(((r >> 3) * (kKT / F::kPerCore) + k / F::kPerCore) * 128 + (r & 7) * 16 +
+                      (k % F::kPerCore) * F::kElem);
 }
 
 // Shared-memory matrix descriptor: start address, leading (K) and stride (M/N) byte
 // offsets, descriptor version 1, no swizzle.
+template <bool BF16>
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
     return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+           ((uint64_t)((Fmt<BF16>::kSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, N and M.
+// Instruction descriptor: D FP32; A and B TF32 (kind::tf32) or BF16 (kind::f16); both
+// K-major; N and M.
+template <bool BF16>
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+    return (1u << 4) | ((BF16 ? 1u : 2u) << 7) | ((BF16 ? 1u : 2u) << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+template <bool BF16>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    if constexpr (BF16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// Writes the pieces of x at byte offset off of the tiles t[0..kPieces): TF32 high part and
+// remainder, or three BF16 pieces.
+template <bool BF16>
+__device__ __forceinline__ void put_pieces(unsigned char *const *t, uint32_t off, float x) {
+    if constexpr (BF16) {
+        const __nv_bfloat16 x1 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(x1);
+        const __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 x3 = __float2bfloat16_rn(r1 - __bfloat162float(x2));
+        *reinterpret_cast<__nv_bfloat16 *>(t[0] + off) = x1;
+        *reinterpret_cast<__nv_bfloat16 *>(t[1] + off) = x2;
+        *reinterpret_cast<__nv_bfloat16 *>(t[2] + off) = x3;
+    } else {
+        const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+        *reinterpret_cast<float *>(t[0] + off) = hi;
+        *reinterpret_cast<float *>(t[1] + off) = x - hi;
+    }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -108,15 +158,20 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
     lo += err;
 }
 
-template <int NC>   // tau columns per block, a multiple of 16, <= 128
+template <int NC, bool BF16>   // tau columns per block (a multiple of 16, <= 128); operand format
 __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevState S, int *status) {
+    using F = Fmt<BF16>;
     constexpr int CS = NC / 4;                    // columns per thread, a multiple of 4
+    constexpr int kATile = kM * kKT * F::kElem;   // bytes of one piece of the spectra tile
+    constexpr int kBTile = NC * kKT * F::kElem;   // bytes of one piece of the kernel tile
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *sAhi = smem;
-    unsigned char *sAlo = sAhi + kM * kKT * 4;
-    unsigned char *sBhi = sAlo + kM * kKT * 4;
-    unsigned char *sBlo = sBhi + NC * kKT * 4;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sBlo + NC * kKT * 4);
+    unsigned char *sA[F::kPieces], *sB[F::kPieces];
+#pragma unroll
+    for (int q = 0; q < F::kPieces; ++q) {
+        sA[q] = smem + q * kATile;
+        sB[q] = smem + F::kPieces * kATile + q * kBTile;
+    }
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + F::kPieces * (kATile + kBTile));
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mbar + 1);
     int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
@@ -142,7 +197,7 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
     const uint32_t mbar_a = smem_u32(mbar);
-    const uint32_t idesc = instr_desc(kM, NC);
+    const uint32_t idesc = instr_desc<BF16>(kM, NC);
     // wait_test: the first tile's MMAs and commit are withheld, so its wait runs out (test hook
     // for the time-out path; nothing is in flight when the block gives up)
     const long long spin = P.wait_test ? 1024 : kSpinLimit;
@@ -157,35 +212,50 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
     const int n_tiles = NOP / kKT;
     for (int t = 0; t < n_tiles; ++t) {
         const int j0 = t * kKT;
-        // spectra tile: 128 walkers x 32 bins, split into TF32 high part and remainder
+        // spectra tile: 128 walkers x 32 bins, split into pieces
         for (int q = tid; q < kM * kKT; q += kThreads) {
             const int r = q / kKT, k = q % kKT;
             const int w = w0 + r, j = j0 + k;
             const float x = (w < P.n_walkers && j < NO) ? S.b32[(size_t)w * NO + j] : 0.0f;
-            const float hi = tf32_hi(x);
-            const uint32_t off = tile_off(r, k);
-            *reinterpret_cast<float *>(sAhi + off) = hi;
-            *reinterpret_cast<float *>(sAlo + off) = x - hi;
+            put_pieces<BF16>(sA, tile_off<BF16>(r, k), x);
         }
-        // kernel tile: NC tau rows x 32 bins of the split K-major tables
+        // kernel tile: NC tau rows x 32 bins (TF32: the precomputed split tables; BF16: the
+        // FP32 table split here)
         for (int q = tid; q < NC * kKT; q += kThreads) {
-            const int r = q / kKT, k = q % kKT;
-            const uint32_t off = tile_off(r, k);
-            *reinterpret_cast<float *>(sBhi + off) = P.Khi32[(size_t)(i0 + r) * NOP + j0 + k];
-            *reinterpret_cast<float *>(sBlo + off) = P.Klo32[(size_t)(i0 + r) * NOP + j0 + k];
+            if constexpr (BF16) {
+                const int r = q % NC, k = q / NC;   // consecutive threads: consecutive tau
+                const int j = j0 + k;
+                const float kv = j < NO ? P.Khat32[(size_t)j * PAD + i0 + r] : 0.0f;
+                put_pieces<BF16>(sB, tile_off<BF16>(r, k), kv);
+            } else {
+                const int r = q / kKT, k = q % kKT;
+                const uint32_t off = tile_off<BF16>(r, k);
+                *reinterpret_cast<float *>(sB[0] + off) = P.Khi32[(size_t)(i0 + r) * NOP + j0 + k];
+                *reinterpret_cast<float *>(sB[1] + off) = P.Klo32[(size_t)(i0 + r) * NOP + j0 + k];
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (*abort_flag) break;
         if (tid == 0 && !(P.wait_test && t == 0)) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int ks = 0; ks < kKT / 8; ++ks) {
-                const uint32_t koff = (uint32_t)ks * 2 * kLBO;   // 8 TF32 = two core matrices along K
-                const uint64_t ahi = smem_desc(smem_u32(sAhi) + koff), alo = smem_desc(smem_u32(sAlo) + koff);
-                const uint64_t bhi = smem_desc(smem_u32(sBhi) + koff), blo = smem_desc(smem_u32(sBlo) + koff);
-                mma_tf32(tmem, ahi, bhi, idesc, ks > 0 ? 1u : 0u);               // main term
-                mma_tf32(tmem + kCorrCol, ahi, blo, idesc, ks > 0 ? 1u : 0u);    // corrections
-                mma_tf32(tmem + kCorrCol, alo, bhi, idesc, 1u);
+            for (int ks = 0; ks < F::kSteps; ++ks) {
+                const uint32_t koff = (uint32_t)ks * 2 * kLBO;   // 32 bytes of K = two core matrices
+                uint64_t a[F::kPieces], b[F::kPieces];
+#pragma unroll
+                for (int q = 0; q < F::kPieces; ++q) {
+                    a[q] = smem_desc<BF16>(smem_u32(sA[q]) + koff);
+                    b[q] = smem_desc<BF16>(smem_u32(sB[q]) + koff);
+                }
+                const uint32_t first = ks > 0 ? 1u : 0u;
+                mma<BF16>(tmem, a[0], b[0], idesc, first);                // main term
+                mma<BF16>(tmem + kCorrCol, a[0], b[1], idesc, first);     // corrections
+                mma<BF16>(tmem + kCorrCol, a[1], b[0], idesc, 1u);
+                if constexpr (BF16) {
+                    mma<BF16>(tmem + kCorrCol, a[0], b[2], idesc, 1u);
+                    mma<BF16>(tmem + kCorrCol, a[1], b[1], idesc, 1u);
+                    mma<BF16>(tmem + kCorrCol, a[2], b[0], idesc, 1u);
+                }
             }
             mma_commit(mbar_a);
         }
@@ -247,19 +317,45 @@ __global__ void resync_chi2_kernel(DevProblem P, DevState S) {
     if (lane == 0) S.chi2[w] = c2;
 }
 
-size_t tc_smem_bytes(int nc) { return (size_t)2 * kM * kKT * 4 + (size_t)2 * nc * kKT * 4 + 64; }
+template <bool BF16>
+size_t tc_smem_bytes(int nc) {
+    using F = Fmt<BF16>;
+    return (size_t)F::kPieces * ((size_t)kM * kKT + (size_t)nc * kKT) * F::kElem + 64;
+}
 
-template <int NC>
+template <int NC, bool BF16>
 cudaError_t launch_nc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st) {
-    const size_t smem = tc_smem_bytes(NC);
-    cudaError_t e = cudaFuncSetAttribute(resync_tc_kernel<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = tc_smem_bytes<BF16>(NC);
+    cudaError_t e =
+        cudaFuncSetAttribute(resync_tc_kernel<NC, BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((P.n_walkers + kM - 1) / kM, P.n_tau_pad / NC);
-    resync_tc_kernel<NC><<<grid, kThreads, smem, st>>>(P, S, status);
+    resync_tc_kernel<NC, BF16><<<grid, kThreads, smem, st>>>(P, S, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     resync_chi2_kernel<<<(P.n_walkers * 32 + 255) / 256, 256, 0, st>>>(P, S);
     return cudaGetLastError();
+}
+
+template <bool BF16>
+cudaError_t launch_tc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st) {
+    const int pad = P.n_tau_pad;
+    for (int nc = 128; nc >= 16; nc -= 16) {
+        if (pad % nc) continue;
+        if (P.tc_cols > 0 && nc != P.tc_cols) continue;
+        switch (nc) {
+            case 128: return launch_nc<128, BF16>(P, S, status, st);
+            case 112: return launch_nc<112, BF16>(P, S, status, st);
+            case 96: return launch_nc<96, BF16>(P, S, status, st);
+            case 80: return launch_nc<80, BF16>(P, S, status, st);
+            case 64: return launch_nc<64, BF16>(P, S, status, st);
+            case 48: return launch_nc<48, BF16>(P, S, status, st);
+            case 32: return launch_nc<32, BF16>(P, S, status, st);
+            case 16: return launch_nc<16, BF16>(P, S, status, st);
+            default: break;
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -267,24 +363,8 @@ cudaError_t launch_nc(const DevProblem &P, const DevState &S, int *status, cudaS
 // Columns per block: P.tc_cols if set (a multiple of 16 dividing n_tau_pad, <= 128), else
 // the widest such width.  Every width gives the same result bit for bit: each column's sum
 // runs over the same tiles in the same order.
-cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st) {
-    const int pad = P.n_tau_pad;
-    for (int nc = 128; nc >= 16; nc -= 16) {
-        if (pad % nc) continue;
-        if (P.tc_cols > 0 && nc != P.tc_cols) continue;
-        switch (nc) {
-            case 128: return launch_nc<128>(P, S, status, st);
-            case 112: return launch_nc<112>(P, S, status, st);
-            case 96: return launch_nc<96>(P, S, status, st);
-            case 80: return launch_nc<80>(P, S, status, st);
-            case 64: return launch_nc<64>(P, S, status, st);
-            case 48: return launch_nc<48>(P, S, status, st);
-            case 32: return launch_nc<32>(P, S, status, st);
-            case 16: return launch_nc<16>(P, S, status, st);
-            default: break;
-        }
-    }
-    return cudaErrorInvalidValue;
+cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, bool bf16, cudaStream_t st) {
+    return bf16 ? launch_tc<true>(P, S, status, st) : launch_tc<false>(P, S, status, st);
 }
 
 }  // namespace sail

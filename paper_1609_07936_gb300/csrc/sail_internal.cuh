@@ -106,9 +106,9 @@ cudaError_t launch_sweep_hastings(const DevProblem &P, const DevState &S, int sw
 cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
                           int *status, cudaStream_t st, int *launches);
 cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStream_t st);
-// Tensor-core (tcgen05, TF32 x3) residual recomputation for FP32 state; status[0] <- 1 on a
-// timed-out wait.
-cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, cudaStream_t st);
+// Tensor-core (tcgen05) residual recomputation for FP32 state, TF32 with a three-term split or
+// (bf16) BF16 with three pieces and six products; status[0] <- 1 on a timed-out wait.
+cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, bool bf16, cudaStream_t st);
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);

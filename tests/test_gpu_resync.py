@@ -1,8 +1,9 @@
 """GPU: the FP32-state residual recomputations against the FP64 oracle.
 
-Both paths compute R = Fhat - Khat a and chi2 = sum R^2 for every walker: the FP32-FMA GEMM
-with FP64 sums over 32-bin chunks (resync_kind 0) and the tcgen05 tensor-core GEMM in TF32
-with a three-term operand split and an FP32 tensor-memory accumulator (resync_kind 1).
+All paths compute R = Fhat - Khat a and chi2 = sum R^2 for every walker: the FP32-FMA GEMM
+with FP64 sums over 32-bin chunks (resync_kind 0), the tcgen05 tensor-core GEMM in TF32
+with a three-term operand split and an FP32 tensor-memory accumulator (resync_kind 1), and
+the same in BF16 with three pieces per operand and six products (resync_kind 2).
 The error bound per element is relative to the model value m_i = sum_j Khat_ij a_j (all
 terms are positive): 2e-6 m_i covers the FP32 accumulation of ~1000 terms and the ~2^-21
 operand precision of the split, plus the FP32 storage of R (6e-8 |R_i|).
@@ -39,13 +40,13 @@ def _check(P, W, kind, seed):
         assert abs(chi2[w] - c2) <= 2 * np.sum(np.abs(R_ref) * tol) + 1e-9 * c2
 
 
-@pytest.mark.parametrize("kind", [sail.RESYNC_FP32, sail.RESYNC_TENSOR])
+@pytest.mark.parametrize("kind", [sail.RESYNC_FP32, sail.RESYNC_TENSOR, sail.RESYNC_TENSOR_BF16])
 def test_resync_paper_scale(kind):
     """200 tau x 1000 bins, 300 walkers (two full 128-walker tiles and a ragged one)."""
     _check(paper_scale_double_lorentz(1e-4, n_walkers=300), 300, kind, 1)
 
 
-@pytest.mark.parametrize("kind", [sail.RESYNC_FP32, sail.RESYNC_TENSOR])
+@pytest.mark.parametrize("kind", [sail.RESYNC_FP32, sail.RESYNC_TENSOR, sail.RESYNC_TENSOR_BF16])
 def test_resync_tiny_and_wide(kind):
     """32 tau x 64 bins (one MMA of N = 32), and 512 tau x 2048 bins (two MMAs of N = 256)."""
     _check(tiny_double_lorentz(), 70, kind, 2)
@@ -57,7 +58,7 @@ def test_anneal_with_tensor_core_resync():
     sum rules and chi2 bookkeeping, like the FP32-FMA path."""
     P = paper_scale_double_lorentz(1e-4, n_walkers=512)
     out = {}
-    for kind in (0, 1):
+    for kind in (0, 1, 2):
         g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
                       sail.Params(n_walkers=512, precision=sail.PREC_FP32, n_sweeps=2000, sweeps_per_block=20,
                                   resync_every=10, branching=True, T_start=10.0, T_end=1e-9, A=P.A, B=P.B,
@@ -73,3 +74,4 @@ def test_anneal_with_tensor_core_resync():
             assert abs(chi2[w] - c2) <= 1e-5 * c2
     # the two paths see the same statistics to within the rounding-driven divergence of chains
     assert abs(out[0][0][-1]["acceptance"] - out[1][0][-1]["acceptance"]) < 0.02
+    assert abs(out[0][0][-1]["acceptance"] - out[2][0][-1]["acceptance"]) < 0.02
