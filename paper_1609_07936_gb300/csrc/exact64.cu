@@ -196,48 +196,51 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
 // reweighting a_j <- a_j kappa (1 + lambda (x_j - c)), c = sum a x / sum a, with
 // kappa = A / sum a and lambda = (B/A - c) / var, which changes each bin by a factor
 // 1 + O(1e-6) and keeps a >= 0.
-__device__ void block_sum2(double &u, double &v, double *red) {
+// FP32 state drifts off the two sum rules by rounding; each walker is put back with the
+// affine reweighting b_j <- b_j kappa (1 + lambda (x_j - c)): c = B'/A', kappa = A / A',
+// lambda = (B/A - c) / var', where A' = sum b, B' = sum b x and var' = sum b x^2 / A' - c^2 are
+// the walker's current moments (lambda = 0 if the tilt could make a factor negative).  One
+// warp per walker, one pass for the moments: FP32 per bin, in the offset t_j = x_j - x_mid =
+// (j - (N-1)/2) dw from the grid's midpoint (uniform bins), with compensated per-lane sums and
+// FP64 across lanes; the factor is applied in FP32, the state's own precision (FP64 runs at a
+// small fraction of the FP32 rate on this GPU).
+__device__ __forceinline__ void kahan_add(float &s, float &comp, float v) {
+    const float y = v - comp;
+    const float t = s + y;
+    comp = (t - s) - y;
+    s = t;
+}
+
+__global__ void __launch_bounds__(256) restore_kernel(DevProblem P, DevState S) {
+    const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= P.n_walkers) return;
+    float *b = S.b32 + (size_t)w * P.n_omega;
+    const float dw = (float)P.dw, half = 0.5f * (float)(P.n_omega - 1);
+    float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f, a2 = 0.f, c2 = 0.f;
+    for (int j = lane; j < P.n_omega; j += 32) {
+        const float v = b[j], xj = ((float)j - half) * dw;
+        kahan_add(a0, c0, v);
+        kahan_add(a1, c1, v * xj);
+        kahan_add(a2, c2, v * xj * xj);
+    }
+    double s0 = (double)a0 - (double)c0, s1 = (double)a1 - (double)c1, s2 = (double)a2 - (double)c2;
     for (int o = 16; o > 0; o >>= 1) {
-        u += __shfl_xor_sync(kFull, u, o);
-        v += __shfl_xor_sync(kFull, v, o);
+        s0 += __shfl_xor_sync(0xFFFFFFFFu, s0, o);
+        s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
+        s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = (int)(blockDim.x >> 5);
-    __syncthreads();
-    if (lane == 0) { red[warp] = u; red[32 + warp] = v; }
-    __syncthreads();
-    u = 0.0;
-    v = 0.0;
-    for (int k = 0; k < nw; ++k) { u += red[k]; v += red[32 + k]; }
-}
-
-__device__ void restore_sum_rules(const DevProblem &P, float *b, double *red) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x) {
-        s0 += (double)b[j];
-        s1 += (double)b[j] * P.x64[j];
-    }
-    block_sum2(s0, s1, red);
     if (!(s0 > 0.0)) return;
-    const double c = s1 / s0;
-    double v2 = 0.0, unused = 0.0;
-    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x) {
-        const double dx = P.x64[j] - c;
-        v2 += (double)b[j] * dx * dx;
-    }
-    block_sum2(v2, unused, red);
-    const double var = v2 / s0;
+    const double xmid = 0.5 * (P.x64[0] + P.x64[P.n_omega - 1]);
+    const double c = s1 / s0;                               // centre, as an offset from xmid
+    const double var = s2 / s0 - c * c;
     const double kappa = P.A / s0;
-    double lambda = var > 0.0 ? (P.B / P.A - c) / var : 0.0;
-    if (!(fabs(lambda * (P.x64[P.n_omega - 1] - P.x64[0])) < 0.5)) lambda = 0.0;
-    __syncthreads();
-    for (int j = threadIdx.x; j < P.n_omega; j += blockDim.x)
-        b[j] = (float)((double)b[j] * (kappa * (1.0 + lambda * (P.x64[j] - c))));
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(128) restore_kernel(DevProblem P, DevState S) {
-    __shared__ double red[64];
-    restore_sum_rules(P, S.b32 + (size_t)blockIdx.x * P.n_omega, red);
+    double lambda = var > 0.0 ? (P.B / P.A - xmid - c) / var : 0.0;
+    if (!(fabs(lambda * (P.n_omega - 1) * P.dw) < 0.5)) lambda = 0.0;
+    const float kf = (float)kappa, lk = (float)(kappa * lambda), cf = (float)c;
+    for (int j = lane; j < P.n_omega; j += 32) {
+        const float xj = ((float)j - half) * dw;
+        b[j] = b[j] * fmaf(lk, xj - cf, kf);
+    }
 }
 
 __global__ void __launch_bounds__(128) resync_kernel(DevProblem P, DevState S, int precision) {
@@ -911,7 +914,7 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         return cudaGetLastError();
     }
     if (restore) {
-        restore_kernel<<<P.n_walkers, 128, 0, st>>>(P, S);
+        restore_kernel<<<(P.n_walkers * 32 + 255) / 256, 256, 0, st>>>(P, S);
         *launches += 1;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -7,7 +7,7 @@
 // products with FP64 summation across the whole bin range: the rounding left in
 // F/sigma ~ 1e4-1e5 minus a model of the same size stays far below 1.  chi2 is summed in
 // FP64 from the FP64 residual.  Before it, for FP32 state only,
-// the spectra can be put back on both sum rules (see restore_sum_rules in exact64.cu).
+// the spectra can be put back on both sum rules (restore_kernel in exact64.cu).
 #include <cstdint>
 
 #include "sail_internal.cuh"

@@ -101,22 +101,40 @@ __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uin
             "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// Writes the pieces of x at byte offset off of the tiles t[0..kPieces): TF32 high part and
-// remainder, or three BF16 pieces.
+// Writes one core-matrix row (kPerCore consecutive K elements, 16 bytes) of every piece of the
+// values v at byte offset off of the tiles t[0..kPieces): the TF32 high part and the remainder,
+// or three BF16 pieces, each the round-to-nearest BF16 of what is left.
 template <bool BF16>
-__device__ __forceinline__ void put_pieces(unsigned char *const *t, uint32_t off, float x) {
+__device__ __forceinline__ void put_row(unsigned char *const *t, uint32_t off, const float *v) {
     if constexpr (BF16) {
-        const __nv_bfloat16 x1 = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(x1);
-        const __nv_bfloat16 x2 = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 x3 = __float2bfloat16_rn(r1 - __bfloat162float(x2));
-        *reinterpret_cast<__nv_bfloat16 *>(t[0] + off) = x1;
-        *reinterpret_cast<__nv_bfloat16 *>(t[1] + off) = x2;
-        *reinterpret_cast<__nv_bfloat16 *>(t[2] + off) = x3;
+        uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            __nv_bfloat16 p1[2], p2[2], p3[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float x = v[e + h];
+                p1[h] = __float2bfloat16_rn(x);
+                const float r1 = x - __bfloat162float(p1[h]);
+                p2[h] = __float2bfloat16_rn(r1);
+                p3[h] = __float2bfloat16_rn(r1 - __bfloat162float(p2[h]));
+            }
+            w1[e / 2] = (uint32_t)__bfloat16_as_ushort(p1[0]) | ((uint32_t)__bfloat16_as_ushort(p1[1]) << 16);
+            w2[e / 2] = (uint32_t)__bfloat16_as_ushort(p2[0]) | ((uint32_t)__bfloat16_as_ushort(p2[1]) << 16);
+            w3[e / 2] = (uint32_t)__bfloat16_as_ushort(p3[0]) | ((uint32_t)__bfloat16_as_ushort(p3[1]) << 16);
+        }
+        *reinterpret_cast<uint4 *>(t[0] + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4 *>(t[1] + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        *reinterpret_cast<uint4 *>(t[2] + off) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
     } else {
-        const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-        *reinterpret_cast<float *>(t[0] + off) = hi;
-        *reinterpret_cast<float *>(t[1] + off) = x - hi;
+        float hi[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            hi[e] = __uint_as_float(__float_as_uint(v[e]) & 0xFFFFE000u);
+            lo[e] = v[e] - hi[e];
+        }
+        *reinterpret_cast<float4 *>(t[0] + off) = make_float4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<float4 *>(t[1] + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
     }
 }
 
@@ -212,26 +230,36 @@ __global__ void __launch_bounds__(kThreads) resync_tc_kernel(DevProblem P, DevSt
     const int n_tiles = NOP / kKT;
     for (int t = 0; t < n_tiles; ++t) {
         const int j0 = t * kKT;
-        // spectra tile: 128 walkers x 32 bins, split into pieces
-        for (int q = tid; q < kM * kKT; q += kThreads) {
-            const int r = q / kKT, k = q % kKT;
-            const int w = w0 + r, j = j0 + k;
-            const float x = (w < P.n_walkers && j < NO) ? S.b32[(size_t)w * NO + j] : 0.0f;
-            put_pieces<BF16>(sA, tile_off<BF16>(r, k), x);
+        // spectra tile: 128 walkers x 32 bins, split into pieces.  A thread writes whole
+        // core-matrix rows (16 bytes of every piece); consecutive threads take consecutive
+        // walkers, so a warp's stores fill 128-byte core matrices without bank conflicts.
+        constexpr int PC = F::kPerCore, RC = kKT / PC;   // row chunks per tile row
+        for (int q = tid; q < kM * RC; q += kThreads) {
+            const int r = q % kM, kc = q / kM;
+            const int w = w0 + r, jb = j0 + kc * PC;
+            float v[PC];
+#pragma unroll
+            for (int e = 0; e < PC; ++e)
+                v[e] = (w < P.n_walkers && jb + e < NO) ? S.b32[(size_t)w * NO + jb + e] : 0.0f;
+            put_row<BF16>(sA, tile_off<BF16>(r, kc * PC), v);
         }
         // kernel tile: NC tau rows x 32 bins (TF32: the precomputed split tables; BF16: the
-        // FP32 table split here)
-        for (int q = tid; q < NC * kKT; q += kThreads) {
+        // FP32 table split here), written the same way
+        for (int q = tid; q < NC * RC; q += kThreads) {
+            const int r = q % NC, kc = q / NC;
+            const uint32_t off = tile_off<BF16>(r, kc * PC);
             if constexpr (BF16) {
-                const int r = q % NC, k = q / NC;   // consecutive threads: consecutive tau
-                const int j = j0 + k;
-                const float kv = j < NO ? P.Khat32[(size_t)j * PAD + i0 + r] : 0.0f;
-                put_pieces<BF16>(sB, tile_off<BF16>(r, k), kv);
+                float v[PC];
+#pragma unroll
+                for (int e = 0; e < PC; ++e) {
+                    const int j = j0 + kc * PC + e;
+                    v[e] = j < NO ? P.Khat32[(size_t)j * PAD + i0 + r] : 0.0f;
+                }
+                put_row<BF16>(sB, off, v);
             } else {
-                const int r = q / kKT, k = q % kKT;
-                const uint32_t off = tile_off<BF16>(r, k);
-                *reinterpret_cast<float *>(sB[0] + off) = P.Khi32[(size_t)(i0 + r) * NOP + j0 + k];
-                *reinterpret_cast<float *>(sB[1] + off) = P.Klo32[(size_t)(i0 + r) * NOP + j0 + k];
+                const size_t g = (size_t)(i0 + r) * NOP + j0 + kc * PC;   // 16-byte aligned: NOP % 32 == 0
+                *reinterpret_cast<float4 *>(sB[0] + off) = *reinterpret_cast<const float4 *>(P.Khi32 + g);
+                *reinterpret_cast<float4 *>(sB[1] + off) = *reinterpret_cast<const float4 *>(P.Klo32 + g);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
