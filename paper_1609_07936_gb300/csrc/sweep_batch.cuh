@@ -1,5 +1,7 @@
 // Batched FP32 sweep: many inversions in one persistent launch per lane count and move-loop
-// variant (the move loop of sweep_group.cuh).  sweep_batch8.cu and sweep_batch16.cu
+// variant (the move loop of sweep_group.cuh).  A launch holds the loops of every chunk count in
+// one body; the one-move-at-a-time loop (run_group) fits that body's registers without spills,
+// the look-ahead loop does not, so the batch keeps the former.  sweep_batch8.cu and sweep_batch16.cu
 // instantiate it for 8 and 16 lanes per walker.
 #pragma once
 #include "sweep_group.cuh"

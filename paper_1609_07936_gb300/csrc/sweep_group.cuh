@@ -440,12 +440,321 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     }
 }
 
-// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker and up to 9 chunks
-// (128 registers a thread); 12 warps past 9 chunks (170 registers: the residual arrays grow
-// with the chunks); 8 warps with 8 lanes per walker (whose 4 walkers a warp hold twice the
-// residual elements per lane).
+// The look-ahead move loop, for uniform bins (the plain and the Hastings variants).
+//
+// A proposal that would make an amplitude negative, or (Hastings) whose reverse move cannot be
+// proposed, is rejected before its kernel columns matter: about 40% of the moves at paper
+// scale.  A move's bins, amplitude and threshold do not depend on the spectrum; its
+// feasibility does, through b_p, b_s and the scale g only.  So each walker keeps its next 2G
+// proposals drawn (lane l of its group holds proposals wb + l, window A, and wb + G + l,
+// window B), tests all of them at once against the spectrum, takes the first feasible one by a
+// ballot, counts the infeasible ones before it as rejected moves, and spends columns, reduction
+// and Metropolis test on feasible moves only.  The chain is the sequential one move for move:
+// the same draws, decisions and arithmetic, in the same order.
+//
+// The walkers of a warp run through their sweeps independently (each has its own move index
+// and sweep); the warp loops until all have finished.  Pipelining: while move k's delta chi2 is
+// reduced, the later proposals' feasibility is evaluated for both outcomes of move k and the
+// columns of the first proposal feasible if move k is rejected are loaded; after the test the
+// outcome picks the flags, and if they name another move (acceptance changed a feasibility,
+// rarely), its columns are loaded then.
+template <int G, int C, bool STAGED, int MODE>
+__device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
+                                                const float *sm, float *b_stage, int walker_lo) {
+    static_assert(MODE != kWalk, "the index walk chooses its bins from the spectrum: run_group");
+    constexpr int E = 32 / G;          // floats of a 32-tau chunk per lane
+    constexpr int H = E / 2;           // float pairs of a chunk per lane
+    constexpr int WPW = 32 / G;        // walkers per warp
+    constexpr bool PIPE = C <= 8;      // registers for the prefetched columns (see run_group)
+    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+    const float *sQhi = sm;
+    const float *sQlo = sQhi + (size_t)NH * PAD;
+    const float *sBeta = sQlo + (size_t)32 * PAD;
+    const float *sRgap = sBeta + NO;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1), sub = lane / G;
+    const uint32_t qhi = (uint32_t)__cvta_generic_to_shared(sQhi) + 4u * E * gl;
+    const uint32_t qlo = (uint32_t)__cvta_generic_to_shared(sQlo) + 4u * E * gl;
+    const uint2 key = philox_key(P.seed);
+    const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
+
+    const int w = WPW * grp + sub;
+    const bool active = w < P.n_walkers;
+    const int wr = active ? w : WPW * grp;            // a valid walker to read from
+    float *b = STAGED ? b_stage + (size_t)(wr - walker_lo) * NO : S.b32 + (size_t)wr * NO;
+    const uint32_t bsh = STAGED ? (uint32_t)__cvta_generic_to_shared(b) : 0u;
+    auto bget = [&](int j) -> float {
+        if constexpr (STAGED) {
+            float v;
+            asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(bsh + 4u * (uint32_t)j));
+            return v;
+        } else {
+            return b[j];
+        }
+    };
+    auto bset = [&](int j, float v) {
+        if constexpr (STAGED)
+            asm volatile("st.shared.f32 [%0], %1;" ::"r"(bsh + 4u * (uint32_t)j), "f"(v) : "memory");
+        else
+            b[j] = v;
+    };
+
+    f2 R[C][H], M[C][H];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const int i = 32 * c + E * gl + 2 * h;
+            const float2 r2 = *reinterpret_cast<const float2 *>(S.R32 + (size_t)wr * PAD + i);
+            const float2 f2v = *reinterpret_cast<const float2 *>(P.Fhat32 + i);
+            R[c][h] = pk(r2.x, r2.y);
+            M[c][h] = pk(f2v.x - r2.x, f2v.y - r2.y);
+        }
+    }
+    float ghi = S.g2[2 * wr], glo = S.g2[2 * wr + 1];
+    double chi2 = S.chi2[wr];
+    int accp = S.acc_prev[wr];
+    unsigned nacc = 0, npos = 0;       // this launch's accepted and positivity-rejected moves
+    const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
+
+    // the walker's sweep (the same in all G lanes of its group)
+    int n = n0;
+    bool done = !active || n0 >= n1;
+    float T = 0.0f, yd = 0.0f, dchi = 0.0f;
+    int acc = 0, pos = 0;
+    int wb = 0;                        // window A = proposals [wb, wb + G), B = [wb + G, wb + 2G)
+    int lo = 0;                        // the first proposal not yet consumed
+    MoveDraw pa, pb;                   // this lane's proposals wb + gl and wb + G + gl
+    pa.ps = pb.ps = 1 << 16;           // valid bins for walkers that draw nothing
+    pa.eps = pb.eps = pa.thr = pb.thr = pa.dp = pb.dp = pa.ds = pb.ds = 0.0f;
+    auto start_sweep = [&]() {
+        T = (float)P.Tsweep[n];
+        yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
+        acc = pos = 0;
+        dchi = 0.0f;
+        wb = lo = 0;
+        pa = draw_move<MODE>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        pb = draw_move<MODE>(G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+    };
+    // slide the windows by G once the current move lies in window B
+    auto slide = [&]() {
+        pa = pb;
+        wb += G;
+        pb = draw_move<MODE>(wb + G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+    };
+    if (!done) start_sweep();
+
+    const int base = sub * G;
+    const uint32_t lowG = G == 32 ? kFull : (1u << G) - 1u;
+    // bit t of the result: proposal wb + t of this lane's walker (A's lanes, then B's)
+    auto group_bits = [&](bool in_a, bool in_b) -> uint32_t {
+        const uint32_t ba = (__ballot_sync(kFull, in_a) >> base) & lowG;
+        const uint32_t bb = (__ballot_sync(kFull, in_b) >> base) & lowG;
+        return ba | (bb << G);
+    };
+    auto below = [](int t) -> uint32_t { return t >= 32 ? kFull : (1u << t) - 1u; };
+    // positivity rejections among the proposals from lo up to bit t (t < 0: all the windows');
+    // a plain move is infeasible only by positivity, so there the count is the skipped span
+    auto count_pos = [&](uint32_t pfm, int t) -> int {
+        if constexpr (MODE == kHastings) return __popc(pfm & below(t < 0 ? 2 * G : t));
+        else return max(0, min(wb + (t < 0 ? 2 * G : t), NO) - lo);
+    };
+    // proposal wb + t, from the lane that holds it (t >= 0; every lane calls)
+    auto take_bit = [&](int t) -> MoveDraw { return take_move(t < G ? pa : pb, t & (G - 1), G); };
+    // feasibility of proposal q (number idx) on the spectrum as it is now
+    auto feasible_now = [&](const MoveDraw &q, int idx, bool live, bool &ok, bool &pf) {
+        const bool valid = live && idx >= lo && idx < NO;
+        const int qp = q.ps & 0xFFFF, qs = q.ps >> 16;
+        const float rq = 1.0f - q.eps;
+        const float ap = fmaf(rq, ghi * bget(qp), q.dp), as = fmaf(rq, ghi * bget(qs), q.ds);
+        const bool posok = ap >= 0.0f && as >= 0.0f;
+        const bool hok = MODE != kHastings || q.thr > -INFINITY;
+        ok = valid && posok && hok;
+        pf = valid && !posok;
+    };
+
+    MoveDraw cur = pa;                 // the move evaluated next: feasible, proposal number icur
+    int icur = 0;
+    bool need = !done;                 // the walker has no current move: search from lo
+    bool load = false;                 // cur's columns are still to be loaded
+    f2 dcur[PIPE ? C : 1][H];
+    for (;;) {
+        // ---- walkers without a current move search their windows (a sweep's start, or no
+        // feasible proposal left in the windows), sliding them and ending sweeps as needed
+        while (__any_sync(kFull, need)) {
+            bool oa, fa, ob, fb;
+            feasible_now(pa, wb + gl, need, oa, fa);
+            feasible_now(pb, wb + G + gl, need, ob, fb);
+            const uint32_t okm = group_bits(oa, ob);
+            const uint32_t pfm = MODE == kHastings ? group_bits(fa, fb) : 0u;
+            const int t = __ffs(okm) - 1;
+            const MoveDraw found = take_bit(t < 0 ? 0 : t);
+            if (need) {
+                pos += count_pos(pfm, t);
+                if (t >= 0) {
+                    cur = found;
+                    icur = wb + t;
+                    lo = icur + 1;
+                    need = false;
+                    load = true;
+                    if (t >= G) slide();
+                } else if (wb + 2 * G >= NO) {
+                    // the sweep is over
+                    chi2 += (double)dchi;
+                    accp = acc;
+                    nacc += acc;
+                    npos += pos;
+                    if (S.acc_trace && gl == 0) S.acc_trace[(size_t)n * P.n_walkers + w] = acc;
+                    if (++n >= n1) {
+                        done = true;
+                        need = false;
+                    } else {
+                        start_sweep();
+                    }
+                } else {
+                    wb += 2 * G;
+                    lo = wb;
+                    pa = draw_move<MODE>(wb + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+                    pb = draw_move<MODE>(wb + G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+                }
+            }
+        }
+        if (!__any_sync(kFull, !done)) break;
+        const bool live = !done;
+        if constexpr (PIPE) {
+            if (load) columns<G, C>(dcur, qhi, qlo, PAD, cur);
+            load = false;
+        }
+        // move icur: the amplitudes it would set, and d = eps M + dpart
+        const int p = cur.ps & 0xFFFF, s = cur.ps >> 16;
+        const float r = 1.0f - cur.eps;
+        const float ap = fmaf(r, ghi * bget(p), cur.dp);
+        const float as = fmaf(r, ghi * bget(s), cur.ds);
+        const f2 e2 = pk(cur.eps, cur.eps);
+        f2 d[C][H];
+        if constexpr (PIPE) {
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], dcur[c][h]);
+        } else {
+            columns<G, C>(d, qhi, qlo, PAD, cur);
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+#pragma unroll
+                for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], d[c][h]);
+        }
+        // the spectrum if the move is accepted: scale g r, b_p and b_s as the update writes them
+        float gah = ghi, gal = glo;
+        pair_scale(gah, gal, r);
+        const float inv_g = 1.0f / gah;
+        const float bpn = ap * inv_g, bsn = as * inv_g;
+        // the later proposals' feasibility for either outcome of this move
+        bool rA, fA, aA, gA, rB, fB, aB, gB;
+        auto feasible_both = [&](const MoveDraw &q, int idx, bool &okr, bool &pfr, bool &oka, bool &pfa) {
+            const bool valid = live && idx >= lo && idx < NO;
+            const int qp = q.ps & 0xFFFF, qs = q.ps >> 16;
+            const float rq = 1.0f - q.eps;
+            const float vp = bget(qp), vs = bget(qs);
+            const float vpa = qp == p ? bpn : (qp == s ? bsn : vp);
+            const float vsa = qs == p ? bpn : (qs == s ? bsn : vs);
+            const bool posr = fmaf(rq, ghi * vp, q.dp) >= 0.0f && fmaf(rq, ghi * vs, q.ds) >= 0.0f;
+            const bool posa = fmaf(rq, gah * vpa, q.dp) >= 0.0f && fmaf(rq, gah * vsa, q.ds) >= 0.0f;
+            const bool hok = MODE != kHastings || q.thr > -INFINITY;
+            okr = valid && posr && hok;
+            pfr = valid && !posr;
+            oka = valid && posa && hok;
+            pfa = valid && !posa;
+        };
+        feasible_both(pa, wb + gl, rA, fA, aA, gA);
+        feasible_both(pb, wb + G + gl, rB, fB, aB, gB);
+        const uint32_t okr = group_bits(rA, rB), oka = group_bits(aA, aB);
+        uint32_t pfr = 0, pfa = 0;
+        if constexpr (MODE == kHastings) {
+            pfr = group_bits(fA, fB);
+            pfa = group_bits(gA, gB);
+        }
+        const int tr = __ffs(okr) - 1;
+        if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, take_bit(tr < 0 ? 0 : tr));
+        // move icur: delta chi2 = sum d (2 R + d) and the Metropolis test (the Hastings
+        // threshold may be negative: then D <= 0 does not pass by itself)
+        const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
+        const bool accepted = live && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr));
+        if (accepted) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    R[c][h] = add2(R[c][h], d[c][h]);
+                    M[c][h] = fma2(minus_one, d[c][h], M[c][h]);
+                }
+            }
+            ghi = gah;
+            glo = gal;
+            if (gl == 0) {
+                bset(p, bpn);
+                bset(s, bsn);
+            }
+            dchi += D;
+            ++acc;
+        }
+        __syncwarp();
+        // the next move: the first feasible proposal for the outcome
+        const uint32_t okm = accepted ? oka : okr, pfm = accepted ? pfa : pfr;
+        const int t = __ffs(okm) - 1;
+        const MoveDraw nxt = take_bit(t < 0 ? 0 : t);
+        if (live) {
+            pos += count_pos(pfm, t);
+            if (t < 0) {
+                need = true;
+                lo = wb + 2 * G;
+            } else {
+                icur = wb + t;
+                lo = icur + 1;
+                cur = nxt;
+                load = t != tr;        // not the prefetched move: its columns are loaded first
+                if (t >= G) slide();
+            }
+        }
+    }
+    if (!active) return;
+    // fold the common scale into the spectrum and write the walker back
+    float *bg = S.b32 + (size_t)w * NO;
+    for (int j = gl; j < NO; j += G) {
+        const float v = b[j];
+        bg[j] = fmaf(glo, v, ghi * v);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+            *reinterpret_cast<float2 *>(S.R32 + (size_t)w * PAD + 32 * c + E * gl + 2 * h) = up(R[c][h]);
+    if (gl == 0) {
+        S.g2[2 * w] = 1.0f;
+        S.g2[2 * w + 1] = 0.0f;
+        S.chi2[w] = chi2;
+        S.acc_prev[w] = accp;
+        S.n_acc[w] += nacc;
+        S.n_pos[w] += npos;
+    }
+}
+
+// The move loop of a variant: the index walk's bins depend on the spectrum, so it proposes
+// and evaluates one move at a time; the uniform-bin variants look ahead.
+template <int G, int C, bool STAGED, int MODE>
+__device__ __forceinline__ void run_walkers(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
+                                            const float *sm, float *b_stage, int walker_lo) {
+    if constexpr (MODE == kWalk)
+        run_group<G, C, STAGED, MODE>(P, S, n0, n1, grp, sm, b_stage, walker_lo);
+    else
+        run_group_ahead<G, C, STAGED, MODE>(P, S, n0, n1, grp, sm, b_stage, walker_lo);
+}
+
+// Threads per block of the sweep kernels: 16 warps with 16 lanes per walker and up to 4
+// chunks, or 9 (the first count without prefetched columns): 128 registers a thread; 12 warps
+// otherwise (168 registers: the residual arrays grow with the chunks); 8 warps with 8 lanes per
+// walker (whose 4 walkers a warp hold twice the residual elements per lane).
 template <int G, int C>
-constexpr int sweep_threads() { return G == 8 ? 256 : (C <= 9 ? kThreads : 384); }
+constexpr int sweep_threads() { return G == 8 ? 256 : ((C <= 4 || C == 9) ? kThreads : 384); }
 
 template <int G, int C, int MODE>
 __global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
@@ -471,9 +780,9 @@ __global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevPr
         const int grp = grp_lo + round * Gm.warps + warp;
         if (grp >= grp_hi) break;                         // uniform across the warp
         if (Gm.stage_b)
-            run_group<G, C, true, MODE>(P, S, n0, n1, grp, sm, sB, walker_lo);
+            run_walkers<G, C, true, MODE>(P, S, n0, n1, grp, sm, sB, walker_lo);
         else
-            run_group<G, C, false, MODE>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
+            run_walkers<G, C, false, MODE>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
     }
 }
 
