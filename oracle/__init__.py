@@ -61,6 +61,7 @@ class OrParams(ctypes.Structure):
         ("walk_len", ctypes.c_int),
         ("walk_uniform", ctypes.c_double),
         ("hastings", ctypes.c_int),
+        ("shared_bins", ctypes.c_int),
     ]
 
 
@@ -319,13 +320,15 @@ class Schedule:
     walk_len: int = 0            # steps of the index walk (Sec. 2.3)
     walk_uniform: float = 0.0    # probability an index skips its walk
     hastings: bool = False       # Metropolis-Hastings acceptance with the move's Jacobian
+    shared_bins: int = 0         # W > 1: the walkers of each group of W propose the same bins
 
     def c(self) -> OrParams:
         return OrParams(self.n_sweeps, self.sweeps_per_block, self.resync_every, int(self.branching),
                         self.T_start, self.T_end, self.branch_fraction, self.imprint_t,
                         self.move_scale, self.y_p, self.y_m, self.y_min, self.seed,
                         int(self.schedule_kind), int(self.adaptive), self.cool_begin, self.freeze_begin,
-                        self.smooth_s, int(self.walk_len), self.walk_uniform, int(self.hastings))
+                        self.smooth_s, int(self.walk_len), self.walk_uniform, int(self.hastings),
+                        int(self.shared_bins))
 
 
 class Anneal:

@@ -25,6 +25,8 @@
  *   - p is uniform on the bins and s uniform on the other bins (zero-length
  *     index walk, Sec. 2.3); an index walk of L > 0 steps is an independence
  *     walk with law a_j / A, s walking on the bins other than p (or_move_bins);
+ *   - optionally the walkers share their bins in groups of W (bin_words): the
+ *     group's first walker's bin draw serves the whole group;
  *   - an optional Hastings acceptance with the move's Jacobian r^(N_omega-4)
  *     (or_accept), for exact detailed balance, with the spectra put back on the
  *     sum rules at every residual recomputation (or_restore);
@@ -334,6 +336,7 @@ typedef struct {
     int walk_len;          /* L: steps of the index walk (Sec. 2.3); 0: uniform bins */
     double walk_uniform;   /* rho: probability that an index skips its walk (uniform admixture) */
     int hastings;          /* 1: Metropolis-Hastings acceptance with the move's Jacobian */
+    int shared_bins;       /* W > 1: walkers w with equal w / W propose the bins of walker W (w / W) */
 } or_params;
 
 /* What the anneal carries from block to block besides the walkers. */
@@ -529,6 +532,26 @@ void or_restore(int n_omega, const double *x, double A, double B, double *a) {
     for (int j = 0; j < N; ++j) a[j] = a[j] * (kappa * (1.0 + lambda * (x[j] - c)));
 }
 
+/* Shared bins (a reading of the move beyond the paper, which draws every walker's
+ * indices on its own): with W > 1 the walkers w with equal w / W all propose, at
+ * move mv of sweep n, the bins that the group's first walker g = W (w / W) draws
+ * from words 0 and 1 of its own counter (mv, n, g, 0); each walker keeps words 2
+ * and 3 of its own counter for its amplitude and its acceptance draw.  A walker's
+ * bins stay uniform and independent of its spectrum, so each walker's chain is the
+ * paper's chain; only the walkers of a group become correlated.  With W <= 1 every
+ * walker uses its own words 0 and 1 (the paper's move). */
+static void bin_words(const or_params *prm, int mv, int n, int w, const uint32_t own[4], uint32_t *w0, uint32_t *w1) {
+    if (prm->shared_bins > 1) {
+        uint32_t g[4];
+        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)(w - w % prm->shared_bins), 0u, g);
+        *w0 = g[0];
+        *w1 = g[1];
+    } else {
+        *w0 = own[0];
+        *w1 = own[1];
+    }
+}
+
 /* One sweep (N_omega proposals) of walker w at sweep index n. */
 static void sweep_walker(int n_tau, int n_omega, const double *Khat, const double *Fhat,
                          const double *x, double A, double B, const or_params *prm, double T,
@@ -540,8 +563,10 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
     for (int mv = 0; mv < n_omega; ++mv) {
         uint32_t rnd[4];
         draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u, rnd);
+        uint32_t w0, w1;
+        bin_words(prm, mv, n, w, rnd, &w0, &w1);
         int p, s;
-        or_move_bins(prm, n_omega, a, rnd[0], rnd[1], mv, n, w, &p, &s);
+        or_move_bins(prm, n_omega, a, w0, w1, mv, n, w, &p, &s);
         double eps = (y * dmove) * (2.0 * unit(rnd[2]) - 1.0);
         double u = unit(rnd[3]);
         double D, ap, as;

@@ -42,6 +42,10 @@ MUTATIONS = {
     "hastings_exponent": ("(double)(n_omega - 4) * log(r)", "(double)(n_omega - 2) * log(r)"),
     # Hastings acceptance without the reverse move's feasibility
     "hastings_reverse": ("    if (!(fabs(eps / r) < yd)) return 0;\n", ""),
+    # shared bins drawn from the group's index instead of its first walker's counter
+    "shared_group_index": ("(uint32_t)(w - w % prm->shared_bins)", "(uint32_t)(w / prm->shared_bins)"),
+    # shared bins ignored (every walker its own bins)
+    "shared_ignored": ("    if (prm->shared_bins > 1) {", "    if (prm->shared_bins > 1 << 30) {"),
 }
 
 
@@ -81,6 +85,7 @@ def _pins_pass(L):
         from tests import test_oracle_protocol as Q
         from tests import test_oracle_walk as Wk
         from tests import test_oracle_hastings as Hs
+        from tests import test_oracle_shared as Sh
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
                   lambda: B.test_multipliers_match_enumeration(0),
@@ -88,7 +93,8 @@ def _pins_pass(L):
                   Q.test_self_cooling_phases, Q.test_adaptive_branching_scales_fraction_and_imprint,
                   lambda: Wk.test_walk_law_matches_the_matrix_power(3, 0.0),
                   lambda: Hs.test_jacobian_is_r_to_the_n_minus_4(0.07),
-                  Hs.test_hastings_chain_samples_the_uniform_polytope]
+                  Hs.test_hastings_chain_samples_the_uniform_polytope,
+                  lambda: Sh.test_first_walkers_follow_their_own_bins(4)]
         for c in checks:
             try:
                 c()
