@@ -42,13 +42,14 @@ RESYNC_KIND = 2    # residual recomputation on the tensor cores (tcgen05, BF16, 
 
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
-               sweep_lanes: int = 0, index_walk: int = 0):
+               sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
-                      resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk)
+                      resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk,
+                      shared_bins=shared_bins)
     return P, prm
 
 
@@ -192,14 +193,16 @@ def run_gpu(args, rank, world, local_rank):
 
     # warm-up: W blocks on a separate handle (same configuration, other seed)
     P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
-                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
+                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
+                        shared_bins=args.shared_bins)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
     del warm
 
     P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
-                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
+                        sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
+                        shared_bins=args.shared_bins)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -230,6 +233,12 @@ def run_gpu(args, rank, world, local_rank):
     col_bytes = 4 * N_TAU * 4
     pos_frac = sum(b["positivity_rejected"] for b in stats) / max(len(stats), 1)
     bytes_per_move = 8 + (1.0 - pos_frac) * col_bytes
+    bytes_rule = f"8 + (1 - positivity-rejected fraction {pos_frac:.4f}) x {col_bytes}"
+    if args.shared_bins:
+        # shared bins: a group of W walkers reads one move's columns once
+        bytes_per_move = 8 + col_bytes / args.shared_bins
+        bytes_rule = f"8 + {col_bytes} / {args.shared_bins} (columns read once per group of {args.shared_bins} walkers)"
+
     achieved = moves_per_launch * bytes_per_move / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9
     clk = clocks.summary(local_rank)
 
@@ -238,7 +247,8 @@ def run_gpu(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
-                              sweep_lanes=args.sweep_lanes, index_walk=args.index_walk)
+                              sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
+                        shared_bins=args.shared_bins)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -270,17 +280,18 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + (f", index walk of {args.index_walk} steps" if args.index_walk else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
+            "config": {"workload": WORKLOAD + (f", index walk of {args.index_walk} steps" if args.index_walk else "")
+                       + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
-            "roofline": {"kernel": "sweep_fp32", "bound": "smem", "achieved": achieved,
+            "roofline": {"kernel": "sweep_shared" if args.shared_bins else "sweep_fp32", "bound": "smem", "achieved": achieved,
                          "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
-                         "traffic": kernel_traffic(),
+                         "traffic": None if (args.shared_bins or args.index_walk) else kernel_traffic(),
                          "peak_source": "measured live: conflict-free 16-byte shared-memory loads, 2 blocks x 1024 "
                                         "threads per SM",
                          "l2_read_gbs_measured": l2_gbs,
                          "algorithmic_bytes_per_move": bytes_per_move,
-                         "bytes_per_move_rule": f"8 + (1 - positivity-rejected fraction {pos_frac:.4f}) x {col_bytes}",
+                         "bytes_per_move_rule": bytes_rule,
                          "sweep_lanes_per_walker": g.info().get("sweep_lanes"),
                          "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
                          "sweep_share_of_step": sweep_ms / ms},
@@ -555,6 +566,8 @@ def main():
                          "2 = tensor cores (tcgen05 BF16 x6)")
     ap.add_argument("--index-walk", type=int, default=0, choices=range(8),
                     help="steps of the index walk choosing a move's bins (0: uniform bins, the paper's runs)")
+    ap.add_argument("--shared-bins", type=int, default=0, choices=[0, 4, 8],
+                    help="walkers per group proposing the same bins (0: every walker its own, the paper's move)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
                     help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,

@@ -24,6 +24,7 @@ UNITS = {
     "sweep_fp32.cu": [],
     "sweep_walk.cu": [],
     "sweep_hastings.cu": [],
+    "sweep_shared.cu": [],
     "sweep_batch8.cu": [],
     "sweep_batch16.cu": [],
     "resync_fp32.cu": [],

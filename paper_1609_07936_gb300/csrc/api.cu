@@ -174,6 +174,14 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (p->hastings && p->index_walk_len > 0)
         return fail(SAIL_EINVAL, "hastings needs uniform bins (index_walk_len = 0): the walk's bin choice "
                                  "depends on the state, and its ratio is not part of the correction");
+    if (p->shared_bins != 0 && p->shared_bins != 1 && p->shared_bins != 4 && p->shared_bins != 8)
+        return fail(SAIL_EINVAL, "shared_bins must be 0, 1, 4 or 8");
+    if (p->shared_bins > 1 && p->index_walk_len > 0)
+        return fail(SAIL_EINVAL, "shared_bins needs uniform bins (index_walk_len = 0): a walk depends on "
+                                 "each walker's spectrum");
+    if (p->shared_bins > 1 && p->precision == SAIL_PREC_FP32 && n_tau > 32 * (p->shared_bins == 8 ? 8 : 16))
+        return fail(SAIL_EINVAL, "shared_bins = %d needs n_tau <= %d in FP32", p->shared_bins,
+                    p->shared_bins == 8 ? 256 : 512);
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -473,6 +481,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.walk_len = p->index_walk_len;
     P.walk_rho = p->walk_uniform;
     P.hastings = p->hastings;
+    P.shared_bins = p->shared_bins > 1 ? p->shared_bins : 0;
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;
@@ -993,6 +1002,7 @@ int check_batch(int n, const sail_problem *probs) {
     for (int k = 0; k < n; ++k) {
         const sail_params &p = probs[k].params;
         if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "problem %d: batches run FP32 precision", k);
+        if (p.shared_bins > 1) return fail(SAIL_EINVAL, "problem %d: batches do not run shared bins", k);
         if (p.sweeps_per_block != probs[0].params.sweeps_per_block || p.resync_every != probs[0].params.resync_every)
             return fail(SAIL_EINVAL, "problem %d: sweeps_per_block and resync_every must match problem 0", k);
         const int rc = check_params(probs[k].n_tau, probs[k].n_omega, &p);
@@ -1424,6 +1434,7 @@ int sail_server_submit(sail_server_t s, const sail_problem *req, int *id) {
     if (!s || !req || !id) return fail(SAIL_EINVAL, "NULL argument");
     const sail_params &p = req->params;
     if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "served inversions run FP32 precision");
+    if (p.shared_bins > 1) return fail(SAIL_EINVAL, "served inversions do not run shared bins");
     if (p.sweeps_per_block != s->sweeps_per_block || p.resync_every != s->resync_every)
         return fail(SAIL_EINVAL, "request periods differ from the server's");
     size_t bytes = 0;

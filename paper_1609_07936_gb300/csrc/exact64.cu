@@ -110,8 +110,15 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
         int acc = 0;
         for (int mv = 0; mv < NO; ++mv) {
             const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u), key);
+            // shared bins: the group's first walker's words 0 and 1 (its own counter)
+            uint2 bw = make_uint2(rnd.x, rnd.y);
+            if (P.shared_bins > 1 && w % P.shared_bins != 0) {
+                const uint4 g = philox4x32_10(
+                    make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)(w - w % P.shared_bins), 0u), key);
+                bw = make_uint2(g.x, g.y);
+            }
             int p, s;
-            walk_bins64(P, a, rnd.x, rnd.y, mv, n, w, key, p, s);
+            walk_bins64(P, a, bw.x, bw.y, mv, n, w, key, p, s);
             const double eps = (y * dmove) * (2.0 * unit64(rnd.z) - 1.0);
             const double u = unit64(rnd.w);
             const double r = 1.0 - eps;

@@ -50,6 +50,7 @@ struct DevProblem {
     int walk_len;          // steps of the index walk (0: uniform bins)
     int hastings;          // Metropolis-Hastings acceptance with the move's Jacobian
     double walk_rho;       // probability that an index skips its walk
+    int shared_bins;       // W > 1: walkers in groups of W propose their first walker's bins
     const double *Tsweep;
 };
 
@@ -97,6 +98,9 @@ cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_
 // The FP32 sweep of a problem with an index walk (P.walk_len > 0); launch_sweep_fp32 calls it.
 cudaError_t launch_sweep_walk(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                               cudaStream_t st);
+// The FP32 sweep of a problem with shared bins (P.shared_bins = 4 or 8), plain or Hastings.
+cudaError_t launch_sweep_shared(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
+                                cudaStream_t st);
 // The FP32 sweep with the Metropolis-Hastings acceptance (P.hastings, uniform bins).
 cudaError_t launch_sweep_hastings(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                                   cudaStream_t st);

@@ -120,6 +120,7 @@ cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sin
 int sweep_walkers_per_warp(const DevProblem &P) { return P.lanes == 8 ? 4 : 2; }
 
 cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    if (P.shared_bins > 1) return launch_sweep_shared(P, S, n0, n1, st);
     if (P.walk_len > 0) return launch_sweep_walk(P, S, n0, n1, st);
     if (P.hastings) return launch_sweep_hastings(P, S, n0, n1, st);
     return launch_sweep_w<kPlain>(P, S, n0, n1, st);
