@@ -143,10 +143,11 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
         SharedDraw cur = shared_draw<MODE>(q, n, w, key, NO, yd, T);
         SharedDraw nxt = cur;
         if (MPD < NO) nxt = shared_draw<MODE>(MPD + q, n, w, key, NO, yd, T);
-        f2 G[C], Gn[C];
-        float cp, cs, cpn = 0.0f, csn = 0.0f;
-        form_g<C>(G, Fh, __shfl_sync(kFull, cur.ps, 0), qhi, qlo, PAD, sBeta, sRgap, cp, cs);
-        for (int mv = 0; mv < NO; ++mv) {
+        f2 Ga[C], Gb[C];
+        float cpa, csa, cpb = 0.0f, csb = 0.0f;
+        form_g<C>(Ga, Fh, __shfl_sync(kFull, cur.ps, 0), qhi, qlo, PAD, sBeta, sRgap, cpa, csa);
+        // one move; the loop runs two per iteration with G and Gn exchanging roles
+        auto move = [&](const int mv, f2 (&G)[C], f2 (&Gn)[C], float &cp, float &cs, float &cpn, float &csn) {
             const int m = mv & (MPD - 1);
             if (m == 0 && mv > 0) {
                 cur = nxt;
@@ -171,11 +172,13 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
                     const f2 d = mul2(e2[j], fma2(minus_one, R[c][j], G[c]));
                     acc2[j] = fma2(d, fma2(two, R[c][j], d), acc2[j]);
                 }
-            // the next move's G, while this one is reduced and tested
-            if (mv + 1 < NO) {
+            // the next move's G, while this one is reduced and tested (after the sweep's last
+            // move: this move's again, unused)
+            {
                 const int nps_cur = __shfl_sync(kFull, cur.ps, (W * (m + 1)) & 31);
                 const int nps_nxt = __shfl_sync(kFull, nxt.ps, 0);
-                form_g<C>(Gn, Fh, m + 1 < MPD ? nps_cur : nps_nxt, qhi, qlo, PAD, sBeta, sRgap, cpn, csn);
+                const int nps = mv + 1 >= NO ? ps : (m + 1 < MPD ? nps_cur : nps_nxt);
+                form_g<C>(Gn, Fh, nps, qhi, qlo, PAD, sBeta, sRgap, cpn, csn);
             }
             // transposing butterfly: after the step with mask 2^b a lane keeps the walkers whose
             // bit b equals its own; the last steps add up the lanes of each walker
@@ -230,11 +233,12 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
                 }
             }
             __syncwarp();
-#pragma unroll
-            for (int c = 0; c < C; ++c) G[c] = Gn[c];
-            cp = cpn;
-            cs = csn;
+        };
+        for (int mv = 0; mv + 1 < NO; mv += 2) {
+            move(mv, Ga, Gb, cpa, csa, cpb, csb);
+            move(mv + 1, Gb, Ga, cpb, csb, cpa, csa);
         }
+        if (NO & 1) move(NO - 1, Ga, Gb, cpa, csa, cpb, csb);
         chi2 += (double)dchi;
         accp = acc;
         nacc += acc;
