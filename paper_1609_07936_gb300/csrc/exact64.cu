@@ -198,12 +198,8 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
 // common scale into b before this runs.
 //
 // FP32 state only: rounding in the moves lets sum a and sum a x wander by ~1e-6 of A and B
-// over a resync interval (exact arithmetic keeps them fixed, Sec. 2.2).  Before the
-// residual is formed the spectrum is put back on both sum rules by the smallest affine
-// reweighting a_j <- a_j kappa (1 + lambda (x_j - c)), c = sum a x / sum a, with
-// kappa = A / sum a and lambda = (B/A - c) / var, which changes each bin by a factor
-// 1 + O(1e-6) and keeps a >= 0.
-// FP32 state drifts off the two sum rules by rounding; each walker is put back with the
+// over a resync interval (exact arithmetic keeps them fixed, Sec. 2.2), so before the residual
+// is formed each walker is put back on both sum rules with the
 // affine reweighting b_j <- b_j kappa (1 + lambda (x_j - c)): c = B'/A', kappa = A / A',
 // lambda = (B/A - c) / var', where A' = sum b, B' = sum b x and var' = sum b x^2 / A' - c^2 are
 // the walker's current moments (lambda = 0 if the tilt could make a factor negative).  One

@@ -1,0 +1,66 @@
+"""GPU: the FP32 look-ahead move loop at the edges of its proposal windows, through the C ABI.
+
+Each walker keeps 16 proposals drawn (two windows of 8), takes the first feasible one by a
+ballot and counts the infeasible ones before it as rejected; windows may run past the end of
+a sweep, and a sweep may hold fewer proposals than one window.  Bin counts of 3 to 37 (fewer
+than a window, partial last windows, sweeps of odd length) and a ragged tau count exercise
+those paths; the FP32 sweep draws the oracle's words, so over a few sweeps nearly every
+walker accepts exactly the oracle's number of moves in every sweep.  The shared-bin sweep is
+run on the same cases.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1609_07936_gb300 as sail
+from workloads import Peak, make_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n_omega, n_tau=40, n_walkers=64):
+    tau = 3.0 * np.arange(n_tau, dtype=np.float64) / (n_tau - 1)
+    peaks = [Peak("lorentz", 2.0, 0.4, 0.6), Peak("gauss", 5.0, 0.8, 0.4)]
+    return make_problem(f"edges_{n_omega}", tau, n_omega, 10.0, peaks, 1e-4, 3, n_walkers)
+
+
+@pytest.mark.parametrize("n_omega", [3, 5, 13, 17, 37])
+@pytest.mark.parametrize("W", [0, 8])
+def test_fp32_windows_take_the_oracle_decisions(n_omega, W):
+    P = _problem(n_omega)
+    kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=23)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(shared_bins=W, **kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, shared_bins=W,
+                              resync_kind=sail.RESYNC_FP32, **kw))
+    g.anneal()
+    acc_g, _, _ = g.trace()
+    assert acc_g.shape == acc_o.shape
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    # the runs took decisions both ways
+    assert acc_o.sum() > 0 and (acc_o < n_omega).any()
+    a = g.state()[0]
+    np.testing.assert_allclose(a.sum(1), P.A, rtol=2e-6)
+    np.testing.assert_allclose(a @ P.omega, P.B, rtol=2e-6)
+    for w in np.flatnonzero(same):
+        np.testing.assert_allclose(a[w], an.a[w], rtol=0, atol=1e-4 * an.a[w].max())
+    g.close()
+
+
+@pytest.mark.parametrize("n_omega", [5, 13])
+def test_fp32_hastings_windows_take_the_oracle_decisions(n_omega):
+    """The Hastings variant also skips proposals whose reverse move cannot be proposed."""
+    P = _problem(n_omega)
+    kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=29)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(hastings=True, **kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, hastings=True,
+                              resync_kind=sail.RESYNC_FP32, **kw))
+    g.anneal()
+    acc_g, _, _ = g.trace()
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    g.close()
