@@ -468,7 +468,7 @@ def run_precision(args):
     for kind, name in ((0, "fp32-fma"), (1, "tcgen05-tf32x3"), (2, "tcgen05-bf16x6")):
         prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=100, sweeps_per_block=50,
                           resync_every=10, branching=False, T_start=10.0, T_end=1e-3, A=P.A, B=P.B, seed=3,
-                          resync_kind=kind, timing=True)
+                          resync_kind=kind, timing=True, shared_bins=args.shared_bins)
         g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
         g.anneal()
         torch.cuda.synchronize()
@@ -490,7 +490,8 @@ def run_precision(args):
            "steps": 3, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "precision: 512 tau x 2048 bins, 16384 walkers, random 1-4 peaks, FP32 moves, "
-                                  "residual recomputation every 10 sweeps by each method",
+                                  "residual recomputation every 10 sweeps by each method"
+                                  + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""),
                       "step": "two blocks of 50 sweeps per recomputation method"},
            "resync": kinds}
     print(json.dumps(out), flush=True)

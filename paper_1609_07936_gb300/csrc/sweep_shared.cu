@@ -272,8 +272,9 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
     }
 }
 
-// At most 4 warps a block: with one warp per scheduler the move loop's latency is not shared.
-constexpr int kSharedWarps = 4;
+// At most 8 warps a block (the widest variants take 254 registers a thread): with more walker
+// groups than that per SM the warps run in rounds.
+constexpr int kSharedWarps = 8;
 
 template <int W, int C, int MODE>
 __global__ void __launch_bounds__(32 * kSharedWarps) sweep_shared_kernel(DevProblem P, DevState S, int n0, int n1,

@@ -6,7 +6,8 @@ a sweep, and a sweep may hold fewer proposals than one window.  Bin counts of 3 
 than a window, partial last windows, sweeps of odd length) and a ragged tau count exercise
 those paths; the FP32 sweep draws the oracle's words, so over a few sweeps nearly every
 walker accepts exactly the oracle's number of moves in every sweep.  The shared-bin sweep is
-run on the same cases.
+run on the same cases, and a 300-point tau grid (10 chunks: the one-move loop, which takes
+over where columns cannot be prefetched) on both.
 """
 import numpy as np
 import pytest
@@ -63,4 +64,22 @@ def test_fp32_hastings_windows_take_the_oracle_decisions(n_omega):
     acc_g, _, _ = g.trace()
     same = np.all(acc_g == acc_o, axis=0)
     assert same.mean() >= 0.9, same.mean()
+    g.close()
+
+
+@pytest.mark.parametrize("W", [0, 4])
+def test_fp32_wide_tau_takes_the_oracle_decisions(W):
+    P = _problem(37, n_tau=300, n_walkers=32)
+    kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=41)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 32, O.Schedule(shared_bins=W, **kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=32, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, shared_bins=W,
+                              resync_kind=sail.RESYNC_FP32, **kw))
+    g.anneal()
+    assert g.info()["sweep_lanes"] == 16
+    acc_g, _, _ = g.trace()
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    assert acc_o.sum() > 0 and (acc_o < 37).any()
     g.close()
