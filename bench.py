@@ -206,8 +206,8 @@ def run_gpu(args, rank, world, local_rank):
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", f"clocks_rank{rank}.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else f"/tmp/sail_clocks_{os.getpid()}.csv")
+    clocks = Clocks(os.path.join(args.clocks_dir, f"clocks_rank{rank}.csv") if args.clocks_dir
+                    else f"/tmp/sail_clocks_{os.getpid()}_{rank}.csv")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with clocks:
         time.sleep(0.3)
@@ -555,6 +555,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample-walkers", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clocks-dir", default="",
+                    help="directory for the raw nvidia-smi clock samples of the timed region (default: /tmp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision"])
     ap.add_argument("--band-sweeps", type=int, default=20000, help="band example: sweep budget per inversion")
