@@ -569,7 +569,7 @@ def main():
                          "2 = tensor cores (tcgen05 BF16 x6)")
     ap.add_argument("--index-walk", type=int, default=0, choices=range(8),
                     help="steps of the index walk choosing a move's bins (0: uniform bins, the paper's runs)")
-    ap.add_argument("--shared-bins", type=int, default=0, choices=[0, 4, 8],
+    ap.add_argument("--shared-bins", type=int, default=0, choices=[0, 2, 4, 8],
                     help="walkers per group proposing the same bins (0: every walker its own, the paper's move)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
                     help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")

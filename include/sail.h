@@ -122,7 +122,7 @@ typedef struct sail_params {
                                Metropolis test */
     double walk_uniform;    /* probability that an index skips its walk (uniform admixture) */
     int shared_bins;        /* W: 0 or 1 = every walker draws its own bins (the paper's move);
-                               4 or 8 = the walkers w with equal w / W all propose, at each
+                               2, 4 or 8 = the walkers w with equal w / W all propose, at each
                                move, the bins of their group's first walker W (w / W) (words 0
                                and 1 of its move counter), each keeping its own amplitude and
                                acceptance draw (words 2 and 3 of its own counter).  Every
@@ -130,7 +130,7 @@ typedef struct sail_params {
                                and independent of its spectrum); the walkers of a group become
                                correlated.  The FP32 sweep then forms the bins' part of the
                                residual change once per group.  Needs index_walk_len = 0; FP32
-                               needs n_tau <= 256 for W = 8 and n_tau <= 512 for W = 4; not
+                               needs n_tau <= 256 for W = 8 (512 for W = 2 and 4); not
                                accepted by the batch and the server */
     int reserved;
 } sail_params;

@@ -25,6 +25,9 @@ UNITS = {
     "sweep_walk.cu": [],
     "sweep_hastings.cu": [],
     "sweep_shared.cu": [],
+    "sweep_shared8.cu": [],
+    "sweep_shared4.cu": [],
+    "sweep_shared2.cu": [],
     "sweep_batch8.cu": [],
     "sweep_batch16.cu": [],
     "resync_fp32.cu": [],

@@ -174,8 +174,9 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (p->hastings && p->index_walk_len > 0)
         return fail(SAIL_EINVAL, "hastings needs uniform bins (index_walk_len = 0): the walk's bin choice "
                                  "depends on the state, and its ratio is not part of the correction");
-    if (p->shared_bins != 0 && p->shared_bins != 1 && p->shared_bins != 4 && p->shared_bins != 8)
-        return fail(SAIL_EINVAL, "shared_bins must be 0, 1, 4 or 8");
+    if (p->shared_bins != 0 && p->shared_bins != 1 && p->shared_bins != 2 && p->shared_bins != 4 &&
+        p->shared_bins != 8)
+        return fail(SAIL_EINVAL, "shared_bins must be 0, 1, 2, 4 or 8");
     if (p->shared_bins > 1 && p->index_walk_len > 0)
         return fail(SAIL_EINVAL, "shared_bins needs uniform bins (index_walk_len = 0): a walk depends on "
                                  "each walker's spectrum");

@@ -98,7 +98,7 @@ cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int sweep_
 // The FP32 sweep of a problem with an index walk (P.walk_len > 0); launch_sweep_fp32 calls it.
 cudaError_t launch_sweep_walk(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                               cudaStream_t st);
-// The FP32 sweep of a problem with shared bins (P.shared_bins = 4 or 8), plain or Hastings.
+// The FP32 sweep of a problem with shared bins (P.shared_bins = 2, 4 or 8), plain or Hastings.
 cudaError_t launch_sweep_shared(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                                 cudaStream_t st);
 // The FP32 sweep with the Metropolis-Hastings acceptance (P.hastings, uniform bins).

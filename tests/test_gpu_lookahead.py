@@ -26,7 +26,7 @@ def _problem(n_omega, n_tau=40, n_walkers=64):
 
 
 @pytest.mark.parametrize("n_omega", [3, 5, 13, 17, 37])
-@pytest.mark.parametrize("W", [0, 8])
+@pytest.mark.parametrize("W", [0, 2, 8])
 def test_fp32_windows_take_the_oracle_decisions(n_omega, W):
     P = _problem(n_omega)
     kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=23)
@@ -67,7 +67,7 @@ def test_fp32_hastings_windows_take_the_oracle_decisions(n_omega):
     g.close()
 
 
-@pytest.mark.parametrize("W", [0, 4])
+@pytest.mark.parametrize("W", [0, 2, 4])
 def test_fp32_wide_tau_takes_the_oracle_decisions(W):
     P = _problem(37, n_tau=300, n_walkers=32)
     kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=41)

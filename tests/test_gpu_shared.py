@@ -32,7 +32,7 @@ def _pair(P, n_walkers, precision, W, hastings=False, **kw):
     return an, g
 
 
-@pytest.mark.parametrize("W,hastings,n_walkers", [(4, False, 48), (8, False, 61), (8, True, 40)])
+@pytest.mark.parametrize("W,hastings,n_walkers", [(2, False, 37), (4, False, 48), (8, False, 61), (8, True, 40)])
 def test_fp64_shared_bins_reproduce_every_decision(W, hastings, n_walkers):
     """Tiny workload, branching every 50 sweeps; 61 walkers leave the last group ragged."""
     P = tiny_double_lorentz()
@@ -52,8 +52,8 @@ def test_fp64_shared_bins_reproduce_every_decision(W, hastings, n_walkers):
     g.close()
 
 
-@pytest.mark.parametrize("W,hastings,n_walkers", [(0, False, 64), (4, False, 64), (8, False, 61),
-                                                  (8, True, 64), (4, True, 37)])
+@pytest.mark.parametrize("W,hastings,n_walkers", [(0, False, 64), (2, False, 64), (4, False, 64), (8, False, 61),
+                                                  (8, True, 64), (4, True, 37), (2, True, 33)])
 def test_fp32_sweep_takes_the_oracle_decisions(W, hastings, n_walkers):
     """Tiny workload (32 tau points, 64 bins), 4 sweeps of 64 moves at T = chi2_0 / 2 with a
     recomputation every 2 sweeps, no branching: at least 90% of the walkers accept exactly
@@ -93,7 +93,7 @@ def test_fp32_shared_hastings_samples_the_uniform_polytope():
     g.close()
 
 
-@pytest.mark.parametrize("W", [4, 8])
+@pytest.mark.parametrize("W", [2, 4, 8])
 def test_fp32_shared_paper_scale_keeps_sums_and_bookkeeping(W):
     """200 x 1000 grid, 4096 walkers, two blocks of 100 sweeps with branching and BF16
     tensor-core recomputation every 50."""
