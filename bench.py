@@ -239,8 +239,21 @@ def run_gpu(args, rank, world, local_rank):
         bytes_per_move = 8 + col_bytes / args.shared_bins
         bytes_rule = f"8 + {col_bytes} / {args.shared_bins} (columns read once per group of {args.shared_bins} walkers)"
 
-    achieved = moves_per_launch * bytes_per_move / (sweep_ms / max(sweep_n, 1) * 1e-3) / 1e9
+    launch_s = sweep_ms / max(sweep_n, 1) * 1e-3
+    achieved = moves_per_launch * bytes_per_move / launch_s / 1e9
     clk = clocks.summary(local_rank)
+    # the sweep is bound by FP32 arithmetic issue and its latency (not HBM, no contraction):
+    # algorithmic FP32 work of a walker-move (Sec. 2.2), per tau point: for a move that passes
+    # the positivity test d_i = eps M_i - delta_p Khat_ip - delta_s Khat_is (1 multiply + 2 FMA =
+    # 5 flops) and d_i (2 R_i + d_i) accumulated (2 FMA = 4 flops); for an accepted move
+    # R_i += d_i, M_i -= d_i (2 flops).  Peak: SMs x 128 FP32 lanes x 2 flops (FMA) x the
+    # maximum SM clock.
+    acc_frac = sum(b["acceptance"] for b in stats) / max(len(stats), 1)
+    flops_per_move = N_TAU * (9.0 * (1.0 - pos_frac) + 2.0 * acc_frac)
+    sms = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    sm_max_mhz = clk.get("sm_max_mhz") or 2070.0
+    fp32_peak = sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    fp32_achieved = moves_per_launch * flops_per_move / launch_s / 1e12
 
     # end to end through the public API from host buffers: create (H2D of inputs and tables),
     # K blocks (per-block statistics D2H), average (D2H of the spectrum and errors)
@@ -284,14 +297,19 @@ def run_gpu(args, rank, world, local_rank):
                        + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
-            "roofline": {"kernel": "sweep_shared" if args.shared_bins else "sweep_fp32", "bound": "smem", "achieved": achieved,
-                         "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
+            "roofline": {"kernel": "sweep_shared" if args.shared_bins else "sweep_fp32", "bound": "alu",
+                         "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                         "frac": fp32_achieved / fp32_peak,
                          "traffic": None if (args.shared_bins or args.index_walk) else kernel_traffic(),
-                         "peak_source": "measured live: conflict-free 16-byte shared-memory loads, 2 blocks x 1024 "
-                                        "threads per SM",
+                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz",
+                         "algorithmic_flops_per_move": flops_per_move,
+                         "flops_per_move_rule": f"{N_TAU} x (9 x (1 - positivity-rejected {pos_frac:.4f}) "
+                                                f"+ 2 x accepted {acc_frac:.4f})",
+                         "smem": {"achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
+                                  "peak_source": "measured live: conflict-free 16-byte shared-memory loads, "
+                                                 "2 blocks x 1024 threads per SM",
+                                  "algorithmic_bytes_per_move": bytes_per_move, "bytes_per_move_rule": bytes_rule},
                          "l2_read_gbs_measured": l2_gbs,
-                         "algorithmic_bytes_per_move": bytes_per_move,
-                         "bytes_per_move_rule": bytes_rule,
                          "sweep_lanes_per_walker": g.info().get("sweep_lanes"),
                          "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
                          "sweep_share_of_step": sweep_ms / ms},
