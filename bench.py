@@ -42,14 +42,14 @@ RESYNC_KIND = 2    # residual recomputation on the tensor cores (tcgen05, BF16, 
 
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
-               sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0):
+               sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0, sweep_loop: int = 0):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
                       resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk,
-                      shared_bins=shared_bins)
+                      shared_bins=shared_bins, sweep_loop=sweep_loop)
     return P, prm
 
 
@@ -194,7 +194,7 @@ def run_gpu(args, rank, world, local_rank):
     # warm-up: W blocks on a separate handle (same configuration, other seed)
     P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
@@ -202,7 +202,7 @@ def run_gpu(args, rank, world, local_rank):
 
     P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -261,7 +261,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_e2e:
         P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
                               sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -534,7 +534,7 @@ def run_band(args):
                           sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
                           schedule_kind=sail.SCHEDULE_SELF_COOLING, adaptive_branching=True, smooth_s=1e-2,
                           T_end_abs=0.3, A=P.A, B=P.B, seed=11, resync_kind=args.resync_kind,
-                          target_chi2=1.2 * P.n_tau, timing=True)
+                          target_chi2=1.2 * P.n_tau, timing=True, sweep_loop=args.sweep_loop)
         t0 = time.perf_counter()
         g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
         g.anneal()
@@ -587,6 +587,8 @@ def main():
                          "2 = tensor cores (tcgen05 BF16 x6)")
     ap.add_argument("--index-walk", type=int, default=0, choices=range(8),
                     help="steps of the index walk choosing a move's bins (0: uniform bins, the paper's runs)")
+    ap.add_argument("--sweep-loop", type=int, default=0, choices=[0, 1, 2],
+                    help="FP32 move loop: 0 choose by walkers per SM, 1 one move at a time, 2 look-ahead")
     ap.add_argument("--shared-bins", type=int, default=0, choices=[0, 2, 4, 8],
                     help="walkers per group proposing the same bins (0: every walker its own, the paper's move)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],

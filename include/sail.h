@@ -132,7 +132,11 @@ typedef struct sail_params {
                                residual change once per group.  Needs index_walk_len = 0; FP32
                                needs n_tau <= 256 for W = 8 (512 for W = 2 and 4); not
                                accepted by the batch and the server */
-    int reserved;
+    int sweep_loop;         /* FP32 move loop for n_tau <= 256 (uniform bins, own bins): 1 = one move
+                               at a time; 2 = look-ahead (each walker keeps its next 16 proposals
+                               drawn and spends columns and reduction on feasible ones only; the
+                               same chain bit for bit); 0 = choose: look-ahead when the problem has
+                               at least 16 walkers per SM (measured faster there, slower with fewer) */
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */

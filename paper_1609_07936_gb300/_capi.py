@@ -57,7 +57,7 @@ class CParams(ctypes.Structure):
         ("wait_test", ctypes.c_int), ("sweep_lanes", ctypes.c_int), ("schedule_kind", ctypes.c_int),
         ("adaptive_branching", ctypes.c_int), ("cool_begin", ctypes.c_double), ("freeze_begin", ctypes.c_double),
         ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("hastings", ctypes.c_int),
-        ("walk_uniform", ctypes.c_double), ("shared_bins", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("walk_uniform", ctypes.c_double), ("shared_bins", ctypes.c_int), ("sweep_loop", ctypes.c_int),
     ]
 
 
@@ -209,6 +209,7 @@ class Params:
     walk_uniform: float = 0.0
     hastings: bool = False
     shared_bins: int = 0
+    sweep_loop: int = 0
 
     def c(self) -> CParams:
         p = CParams()

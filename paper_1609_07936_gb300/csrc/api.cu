@@ -183,6 +183,7 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (p->shared_bins > 1 && p->precision == SAIL_PREC_FP32 && n_tau > 32 * (p->shared_bins == 8 ? 8 : 16))
         return fail(SAIL_EINVAL, "shared_bins = %d needs n_tau <= %d in FP32", p->shared_bins,
                     p->shared_bins == 8 ? 256 : 512);
+    if (p->sweep_loop < 0 || p->sweep_loop > 2) return fail(SAIL_EINVAL, "sweep_loop must be 0, 1 or 2");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -483,6 +484,15 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.walk_rho = p->walk_uniform;
     P.hastings = p->hastings;
     P.shared_bins = p->shared_bins > 1 ? p->shared_bins : 0;
+    {
+        // the look-ahead loop pays where several warps share each scheduler (4096 walkers on
+        // 152 SMs: +12%); with few walkers per SM its longer chain per move costs more (1500:
+        // -14%)
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        P.ahead = p->sweep_loop == 2 ? 1 : p->sweep_loop == 1 ? 0 : (p->n_walkers >= 16 * sms ? 1 : 0);
+    }
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
     DevState &S = h->S;

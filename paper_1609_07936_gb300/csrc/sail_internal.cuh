@@ -51,6 +51,7 @@ struct DevProblem {
     int hastings;          // Metropolis-Hastings acceptance with the move's Jacobian
     double walk_rho;       // probability that an index skips its walk
     int shared_bins;       // W > 1: walkers in groups of W propose their first walker's bins
+    int ahead;             // FP32, up to 8 chunks: the look-ahead move loop (else one move at a time)
     const double *Tsweep;
 };
 

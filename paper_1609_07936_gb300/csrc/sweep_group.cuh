@@ -739,14 +739,14 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
 }
 
 // The move loop of a variant: the index walk's bins depend on the spectrum, so it proposes
-// and evaluates one move at a time; the uniform-bin variants look ahead where the next move's
-// columns can be prefetched (up to 8 chunks).  Past that the look-ahead's search would stand
-// in front of every column load, and the one-move loop is faster (measured at 512 tau:
-// 3.69e9 against 2.16e9 walker-moves/s).
-template <int G, int C, bool STAGED, int MODE>
+// and evaluates one move at a time; the uniform-bin variants may look ahead (AHEAD) where the
+// next move's columns can be prefetched (up to 8 chunks).  Past that the look-ahead's search
+// would stand in front of every column load, and the one-move loop is faster (measured at
+// 512 tau: 3.69e9 against 2.16e9 walker-moves/s).
+template <int G, int C, bool STAGED, int MODE, bool AHEAD>
 __device__ __forceinline__ void run_walkers(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
                                             const float *sm, float *b_stage, int walker_lo) {
-    if constexpr (MODE == kWalk || C > 8)
+    if constexpr (MODE == kWalk || C > 8 || !AHEAD)
         run_group<G, C, STAGED, MODE>(P, S, n0, n1, grp, sm, b_stage, walker_lo);
     else
         run_group_ahead<G, C, STAGED, MODE>(P, S, n0, n1, grp, sm, b_stage, walker_lo);
@@ -759,7 +759,7 @@ __device__ __forceinline__ void run_walkers(const DevProblem &P, const DevState 
 template <int G, int C>
 constexpr int sweep_threads() { return G == 8 ? 256 : ((C <= 4 || C == 9) ? kThreads : 384); }
 
-template <int G, int C, int MODE>
+template <int G, int C, int MODE, bool AHEAD>
 __global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom Gm) {
     extern __shared__ float4 smem4[];
@@ -783,9 +783,9 @@ __global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevPr
         const int grp = grp_lo + round * Gm.warps + warp;
         if (grp >= grp_hi) break;                         // uniform across the warp
         if (Gm.stage_b)
-            run_walkers<G, C, true, MODE>(P, S, n0, n1, grp, sm, sB, walker_lo);
+            run_walkers<G, C, true, MODE, AHEAD>(P, S, n0, n1, grp, sm, sB, walker_lo);
         else
-            run_walkers<G, C, false, MODE>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
+            run_walkers<G, C, false, MODE, AHEAD>(P, S, n0, n1, grp, sm, nullptr, walker_lo);
     }
 }
 
@@ -794,7 +794,7 @@ size_t table_bytes(const DevProblem &P) {
     return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
 }
 
-template <int G, int C, int MODE>
+template <int G, int C, int MODE, bool AHEAD>
 cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
     int dev = 0, sms = 0, smem_max = 0;
     cudaGetDevice(&dev);
@@ -813,45 +813,54 @@ cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cud
     if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
     Gm.stage_b = tb + staged <= (size_t)smem_max;
     const size_t smem = tb + (Gm.stage_b ? staged : 0);
-    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fp32_kernel<G, C, MODE, AHEAD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e != cudaSuccess) return e;
     const int n_ctas = (Gm.groups_total + Gm.groups_per_cta - 1) / Gm.groups_per_cta;
-    sweep_fp32_kernel<G, C, MODE><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
+    sweep_fp32_kernel<G, C, MODE, AHEAD><<<n_ctas, Gm.warps * 32, smem, st>>>(P, S, n0, n1, Gm);
     return cudaGetLastError();
+}
+
+// Up to 8 chunks the plain and Hastings variants come in both move loops (P.ahead chooses).
+template <int G, int C, int MODE>
+cudaError_t launch_pick(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
+    if constexpr (MODE != kWalk && C <= 8)
+        if (P.ahead) return launch_c<G, C, MODE, true>(P, S, n0, n1, st);
+    return launch_c<G, C, MODE, false>(P, S, n0, n1, st);
 }
 
 template <int MODE>
 cudaError_t launch_sweep_w(const DevProblem &P, const DevState &S, int n0, int n1, cudaStream_t st) {
     if (P.lanes == 8) {
         switch (P.n_tau_pad / 32) {
-            case 1: return launch_c<8, 1, MODE>(P, S, n0, n1, st);
-            case 2: return launch_c<8, 2, MODE>(P, S, n0, n1, st);
-            case 3: return launch_c<8, 3, MODE>(P, S, n0, n1, st);
-            case 4: return launch_c<8, 4, MODE>(P, S, n0, n1, st);
-            case 5: return launch_c<8, 5, MODE>(P, S, n0, n1, st);
-            case 6: return launch_c<8, 6, MODE>(P, S, n0, n1, st);
-            case 7: return launch_c<8, 7, MODE>(P, S, n0, n1, st);
-            case 8: return launch_c<8, 8, MODE>(P, S, n0, n1, st);
+            case 1: return launch_pick<8, 1, MODE>(P, S, n0, n1, st);
+            case 2: return launch_pick<8, 2, MODE>(P, S, n0, n1, st);
+            case 3: return launch_pick<8, 3, MODE>(P, S, n0, n1, st);
+            case 4: return launch_pick<8, 4, MODE>(P, S, n0, n1, st);
+            case 5: return launch_pick<8, 5, MODE>(P, S, n0, n1, st);
+            case 6: return launch_pick<8, 6, MODE>(P, S, n0, n1, st);
+            case 7: return launch_pick<8, 7, MODE>(P, S, n0, n1, st);
+            case 8: return launch_pick<8, 8, MODE>(P, S, n0, n1, st);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (P.n_tau_pad / 32) {
-        case 1: return launch_c<16, 1, MODE>(P, S, n0, n1, st);
-        case 2: return launch_c<16, 2, MODE>(P, S, n0, n1, st);
-        case 3: return launch_c<16, 3, MODE>(P, S, n0, n1, st);
-        case 4: return launch_c<16, 4, MODE>(P, S, n0, n1, st);
-        case 5: return launch_c<16, 5, MODE>(P, S, n0, n1, st);
-        case 6: return launch_c<16, 6, MODE>(P, S, n0, n1, st);
-        case 7: return launch_c<16, 7, MODE>(P, S, n0, n1, st);
-        case 8: return launch_c<16, 8, MODE>(P, S, n0, n1, st);
-        case 9: return launch_c<16, 9, MODE>(P, S, n0, n1, st);
-        case 10: return launch_c<16, 10, MODE>(P, S, n0, n1, st);
-        case 11: return launch_c<16, 11, MODE>(P, S, n0, n1, st);
-        case 12: return launch_c<16, 12, MODE>(P, S, n0, n1, st);
-        case 13: return launch_c<16, 13, MODE>(P, S, n0, n1, st);
-        case 14: return launch_c<16, 14, MODE>(P, S, n0, n1, st);
-        case 15: return launch_c<16, 15, MODE>(P, S, n0, n1, st);
-        case 16: return launch_c<16, 16, MODE>(P, S, n0, n1, st);
+        case 1: return launch_pick<16, 1, MODE>(P, S, n0, n1, st);
+        case 2: return launch_pick<16, 2, MODE>(P, S, n0, n1, st);
+        case 3: return launch_pick<16, 3, MODE>(P, S, n0, n1, st);
+        case 4: return launch_pick<16, 4, MODE>(P, S, n0, n1, st);
+        case 5: return launch_pick<16, 5, MODE>(P, S, n0, n1, st);
+        case 6: return launch_pick<16, 6, MODE>(P, S, n0, n1, st);
+        case 7: return launch_pick<16, 7, MODE>(P, S, n0, n1, st);
+        case 8: return launch_pick<16, 8, MODE>(P, S, n0, n1, st);
+        case 9: return launch_pick<16, 9, MODE>(P, S, n0, n1, st);
+        case 10: return launch_pick<16, 10, MODE>(P, S, n0, n1, st);
+        case 11: return launch_pick<16, 11, MODE>(P, S, n0, n1, st);
+        case 12: return launch_pick<16, 12, MODE>(P, S, n0, n1, st);
+        case 13: return launch_pick<16, 13, MODE>(P, S, n0, n1, st);
+        case 14: return launch_pick<16, 14, MODE>(P, S, n0, n1, st);
+        case 15: return launch_pick<16, 15, MODE>(P, S, n0, n1, st);
+        case 16: return launch_pick<16, 16, MODE>(P, S, n0, n1, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -7,7 +7,8 @@ than a window, partial last windows, sweeps of odd length) and a ragged tau coun
 those paths; the FP32 sweep draws the oracle's words, so over a few sweeps nearly every
 walker accepts exactly the oracle's number of moves in every sweep.  The shared-bin sweep is
 run on the same cases, and a 300-point tau grid (10 chunks: the one-move loop, which takes
-over where columns cannot be prefetched) on both.
+over where columns cannot be prefetched) on both.  The look-ahead loop and the one-move loop
+(sweep_loop = 2 and 1) leave bit-identical states, with branching and recomputation.
 """
 import numpy as np
 import pytest
@@ -26,15 +27,15 @@ def _problem(n_omega, n_tau=40, n_walkers=64):
 
 
 @pytest.mark.parametrize("n_omega", [3, 5, 13, 17, 37])
-@pytest.mark.parametrize("W", [0, 2, 8])
-def test_fp32_windows_take_the_oracle_decisions(n_omega, W):
+@pytest.mark.parametrize("W,loop", [(0, 2), (0, 1), (2, 0), (8, 0)])
+def test_fp32_windows_take_the_oracle_decisions(n_omega, W, loop):
     P = _problem(n_omega)
     kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=23)
     an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(shared_bins=W, **kw))
     acc_o, _, _ = an.run(trace=True)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
                   sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, shared_bins=W,
-                              resync_kind=sail.RESYNC_FP32, **kw))
+                              sweep_loop=loop, resync_kind=sail.RESYNC_FP32, **kw))
     g.anneal()
     acc_g, _, _ = g.trace()
     assert acc_g.shape == acc_o.shape
@@ -59,7 +60,7 @@ def test_fp32_hastings_windows_take_the_oracle_decisions(n_omega):
     acc_o, _, _ = an.run(trace=True)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
                   sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, hastings=True,
-                              resync_kind=sail.RESYNC_FP32, **kw))
+                              sweep_loop=2, resync_kind=sail.RESYNC_FP32, **kw))
     g.anneal()
     acc_g, _, _ = g.trace()
     same = np.all(acc_g == acc_o, axis=0)
@@ -83,3 +84,23 @@ def test_fp32_wide_tau_takes_the_oracle_decisions(W):
     assert same.mean() >= 0.9, same.mean()
     assert acc_o.sum() > 0 and (acc_o < 37).any()
     g.close()
+
+
+@pytest.mark.parametrize("hastings", [False, True])
+def test_lookahead_and_one_move_loops_are_the_same_chain(hastings):
+    """Paper-scale grid (200 tau, 1000 bins), 512 walkers, two blocks of 50 sweeps with branching
+    and tensor-core recomputation: both FP32 move loops end in the same bits."""
+    from workloads import paper_scale_double_lorentz
+    P = paper_scale_double_lorentz(1e-4, n_walkers=512)
+    out = []
+    for loop in (1, 2):
+        prm = sail.Params(n_walkers=512, precision=sail.PREC_FP32, n_sweeps=100, sweeps_per_block=50,
+                          resync_every=25, branching=True, T_start=10.0, T_end=1e-6, A=P.A, B=P.B, seed=13,
+                          hastings=hastings, sweep_loop=loop, resync_kind=sail.RESYNC_TENSOR_BF16, trace=True)
+        g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
+        stats = g.anneal()
+        a, R, chi2, acc, _ = g.state()
+        out.append((a, R, chi2, acc, g.trace()[0], [s["positivity_rejected"] for s in stats]))
+        g.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
