@@ -104,3 +104,24 @@ def test_lookahead_and_one_move_loops_are_the_same_chain(hastings):
         g.close()
     for x, y in zip(out[0], out[1]):
         np.testing.assert_array_equal(np.asarray(x), np.asarray(y))
+
+
+@pytest.mark.parametrize("W,loop", [(0, 1), (0, 2), (4, 0)])
+def test_fp32_paper_grid_takes_the_oracle_decisions(W, loop):
+    """The benchmark's grid (200 tau, 1000 bins, noise 1e-4), 64 walkers, 2 sweeps of 1000 moves
+    at T = chi2_0 / 10: at least 90% of the walkers accept exactly the oracle's number of moves
+    in both sweeps."""
+    from workloads import paper_scale_double_lorentz
+    P = paper_scale_double_lorentz(1e-4, n_walkers=64)
+    kw = dict(n_sweeps=2, sweeps_per_block=2, resync_every=1, branching=False, T_start=0.1, T_end=0.1, seed=47)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(shared_bins=W, **kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, shared_bins=W,
+                              sweep_loop=loop, resync_kind=sail.RESYNC_FP32, **kw))
+    g.anneal()
+    acc_g, _, _ = g.trace()
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    assert 0 < acc_o.mean() < P.n_omega
+    g.close()
