@@ -1,6 +1,9 @@
 // The FP32 production sweep (Sec. 2.2 moves, Eq. probability-density acceptance): the device
 // code shared by the sweep translation units (sweep_fp32.cu: single-problem kernels and
-// probes; sweep_walk.cu: the kernels with an index walk; sweep_batch.cu: batched kernels).
+// probes; sweep_walk.cu and sweep_hastings.cu: the kernels with an index walk and with the
+// Hastings acceptance; sweep_batch8.cu and sweep_batch16.cu: batched kernels).  Two move loops:
+// run_group takes one move at a time; run_group_ahead looks ahead over drawn proposals and
+// spends the kernel columns on feasible moves only (the same chain bit for bit).
 //
 // Kernel columns from two small tables.  Eq. (efficient-correlation-model) writes the bin
 // kernel as c_i q_i^j with q_i = e^{-dw tau_i}; so with j = 32 h + l,
@@ -11,8 +14,9 @@
 // Walker layout.  One persistent block per SM; G lanes per walker (G = 8: four walkers a warp,
 // for n_tau <= 256; G = 16: two), lane l of a walker's group holding R_i and M_i = Fhat_i - R_i
 // for its 32 / G consecutive i of every 32-tau chunk.  Each lane of a group draws the random
-// words of one of G consecutive moves at once (one Philox call) and works out that move's
-// scalars; the move loop takes them by shuffle within the group.  Delta chi2 =
+// words of one move at a time (one Philox call per move: G consecutive moves, or one window of
+// proposals, per round) and works out that move's scalars; the move loop takes them by shuffle
+// within the group.  Delta chi2 =
 // sum_i d_i (2 R_i + d_i) is reduced by an xor butterfly over the group.
 //
 // Spectrum.  a = g b: an accepted move multiplies the common scale g by r (an unevaluated
