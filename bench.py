@@ -515,6 +515,115 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_versus_fp64(args):
+    """Served mixed precision against the plain FP64 path at equal final chi2.  A closed set of
+    requests, sizes as the uneven batch with the ranges' upper ends lowered (n_tau U{50..200},
+    n_omega U{200..800}, walkers U{256..1024}) so that the FP64 path finishes in seconds, all
+    with the served schedule (T 1e-2 chi2_0 -> 0.3 absolute over --cmp-sweeps sweeps, branching
+    every 100, recomputation every 50), is inverted three ways:
+      fp64:        the plain FP64 path, one handle after another: FP64 spectra and moves, sums
+                   in the oracle's order, FP64 residual recomputation;
+      mixed:       FP32 moves with the tcgen05 BF16 x6 recomputation and FP64 residuals, one
+                   handle after another, each stopping at the first block end where chi2 of
+                   its averaged spectrum is at or below what the FP64 path ended with (else at
+                   the end of the same schedule);
+      mixed_served: the same as mixed, all requests submitted to one server at once
+                   (continuous batching: they share persistent sweep launches);
+      mixed_reseeded: mixed with other seeds and no target, the yardstick for "equal": how far
+                   two runs of the same precision land apart.
+    Each leg's wall time covers create (host arrays in), the anneal and the averaged spectrum
+    back on the host.  Reports inversions/s of each leg and, per request, the final chi2 of the
+    averaged spectrum of each leg."""
+    import torch
+    import paper_1609_07936_gb300 as sail
+    from workloads import random_batch_problem
+    sail.load()
+    probs = [random_batch_problem(i, seed=77, max_tau=200, max_omega=800, max_walkers=1024)
+             for i in range(args.cmp_requests)]
+
+    def prm(P, i, precision, target=0.0):
+        return sail.Params(n_walkers=P.n_walkers, precision=precision, n_sweeps=args.cmp_sweeps,
+                           sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
+                           T_start=1e-2, T_end_abs=0.3, A=P.A, B=P.B, seed=i, target_chi2=target,
+                           resync_kind=RESYNC_KIND)
+
+    # warm-up: module loading and first launches of both paths, outside the timed legs
+    for precision in (sail.PREC_FP64, sail.PREC_FP32):
+        P = probs[0]
+        w = prm(P, 0, precision)
+        w.n_sweeps = 2 * SWEEPS_PER_BLOCK
+        g = sail.Sail(P.tau, P.F, P.sigma, P.omega, w)
+        g.anneal()
+        g.average()
+        g.close()
+    torch.cuda.synchronize()
+
+    def one_by_one(precision, targets, seed0=0):
+        out = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i, P in enumerate(probs):
+            g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm(P, seed0 + i, precision, targets[i]))
+            g.anneal()
+            _, _, _, c2 = g.average()
+            out.append((c2, g.info()["sweeps_done"]))
+            g.close()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, out
+
+    wall64, res64 = one_by_one(sail.PREC_FP64, [0.0] * len(probs))
+    targets = [c2 for c2, _ in res64]
+    wall32, res32 = one_by_one(sail.PREC_FP32, targets)
+    _, resr = one_by_one(sail.PREC_FP32, [0.0] * len(probs), seed0=1000)
+
+    need = sum(sail.workspace_size(P.n_tau, P.n_omega, prm(P, i, sail.PREC_FP32)) for i, P in enumerate(probs))
+    server = sail.Server(workspace_bytes=2 * need + (64 << 20), max_resident=len(probs), max_walkers=1 << 20,
+                         sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rids = [server.submit(P.tau, P.F, P.sigma, P.omega, prm(P, i, sail.PREC_FP32, targets[i]))
+            for i, P in enumerate(probs)]
+    resv = {}
+    while len(resv) < len(rids):
+        completed, _, _ = server.step()
+        for rid in completed:
+            r = server.result(rid)
+            resv[rid] = (r["chi2_of_mean"], r["sweeps"])
+    torch.cuda.synchronize()
+    walls = time.perf_counter() - t0
+    server.close()
+    ress = [resv[r] for r in rids]
+
+    per = []
+    for i, P in enumerate(probs):
+        per.append({"n_tau": P.n_tau, "n_omega": P.n_omega, "walkers": P.n_walkers,
+                    "chi2_fp64": res64[i][0], "chi2_mixed": res32[i][0], "chi2_mixed_served": ress[i][0],
+                    "chi2_mixed_reseeded": resr[i][0],
+                    "sweeps_fp64": res64[i][1], "sweeps_mixed": res32[i][1], "sweeps_mixed_served": ress[i][1]})
+    r32 = np.array([p["chi2_mixed"] / p["chi2_fp64"] for p in per])
+    rsv = np.array([p["chi2_mixed_served"] / p["chi2_fp64"] for p in per])
+    rsd = np.array([p["chi2_mixed_reseeded"] / p["chi2_mixed"] for p in per])
+    gm = lambda r: float(np.exp(np.mean(np.log(r))))
+    n = len(probs)
+    out = {"metric": "inversions/sec at equal final chi2", "value": n / walls, "unit": "inversions/s", "n_gpus": 1,
+           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{n} requests, n_tau U{{50..200}} x n_omega U{{200..800}} x walkers U{{256..1024}}, "
+                                  f"random 1-4 peaks, noise log-uniform [1e-5, 1e-3], {args.cmp_sweeps}-sweep schedule "
+                                  "T 1e-2 chi2_0 -> 0.3 absolute, branching every 100 sweeps, recomputation every 50",
+                      "target": "chi2 of the averaged spectrum <= the FP64 path's final value, or the schedule's end"},
+           "inversions_per_s": {"fp64": n / wall64, "mixed": n / wall32, "mixed_served": n / walls},
+           "wall_s": {"fp64": wall64, "mixed": wall32, "mixed_served": walls},
+           "speedup_served_vs_fp64": wall64 / walls,
+           "reached_fp64_chi2": {"mixed": float(np.mean(r32 <= 1.0)), "mixed_served": float(np.mean(rsv <= 1.0))},
+           "chi2_ratio_to_fp64": {"mixed_geomean": gm(r32), "mixed_median": float(np.median(r32)),
+                                  "mixed_min": float(r32.min()), "mixed_max": float(r32.max()),
+                                  "served_geomean": gm(rsv), "served_max": float(rsv.max())},
+           "chi2_ratio_reseeded_to_mixed": {"geomean": gm(rsd), "median": float(np.median(rsd)),
+                                            "min": float(rsd.min()), "max": float(rsd.max())},
+           "requests": per}
+    print(json.dumps(out), flush=True)
+
+
 def run_band(args):
     """The paper's example (Sec. lorentzian-model): the two-peak Lorentzian band on 1000 bins of
     [0, 3.5], 1500 walkers, exact data and correlated undersampling noise at relative levels
@@ -576,12 +685,14 @@ def main():
     ap.add_argument("--clocks-dir", default="",
                     help="directory for the raw nvidia-smi clock samples of the timed region (default: /tmp)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision"])
+    ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision", "versus_fp64"])
     ap.add_argument("--band-sweeps", type=int, default=20000, help="band example: sweep budget per inversion")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
+    ap.add_argument("--cmp-requests", type=int, default=12, help="versus_fp64: requests in the closed set")
+    ap.add_argument("--cmp-sweeps", type=int, default=400, help="versus_fp64: sweeps of the schedule")
     ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1, 2],
                     help="residual recomputation: 0 = FP32-FMA GEMM, 1 = tensor cores (tcgen05 TF32 x3), "
                          "2 = tensor cores (tcgen05 BF16 x6)")
@@ -611,6 +722,8 @@ def main():
         run_band(args)
     elif args.workload == "precision":
         run_precision(args)
+    elif args.workload == "versus_fp64":
+        run_versus_fp64(args)
     else:
         run_gpu(args, rank, world, local_rank)
 

@@ -52,17 +52,19 @@ def test_fp64_shared_bins_reproduce_every_decision(W, hastings, n_walkers):
     g.close()
 
 
-@pytest.mark.parametrize("W,hastings,n_walkers", [(0, False, 64), (2, False, 64), (4, False, 64), (8, False, 61),
-                                                  (8, True, 64), (4, True, 37), (2, True, 33)])
-@pytest.mark.parametrize("loop", [1, 2])
+_DECISION_CASES = [(0, False, 64), (2, False, 64), (4, False, 64), (8, False, 61), (8, True, 64), (4, True, 37),
+                   (2, True, 33)]
+
+
+# the move-loop choice (1 one move at a time, 2 look-ahead) applies to own bins only
+@pytest.mark.parametrize("W,hastings,n_walkers,loop",
+                         [c + (2,) for c in _DECISION_CASES] + [c + (1,) for c in _DECISION_CASES if c[0] == 0])
 def test_fp32_sweep_takes_the_oracle_decisions(W, hastings, n_walkers, loop):
     """Tiny workload (32 tau points, 64 bins), 4 sweeps of 64 moves at T = chi2_0 / 2 with a
     recomputation every 2 sweeps, no branching: at least 90% of the walkers accept exactly
     the oracle's number of moves in every sweep, and those walkers end within 1e-4 of the
     oracle's spectra."""
     P = tiny_double_lorentz()
-    if W and loop == 1:
-        pytest.skip("the move loop choice applies to own bins")
     an, g = _pair(P, n_walkers, sail.PREC_FP32, W, hastings, loop=loop, n_sweeps=4, sweeps_per_block=4,
                   resync_every=2, branching=False, T_start=0.5, T_end=0.5, seed=17)
     acc_o, _, _ = an.run(trace=True)

@@ -67,3 +67,9 @@ def test_other_recipes_shapes():
     R = random_batch_problem(5, seed=1)
     assert 50 <= R.n_tau <= 500 and 200 <= R.n_omega <= 2000 and 256 <= R.n_walkers <= 4096
     assert 1e-5 <= R.extra["noise_level"] <= 1e-3
+    # lowered size caps draw in the same order: the noise level and the peaks are unchanged
+    for i in range(8):
+        full = random_batch_problem(i, seed=77)
+        small = random_batch_problem(i, seed=77, max_tau=200, max_omega=800, max_walkers=1024)
+        assert 50 <= small.n_tau <= 200 and 200 <= small.n_omega <= 800 and 256 <= small.n_walkers <= 1024
+        assert small.extra["noise_level"] == full.extra["noise_level"] and small.peaks == full.peaks

@@ -109,13 +109,15 @@ def precision_random_peaks(seed: int = 0, n_tau: int = 512, n_omega: int = 2048,
                         noise_level, seed + 1, n_walkers)
 
 
-def random_batch_problem(index: int, seed: int = 0, rng: Optional[np.random.Generator] = None) -> Problem:
+def random_batch_problem(index: int, seed: int = 0, rng: Optional[np.random.Generator] = None,
+                         max_tau: int = 500, max_omega: int = 2000, max_walkers: int = 4096) -> Problem:
     """One inversion of the uneven batch: n_tau ~ U{50..500}, n_omega ~ U{200..2000},
-    walkers ~ U{256..4096}, noise log-uniform on [1e-5, 1e-3]."""
+    walkers ~ U{256..4096}, noise log-uniform on [1e-5, 1e-3].  The max_* arguments lower the
+    upper ends of the three size ranges (same draws, same order)."""
     rng = rng or np.random.default_rng([seed, index])
-    n_tau = int(rng.integers(50, 501))
-    n_omega = int(rng.integers(200, 2001))
-    n_walkers = int(rng.integers(256, 4097))
+    n_tau = int(rng.integers(50, max_tau + 1))
+    n_omega = int(rng.integers(200, max_omega + 1))
+    n_walkers = int(rng.integers(256, max_walkers + 1))
     level = float(10.0 ** rng.uniform(-5.0, -3.0))
     peaks = random_peaks(rng)
     tau = 8.0 * np.arange(n_tau, dtype=np.float64) / (n_tau - 1)
