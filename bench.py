@@ -437,7 +437,8 @@ def run_serve(args):
     wall = time.perf_counter() - t_start
     lat = np.array([v[0] for v in done.values()])
     conv = np.array([v[1] for v in done.values()])
-    ttt = lat[conv] if conv.any() else np.array([np.nan])
+    ttt = lat[conv]
+    pct = lambda x, q: float(np.percentile(x, q)) if x.size else None   # null when none converged
     out = {"metric": "inversions/sec (served)", "value": len(done) / wall, "unit": "inversions/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served: Poisson arrivals {args.rate}/s for {args.duration} s ({len(arrivals)} requests), "
@@ -447,7 +448,7 @@ def run_serve(args):
            "wall_s": wall, "walker_moves_per_s": moves / wall,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "converged_fraction": float(conv.mean()),
-           "time_to_target_p50_s": float(np.nanpercentile(ttt, 50)), "time_to_target_p99_s": float(np.nanpercentile(ttt, 99))}
+           "time_to_target_p50_s": pct(ttt, 50), "time_to_target_p99_s": pct(ttt, 99)}
     print(json.dumps(out), flush=True)
     server.close()
 

@@ -1,5 +1,6 @@
 // Batched FP32 sweep: many inversions in one persistent launch per lane count and move-loop
-// variant (the move loop of sweep_group.cuh).  A launch holds the loops of every chunk count in
+// variant (the move loop of sweep_group.cuh; the plain loop reads each move's spectrum values
+// one move ahead, since the batch's spectra stay in global memory).  A launch holds the loops of every chunk count in
 // one body; the one-move-at-a-time loop (run_group) fits that body's registers without spills,
 // the look-ahead loop does not, so the batch keeps the former.  sweep_batch8.cu and sweep_batch16.cu
 // instantiate it for 8 and 16 lanes per walker.
@@ -13,25 +14,25 @@ namespace {
 template <int G, int MODE>
 __device__ __forceinline__ void run_group_c(const BatchProblem &BP, int grp, const float *sm) {
     switch (BP.P.n_tau_pad / 32) {
-        case 1: run_group<G, 1, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 2: run_group<G, 2, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 3: run_group<G, 3, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 4: run_group<G, 4, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 5: run_group<G, 5, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 6: run_group<G, 6, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 7: run_group<G, 7, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-        case 8: run_group<G, 8, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 1: run_group<G, 1, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 2: run_group<G, 2, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 3: run_group<G, 3, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 4: run_group<G, 4, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 5: run_group<G, 5, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 6: run_group<G, 6, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 7: run_group<G, 7, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+        case 8: run_group<G, 8, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
         default:
             if constexpr (G == 16) {
                 switch (BP.P.n_tau_pad / 32) {
-                    case 9: run_group<16, 9, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 10: run_group<16, 10, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 11: run_group<16, 11, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 12: run_group<16, 12, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 13: run_group<16, 13, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 14: run_group<16, 14, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 15: run_group<16, 15, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
-                    case 16: run_group<16, 16, false, MODE>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 9: run_group<16, 9, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 10: run_group<16, 10, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 11: run_group<16, 11, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 12: run_group<16, 12, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 13: run_group<16, 13, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 14: run_group<16, 14, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 15: run_group<16, 15, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
+                    case 16: run_group<16, 16, false, MODE, MODE == kPlain>(BP.P, BP.S, BP.n0, BP.n1, grp, sm, nullptr, 0); break;
                     default: break;
                 }
             }

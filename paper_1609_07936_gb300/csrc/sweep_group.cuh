@@ -255,7 +255,13 @@ __device__ __forceinline__ float delta_sum(const f2 (&d)[C][H], const f2 (&R)[C]
 // evaluated: the pipeline's registers do not fit).  Columns are loaded for every walker, also
 // those whose move then fails the positivity test: with few warps per SM the sweep is bound by
 // the latency of each warp's instruction stream more than by shared-memory bandwidth.
-template <int G, int C, bool STAGED, int MODE>
+//
+// BA (uniform bins only): each move's b_p, b_s are read one move ahead, during the move before
+// it, and patched if that move wrote one of those bins.  The batched kernel's plain loop, whose
+// spectra stay in global memory, takes this (measured +6% on uneven batches); the
+// single-problem kernel reads b when the move is evaluated (the early read measured 0.5% slower
+// with staged spectra and 6% slower at 512 tau, where the columns are not pipelined).
+template <int G, int C, bool STAGED, int MODE, bool BA = false>
 __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S, int n0, int n1, int grp,
                                           const float *sm,
                           float *b_stage, int walker_lo) {
@@ -267,6 +273,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     // when it is evaluated
     constexpr bool WALK = MODE == kWalk;
     constexpr bool PIPE = C <= 8 && !WALK;
+    constexpr bool BAHEAD = BA && !WALK;   // b read one move ahead (above)
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
     const float *sQhi = sm;
     const float *sQlo = sQhi + (size_t)NH * PAD;
@@ -328,6 +335,12 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
         MoveDraw cur = take_move(mine, 0, G);
         f2 dcur[PIPE ? C : 1][H];
         if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
+        // b at the current move's bins, read one move ahead (BAHEAD, see below)
+        float bpc = 0.0f, bsc = 0.0f;
+        if constexpr (BAHEAD) {
+            bpc = bget(cur.ps & 0xFFFF);
+            bsc = bget(cur.ps >> 16);
+        }
         for (int mv = 0; mv < NO; ++mv) {
             if constexpr (WALK) {
                 // the index walk (Sec. 2.3) on the spectrum as it is now: lane t of the group
@@ -363,11 +376,31 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
                 cur.ps = wp | (ws << 16);
                 deltas(cur.eps, wp, ws, sBeta, sRgap, cur.dp, cur.ds);
             }
+            // BAHEAD: move k+1's words (they do not depend on move k's outcome) and its b
+            // values, read now so that their latency overlaps move k; if move k is accepted
+            // and writes one of those bins, the written value replaces the one read (the value
+            // a read after the write returns).  nxt's bins are valid indices also past the
+            // sweep's last move.
+            MoveDraw nxt;
+            float bpn = 0.0f, bsn = 0.0f;
+            if constexpr (BAHEAD) {
+                nxt = take_move(mine, (mv + 1) & (G - 1), G);
+                bpn = bget(nxt.ps & 0xFFFF);
+                bsn = bget(nxt.ps >> 16);
+            }
             // move k: positivity (Eq. probability-density) on the spectrum as it is now
             const int p = cur.ps & 0xFFFF, s = cur.ps >> 16;
             const float r = 1.0f - cur.eps;
-            const float ap = fmaf(r, ghi * bget(p), cur.dp);
-            const float as = fmaf(r, ghi * bget(s), cur.ds);
+            float bp, bs;
+            if constexpr (BAHEAD) {
+                bp = bpc;
+                bs = bsc;
+            } else {
+                bp = bget(p);
+                bs = bget(s);
+            }
+            const float ap = fmaf(r, ghi * bp, cur.dp);
+            const float as = fmaf(r, ghi * bs, cur.ds);
             const bool ok = active && ap >= 0.0f && as >= 0.0f;
             pos += (active && !ok);
             // move k: residual change d = eps M + dpart
@@ -385,9 +418,9 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
 #pragma unroll
                     for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], d[c][h]);
             }
-            // move k+1: its words and (pipelined) its columns, into dcur, now free; neither
-            // depends on move k's outcome
-            const MoveDraw nxt = take_move(mine, (mv + 1) & (G - 1), G);
+            // move k+1: its words (unless taken above) and (pipelined) its columns, into dcur,
+            // now free; neither depends on move k's outcome
+            if constexpr (!BAHEAD) nxt = take_move(mine, (mv + 1) & (G - 1), G);
             if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
             // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
             const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
@@ -402,7 +435,17 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
                     }
                 }
                 pair_scale(ghi, glo, r);
-                if (gl == 0) {
+                if constexpr (BAHEAD) {
+                    const float inv_g = 1.0f / ghi;
+                    const float bp_new = ap * inv_g, bs_new = as * inv_g;
+                    if (gl == 0) {
+                        bset(p, bp_new);
+                        bset(s, bs_new);
+                    }
+                    const int pn = nxt.ps & 0xFFFF, sn = nxt.ps >> 16;
+                    bpn = pn == p ? bp_new : (pn == s ? bs_new : bpn);
+                    bsn = sn == p ? bp_new : (sn == s ? bs_new : bsn);
+                } else if (gl == 0) {
                     const float inv_g = 1.0f / ghi;
                     bset(p, ap * inv_g);
                     bset(s, as * inv_g);
@@ -412,6 +455,10 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             }
             __syncwarp();
             cur = nxt;
+            if constexpr (BAHEAD) {
+                bpc = bpn;
+                bsc = bsn;
+            }
             // the next batch of G moves, one per lane, before its first move is taken
             if (((mv + 2) & (G - 1)) == 0 && mv + 2 < NO)
                 mine = draw_move<MODE>(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);

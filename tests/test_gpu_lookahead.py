@@ -68,9 +68,11 @@ def test_fp32_hastings_windows_take_the_oracle_decisions(n_omega):
     g.close()
 
 
+@pytest.mark.parametrize("n_tau", [300, 512])
 @pytest.mark.parametrize("W", [0, 2, 4])
-def test_fp32_wide_tau_takes_the_oracle_decisions(W):
-    P = _problem(37, n_tau=300, n_walkers=32)
+def test_fp32_wide_tau_takes_the_oracle_decisions(W, n_tau):
+    """300 tau points (10 chunks) and the library's maximum, 512 (16 chunks)."""
+    P = _problem(37, n_tau=n_tau, n_walkers=32)
     kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=41)
     an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 32, O.Schedule(shared_bins=W, **kw))
     acc_o, _, _ = an.run(trace=True)
@@ -125,3 +127,30 @@ def test_fp32_paper_grid_takes_the_oracle_decisions(W, loop):
     assert same.mean() >= 0.9, same.mean()
     assert 0 < acc_o.mean() < P.n_omega
     g.close()
+
+
+@pytest.mark.parametrize("W", [0, 4])
+def test_spectra_in_global_memory_leave_the_same_bits(W):
+    """512 tau x 1024 bins, no branching: 64 walkers leave their spectra staged in shared memory
+    (factor tables 136 KB + 8 or 16 KB per walker group), 4096 walkers do not (7-14 groups per
+    block), and each walker's chain depends only on its own index, so walkers 0..63 end in the
+    same bits either way.  The one-move loop reads a move's b values one move ahead and patches
+    them after an accepted move that wrote one of those bins; this compares that path in shared
+    and in global memory."""
+    from workloads import make_problem as mk
+    tau = 8.0 * np.arange(512, dtype=np.float64) / 511
+    P = mk("global_b", tau, 1024, 20.0, [Peak("lorentz", 2.0, 0.3, 0.6), Peak("lorentz", 5.0, 0.5, 0.4)],
+           1e-4, 5, 64)
+    out = []
+    for n_walkers in (64, 4096):
+        prm = sail.Params(n_walkers=n_walkers, precision=sail.PREC_FP32, n_sweeps=4, sweeps_per_block=4,
+                          resync_every=2, branching=False, T_start=0.5, T_end=0.5, A=P.A, B=P.B, seed=53,
+                          shared_bins=W, resync_kind=sail.RESYNC_FP32, trace=True)
+        g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
+        g.anneal()
+        a, R, chi2, acc, _ = g.state()
+        out.append((a[:64], R[:64], chi2[:64], acc[:64], g.trace()[0][:, :64]))
+        g.close()
+    assert out[0][4].sum() > 0 and (out[0][4] < 1024).any()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)

@@ -140,6 +140,30 @@ def test_fp64_path_ragged_sizes_and_partial_block():
     np.testing.assert_array_equal(chi2, an.chi2)
 
 
+def test_fp64_path_at_the_maximum_tau_count():
+    """512 tau points (the library's maximum: 16 chunks of 32 per lane), a bin count that is not
+    a multiple of 32, branching every 3 sweeps and a recomputation every 2: every decision,
+    multiplier and final state bit-identical to the oracle."""
+    tau = 8.0 * np.arange(512, dtype=np.float64) / 511
+    P = make_problem("max_tau", tau, 45, 10.0, [Peak("lorentz", 2.0, 0.3, 0.6), Peak("gauss", 5.0, 0.5, 0.4)],
+                     1e-4, 9, 8)
+    an, g = _pair(P, 8, sail.PREC_FP64, n_sweeps=7, sweeps_per_block=3, resync_every=2,
+                  branching=True, T_start=1.0, T_end=1e-2, seed=19)
+    acc_o, m_o, d_o = an.run(trace=True)
+    g.anneal()
+    acc_g, m_g, d_g = g.trace()
+    np.testing.assert_array_equal(acc_g, acc_o)
+    np.testing.assert_array_equal(m_g, m_o)
+    np.testing.assert_array_equal(d_g, d_o)
+    assert acc_o.sum() > 0 and (acc_o < P.n_omega).any()
+    a, R, chi2, _, h = g.state()
+    np.testing.assert_array_equal(h, an.hash)
+    np.testing.assert_array_equal(a, an.a)
+    np.testing.assert_array_equal(R, an.R)
+    np.testing.assert_array_equal(chi2, an.chi2)
+    g.close()
+
+
 def test_single_walker_and_edge_cases():
     """One walker (no branching possible) and a two-bin model (every move a no-op)."""
     P = tiny_double_lorentz()
