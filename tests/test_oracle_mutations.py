@@ -46,6 +46,20 @@ MUTATIONS = {
     "shared_group_index": ("(uint32_t)(w - w % prm->shared_bins)", "(uint32_t)(w / prm->shared_bins)"),
     # shared bins ignored (every walker its own bins)
     "shared_ignored": ("    if (prm->shared_bins > 1) {", "    if (prm->shared_bins > 1 << 30) {"),
+    # Metropolis test for exp(+chi2 / T)
+    "metropolis_sign": ("return D <= 0.0 || u < exp(-D / T);", "return D <= 0.0 || u < exp(D / T);"),
+    # accepted move that forgets to rescale the other bins by r
+    "rescale_dropped": ("for (int j = 0; j < n_omega; ++j) a[j] = r * a[j];", ""),
+    # residual updated with the wrong sign of d
+    "residual_sign": ("R[i] = R[i] + d[i];", "R[i] = R[i] - d[i];"),
+    # amplitude heuristic with one power of the acceptance too many
+    "amplitude_power": ("for (int k = 1; k < (int)y_m; ++k) y = y * q;", "for (int k = 1; k <= (int)y_m; ++k) y = y * q;"),
+    # start-spectrum bisection moving the wrong end
+    "start_bisection": ("if (s1 / s0 > target) lo = mid; else hi = mid;", "if (s1 / s0 > target) hi = mid; else lo = mid;"),
+    # geometric schedule running from T_end up to T_start
+    "schedule_inverted": ("pow(prm->T_end / prm->T_start, t)", "pow(prm->T_start / prm->T_end, t)"),
+    # average that drops walkers exactly at the chi2 cut
+    "average_cut": ("if (!(chi2[w] <= cut)) continue;\n        used += 1;", "if (!(chi2[w] < cut)) continue;\n        used += 1;"),
 }
 
 
@@ -94,7 +108,11 @@ def _pins_pass(L):
                   lambda: Wk.test_walk_law_matches_the_matrix_power(3, 0.0),
                   lambda: Hs.test_jacobian_is_r_to_the_n_minus_4(0.07),
                   Hs.test_hastings_chain_samples_the_uniform_polytope,
-                  lambda: Sh.test_first_walkers_follow_their_own_bins(4)]
+                  lambda: Sh.test_first_walkers_follow_their_own_bins(4),
+                  V.test_zero_temperature_never_raises_chi2, V.test_sweeps_keep_invariants_and_bookkeeping,
+                  V.test_amplitude_heuristic, V.test_temperature_schedule_is_geometric,
+                  lambda: M.test_start_spectrum_sum_rules_and_max_entropy(0.15),
+                  B.test_average_over_good_walkers]
         for c in checks:
             try:
                 c()
