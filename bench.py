@@ -416,7 +416,8 @@ def run_serve(args):
     while nxt < len(arrivals) or len(done) < len(arrivals):
         now = time.perf_counter() - t_start
         while nxt < len(arrivals) and arrivals[nxt] <= now:
-            P = random_batch_problem(nxt, seed=99)
+            P = random_batch_problem(nxt, seed=99, max_tau=args.max_tau, max_omega=args.max_omega,
+                                     max_walkers=args.max_walkers)
             prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=args.serve_sweeps,
                               sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
                               T_start=1e-2, T_end_abs=0.3, A=P.A, B=P.B, seed=nxt, target_chi2=1.2 * P.n_tau,
@@ -442,13 +443,15 @@ def run_serve(args):
     out = {"metric": "inversions/sec (served)", "value": len(done) / wall, "unit": "inversions/s", "n_gpus": 1,
            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"served: Poisson arrivals {args.rate}/s for {args.duration} s ({len(arrivals)} requests), "
-                                  f"sizes as the uneven batch, target chi2 <= 1.2 n_tau, budget {args.serve_sweeps} sweeps, "
+                                  f"sizes as the uneven batch (n_tau U{{50..{args.max_tau}}}, n_omega U{{200..{args.max_omega}}}, "
+                                  f"walkers U{{256..{args.max_walkers}}}), target chi2 <= 1.2 n_tau, budget {args.serve_sweeps} sweeps, "
                                   f"T 1e-2 chi2_0 -> 0.3 absolute, admission cap {cap / 1e9:.0f} GB",
                       "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6"}[args.resync_kind]},
            "wall_s": wall, "walker_moves_per_s": moves / wall,
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "converged_fraction": float(conv.mean()),
-           "time_to_target_p50_s": pct(ttt, 50), "time_to_target_p99_s": pct(ttt, 99)}
+           "time_to_target_p50_s": pct(ttt, 50), "time_to_target_p99_s": pct(ttt, 99),
+           "sweeps_to_target_p50": pct(np.array([v[2] for v in done.values() if v[1]], dtype=float), 50)}
     print(json.dumps(out), flush=True)
     server.close()
 
@@ -692,6 +695,9 @@ def main():
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
     ap.add_argument("--serve-sweeps", type=int, default=1000, help="serving: sweep budget per request")
+    ap.add_argument("--max-tau", type=int, default=500, help="serving: upper end of the n_tau range")
+    ap.add_argument("--max-omega", type=int, default=2000, help="serving: upper end of the n_omega range")
+    ap.add_argument("--max-walkers", type=int, default=4096, help="serving: upper end of the walker range")
     ap.add_argument("--cmp-requests", type=int, default=12, help="versus_fp64: requests in the closed set")
     ap.add_argument("--cmp-sweeps", type=int, default=400, help="versus_fp64: sweeps of the schedule")
     ap.add_argument("--resync-kind", type=int, default=RESYNC_KIND, choices=[0, 1, 2],
