@@ -58,6 +58,11 @@ MUTATIONS = {
     "start_bisection": ("if (s1 / s0 > target) lo = mid; else hi = mid;", "if (s1 / s0 > target) hi = mid; else lo = mid;"),
     # geometric schedule running from T_end up to T_start
     "schedule_inverted": ("pow(prm->T_end / prm->T_start, t)", "pow(prm->T_start / prm->T_end, t)"),
+    # sum-rule restoration tilting the wrong way
+    "restore_tilt_sign": ("double lambda = V > 0.0 ? (B / A - c) * A1 / V : 0.0;",
+                          "double lambda = V > 0.0 ? (c - B / A) * A1 / V : 0.0;"),
+    # sum-rule restoration without its guard against negative factors
+    "restore_unguarded": ("    if (!(fabs(lambda * (x[N - 1] - x[0])) < 0.5)) lambda = 0.0;\n", ""),
     # average that drops walkers exactly at the chi2 cut
     "average_cut": ("if (!(chi2[w] <= cut)) continue;\n        used += 1;", "if (!(chi2[w] < cut)) continue;\n        used += 1;"),
 }
@@ -100,6 +105,7 @@ def _pins_pass(L):
         from tests import test_oracle_walk as Wk
         from tests import test_oracle_hastings as Hs
         from tests import test_oracle_shared as Sh
+        from tests import test_oracle_restore as Rs
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
                   lambda: B.test_multipliers_match_enumeration(0),
@@ -112,7 +118,8 @@ def _pins_pass(L):
                   V.test_zero_temperature_never_raises_chi2, V.test_sweeps_keep_invariants_and_bookkeeping,
                   V.test_amplitude_heuristic, V.test_temperature_schedule_is_geometric,
                   lambda: M.test_start_spectrum_sum_rules_and_max_entropy(0.15),
-                  B.test_average_over_good_walkers]
+                  B.test_average_over_good_walkers,
+                  Rs.test_hand_worked_example, Rs.test_tilt_skipped_when_a_factor_could_turn_negative]
         for c in checks:
             try:
                 c()
