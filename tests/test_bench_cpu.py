@@ -1,5 +1,6 @@
-"""CPU: the benchmark's reference arm (the FP64 oracle on the host cores) prints the one JSON
-line of the benchmark contract; under a multi-rank launch only rank 0 prints."""
+"""CPU: the benchmark's reference arm (the FP64 oracle on the host cores, warm-up and timed
+steps of one block each) prints the one JSON line of the benchmark contract; under a
+multi-rank launch only rank 0 prints."""
 import json
 import os
 import subprocess
@@ -11,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(env_extra):
     env = dict(os.environ, **env_extra)
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                          "--cpu-sample-walkers", "8", "--steps", "2", "--warmup", "3"],
+                          "--cpu-sample-walkers", "8", "--ref-seconds", "5", "--steps", "2", "--warmup", "3"],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr[-2000:]
     return [ln for ln in out.stdout.splitlines() if ln.strip()]
@@ -26,7 +27,8 @@ def test_reference_arm_prints_the_contract_line():
     assert d["n_gpus"] == 1 and d["dtype"] == "f64" and d["data"] == "synthetic"
     assert "paper_scale_double_lorentz" in d["config"]["workload"]
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and "8 walkers" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
+    assert "of the 4096 walkers, 3 untimed + 2 timed blocks" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "walker-moves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["ms_per_step"] > 0
