@@ -58,6 +58,12 @@ MUTATIONS = {
     "start_bisection": ("if (s1 / s0 > target) lo = mid; else hi = mid;", "if (s1 / s0 > target) hi = mid; else lo = mid;"),
     # geometric schedule running from T_end up to T_start
     "schedule_inverted": ("pow(prm->T_end / prm->T_start, t)", "pow(prm->T_start / prm->T_end, t)"),
+    # amplitude and acceptance draws taken from each other's word
+    "words_swapped": ("double eps = (y * dmove) * (2.0 * unit(rnd[2]) - 1.0);\n        double u = unit(rnd[3]);",
+                      "double eps = (y * dmove) * (2.0 * unit(rnd[3]) - 1.0);\n        double u = unit(rnd[2]);"),
+    # the bins' word mapped by the other rounding (ceiling instead of floor of w N / 2^32)
+    "bin_rounding": ("int p = (int)(((uint64_t)w0 * (uint64_t)n_omega) >> 32);",
+                     "int p = (int)((((uint64_t)w0 * (uint64_t)n_omega) + 0xFFFFFFFFull) >> 32) % n_omega;"),
     # sum-rule restoration tilting the wrong way
     "restore_tilt_sign": ("double lambda = V > 0.0 ? (B / A - c) * A1 / V : 0.0;",
                           "double lambda = V > 0.0 ? (c - B / A) * A1 / V : 0.0;"),
@@ -106,6 +112,7 @@ def _pins_pass(L):
         from tests import test_oracle_hastings as Hs
         from tests import test_oracle_shared as Sh
         from tests import test_oracle_restore as Rs
+        from tests import test_oracle_sweep_definition as Sd
         checks = [M.test_kernel_is_the_bin_integral, M.test_philox_inverts_to_its_counter,
                   V.test_delta_formulas_keep_both_sums, V.test_delta_chi2_matches_brute_force,
                   lambda: B.test_multipliers_match_enumeration(0),
@@ -119,7 +126,8 @@ def _pins_pass(L):
                   V.test_amplitude_heuristic, V.test_temperature_schedule_is_geometric,
                   lambda: M.test_start_spectrum_sum_rules_and_max_entropy(0.15),
                   B.test_average_over_good_walkers,
-                  Rs.test_hand_worked_example, Rs.test_tilt_skipped_when_a_factor_could_turn_negative]
+                  Rs.test_hand_worked_example, Rs.test_tilt_skipped_when_a_factor_could_turn_negative,
+                  Sd.test_oracle_sweeps_are_the_definition]
         for c in checks:
             try:
                 c()
