@@ -294,6 +294,7 @@ const char *sail_last_error(void) { return g_err.c_str(); }
 
 int sail_workspace_size(int n_tau, int n_omega, const sail_params *p, size_t *bytes) {
     if (!bytes) return fail(SAIL_EINVAL, "bytes is NULL");
+    if (!p) return fail(SAIL_EINVAL, "params is NULL");
     sail_params q = *p;
     if (!std::isfinite(q.B)) q.B = 0.0;  // size does not depend on B
     const int rc = check_params(n_tau, n_omega, &q);
