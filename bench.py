@@ -34,17 +34,24 @@ NOISE = 1e-4
 WORKLOAD = (f"paper_scale_double_lorentz: N_tau={N_TAU} on [0,8], N_omega={N_OMEGA} on [0,20], "
             f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, tensor-core (BF16 x6) resync every {RESYNC_EVERY} sweeps, "
             f"branching every {SWEEPS_PER_BLOCK} sweeps (f=1/4, t=0.1), {N_SWEEPS}-sweep schedule T 10->1e-9")
-METRIC = "walker-moves/sec"
+METRIC = "walker-moves/s"
 MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 
 
 RESYNC_KIND = 2    # residual recomputation on the tensor cores (tcgen05, BF16, three pieces, six products)
 
+# Time to target: each inversion runs until chi2 of its averaged spectrum is <= 1.2 N_tau
+# (checked at every block end) or 20000 sweeps, on the schedule measured to reach that target
+# (geometric from an absolute 1e6 to 0.03, move scale d = 0.1 / N_omega).
+TTT_SWEEPS, TTT_T_START, TTT_T_END, TTT_D_FACTOR, TTT_TARGET = 20000, 1e6, 0.03, 0.1, 1.2
+TTT_INVERSIONS = 4
+
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
-               sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0, sweep_loop: int = 0):
+               sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0, sweep_loop: int = 0,
+               noise: float = NOISE):
     import paper_1609_07936_gb300 as sail
-    P = paper_scale_double_lorentz(NOISE, n_walkers=N_WALKERS)
+    P = paper_scale_double_lorentz(noise, n_walkers=N_WALKERS)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
@@ -227,17 +234,18 @@ def run_gpu(args, rank, world, local_rank):
     launches = info1["kernel_launches"] - info0["kernel_launches"] + args.steps  # + one flush per step
     own_launches = info1["kernel_launches"] - info0["kernel_launches"]
     moves_per_launch = (info1["moves"] - info0["moves"]) / max(sweep_n, 1)
-    # algorithmic shared-memory bytes of a walker-move: b_p and b_s (8 B); then, unless the
-    # move fails the positivity test (Sec. 2.2: checked before delta chi2), two kernel columns,
-    # each the product of two FP32 factor rows of N_tau entries (4 N_tau 4 B)
-    col_bytes = 4 * N_TAU * 4
+    # algorithmic bytes of a walker-move (Sec. 2.2: the update needs the two kernel columns of
+    # the proposed bins and nothing else of size N_tau): b_p and b_s read and, on acceptance,
+    # written (16 B); then, unless the move fails the positivity test (checked before delta
+    # chi2), the columns Khat_p and Khat_s in FP32 (2 N_tau 4 B)
+    col_bytes = 2 * N_TAU * 4
     pos_frac = sum(b["positivity_rejected"] for b in stats) / max(len(stats), 1)
-    bytes_per_move = 8 + (1.0 - pos_frac) * col_bytes
-    bytes_rule = f"8 + (1 - positivity-rejected fraction {pos_frac:.4f}) x {col_bytes}"
+    bytes_per_move = 16 + (1.0 - pos_frac) * col_bytes
+    bytes_rule = f"16 + (1 - positivity-rejected fraction {pos_frac:.4f}) x 2 x {N_TAU} x 4"
     if args.shared_bins:
         # shared bins: a group of W walkers reads one move's columns once
-        bytes_per_move = 8 + col_bytes / args.shared_bins
-        bytes_rule = f"8 + {col_bytes} / {args.shared_bins} (columns read once per group of {args.shared_bins} walkers)"
+        bytes_per_move = 16 + col_bytes / args.shared_bins
+        bytes_rule = f"16 + 2 x {N_TAU} x 4 / {args.shared_bins} (columns read once per group of {args.shared_bins} walkers)"
 
     launch_s = sweep_ms / max(sweep_n, 1) * 1e-3
     achieved = moves_per_launch * bytes_per_move / launch_s / 1e9
@@ -285,6 +293,41 @@ def run_gpu(args, rank, world, local_rank):
                "wall_s": float(t_t.item()), "chi2_of_mean": c2, "walkers_averaged": used}
         h.close()
 
+    # the other two noise levels of the workload (sigma = 1e-3 F and 1e-5 F): the same timed
+    # steps on their own handles, walker-moves/s from CUDA events on the handle's stream
+    noise_levels = []
+    if not args.no_noise_levels:
+        for lvl in (1e-3, 1e-5):
+            P3, prm3 = params_for(seed=rank + 500, resync_kind=args.resync_kind, sweep_lanes=args.sweep_lanes,
+                                  index_walk=args.index_walk, shared_bins=args.shared_bins,
+                                  sweep_loop=args.sweep_loop, noise=lvl)
+            h3 = sail.Sail(P3.tau, P3.F, P3.sigma, P3.omega, prm3)
+            h3.anneal(args.warmup)
+            m0 = h3.info()["moves"]
+            barrier()
+            e0.record(h3.stream)
+            for k in range(args.steps):
+                h3.anneal(1)
+                flush.zero_()
+            e1.record(h3.stream)
+            barrier()
+            ms3, moves3, value3 = aggregate(e0.elapsed_time(e1), h3.info()["moves"] - m0, dist, "cuda")
+            noise_levels.append({"sigma": f"{lvl:g} F", "value": value3, "unit": "walker-moves/s",
+                                 "ms_per_step": ms3 / args.steps})
+            h3.close()
+
+    # inversions/s to target chi2 (p50 / p99), mixed precision against the plain FP64
+    # recomputation of the residual (the same served FP32 sweep; only the recomputation differs)
+    ttt = None
+    if not args.no_to_target:
+        ttt = to_target(sail, torch, args.ttt_inversions, args.resync_kind, seed0=100 * rank)
+        ttt64 = to_target(sail, torch, args.ttt_inversions, 3, seed0=100 * rank)
+        ttt["vs_plain_fp64_resync"] = {
+            "fp64_resync": ttt64,
+            "inversions_per_s_ratio": (ttt["inversions_per_s"] / ttt64["inversions_per_s"]
+                                       if ttt64["inversions_per_s"] > 0 else None),
+            "equal_final_chi2": "both legs stop at the same target chi2 (or the same sweep budget)"}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_walkers)
@@ -297,31 +340,80 @@ def run_gpu(args, rank, world, local_rank):
                        + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
-            "roofline": {"kernel": "sweep_shared" if args.shared_bins else "sweep_fp32", "bound": "alu",
-                         "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                         "frac": fp32_achieved / fp32_peak,
+            "roofline": {"kernel": "sweep_shared" if args.shared_bins else "sweep_fp32", "bound": "smem",
+                         "achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
                          "traffic": None if (args.shared_bins or args.index_walk) else kernel_traffic(),
-                         "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz",
-                         "algorithmic_flops_per_move": flops_per_move,
-                         "flops_per_move_rule": f"{N_TAU} x (9 x (1 - positivity-rejected {pos_frac:.4f}) "
-                                                f"+ 2 x accepted {acc_frac:.4f})",
-                         "smem": {"achieved": achieved, "peak": smem_gbs, "unit": "GB/s", "frac": achieved / smem_gbs,
-                                  "peak_source": "measured live: conflict-free 16-byte shared-memory loads, "
-                                                 "2 blocks x 1024 threads per SM",
-                                  "algorithmic_bytes_per_move": bytes_per_move, "bytes_per_move_rule": bytes_rule},
+                         "traffic_note": "DRAM bytes per sweep launch (ncu); the sweep's operands live in shared memory",
+                         "peak_source": "measured live in this run (not in MEASURED_PEAKS.json, which has HBM and bf16 only): "
+                                        "conflict-free 16-byte shared-memory loads, 2 blocks x 1024 threads per SM",
+                         "algorithmic_bytes_per_move": bytes_per_move, "bytes_per_move_rule": bytes_rule,
+                         "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
+                         "achieved_rule": "moves_per_launch x algorithmic_bytes_per_move / launch_ms (CUDA events "
+                                          "around every sweep launch on the handle's stream)",
+                         "alu": {"bound": "alu", "achieved": fp32_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                                 "frac": fp32_achieved / fp32_peak,
+                                 "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {sm_max_mhz:.0f} MHz",
+                                 "algorithmic_flops_per_move": flops_per_move,
+                                 "flops_per_move_rule": f"{N_TAU} x (9 x (1 - positivity-rejected {pos_frac:.4f}) "
+                                                        f"+ 2 x accepted {acc_frac:.4f})"},
                          "l2_read_gbs_measured": l2_gbs,
                          "sweep_lanes_per_walker": g.info().get("sweep_lanes"),
-                         "moves_per_launch": moves_per_launch, "launch_ms": sweep_ms / max(sweep_n, 1),
                          "sweep_share_of_step": sweep_ms / ms},
             "kernel_ms": {"sweep": sweep_ms, "resync": info1["resync_ms"] - info0["resync_ms"],
                           "branch": info1["branch_ms"] - info0["branch_ms"], "total": ms},
             "e2e": e2e, "gpu_launches": own_launches, "clocks": clk, "cpu_baseline": cpu,
+            "other_noise_levels": noise_levels, "to_target": ttt,
             "last_block": stats[-1] if stats else None,
         }
         print(json.dumps(out), flush=True)
     g.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, seed0: int = 0):
+    """n_inv inversions of the workload (4096 walkers each, seeds seed0..) submitted together to
+    one server whose worker thread runs their blocks side by side (continuous batching); each
+    stops at chi2 of its averaged spectrum <= 1.2 N_tau or at 20000 sweeps.  Times are from the
+    submission of the host arrays to the averaged spectrum on the host (the server's clock)."""
+    P = paper_scale_double_lorentz(noise, n_walkers=N_WALKERS)
+    prms = []
+    for k in range(n_inv):
+        prms.append(sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=TTT_SWEEPS,
+                                sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
+                                T_start_abs=TTT_T_START, T_end_abs=TTT_T_END, move_scale=TTT_D_FACTOR / N_OMEGA,
+                                A=P.A, B=P.B, seed=seed0 + k, target_chi2=TTT_TARGET * N_TAU,
+                                resync_kind=resync_kind))
+    need = n_inv * sail.workspace_size(N_TAU, N_OMEGA, prms[0]) + (256 << 20)
+    server = sail.Server(workspace_bytes=need, max_resident=n_inv, max_walkers=n_inv * N_WALKERS,
+                         sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY)
+    torch.cuda.synchronize()
+    server.start()
+    t0 = time.perf_counter()
+    rids = [server.submit(P.tau, P.F, P.sigma, P.omega, prm) for prm in prms]
+    done = set()
+    while len(done) < n_inv:
+        done.update(server.poll()[0])
+        time.sleep(0.01)
+    wall = time.perf_counter() - t0
+    server.stop()
+    res = []
+    for rid in rids:
+        r, inf = server.result(rid), server.request_info(rid)
+        res.append({"converged": r["converged"], "sweeps": r["sweeps"], "chi2_of_mean": r["chi2_of_mean"],
+                    "time_s": inf["t_done"] - inf["t_submit"]})
+    server.close()
+    t = np.array([x["time_s"] for x in res])
+    conv = np.array([x["converged"] for x in res])
+    moves = sum(x["sweeps"] for x in res) * N_OMEGA * N_WALKERS
+    pct = lambda q: float(np.percentile(t[conv], q)) if conv.any() else None
+    return {"inversions": n_inv, "target": f"chi2 of the averaged spectrum <= {TTT_TARGET} N_tau = {TTT_TARGET * N_TAU:g}",
+            "converged_fraction": float(conv.mean()), "time_to_target_p50_s": pct(50), "time_to_target_p99_s": pct(99),
+            "inversions_per_s": float(conv.sum()) / wall, "wall_s": wall, "walker_moves_per_s": moves / wall,
+            "sweeps_to_target": [x["sweeps"] for x in res], "final_chi2": [x["chi2_of_mean"] for x in res],
+            "schedule": f"geometric T {TTT_T_START:g} -> {TTT_T_END:g} (absolute) over {TTT_SWEEPS} sweeps, "
+                        f"move scale {TTT_D_FACTOR:g} / N_omega, branching every {SWEEPS_PER_BLOCK} sweeps",
+            "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6", 3: "fp64-fma"}[resync_kind]}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -490,11 +582,15 @@ def run_reference(args, rank, world):
            "sample": f"{n_w} of the {N_WALKERS} walkers, {args.warmup} untimed + {args.steps} timed blocks of "
                      f"{SWEEPS_PER_BLOCK} sweeps (2 resyncs and a branching each), {moves:.3g} moves in {dt:.1f} s"}
     out = {"metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": MOVES_PER_STEP / value * 1e3,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "ms_per_step_scaled": {"value": MOVES_PER_STEP / value * 1e3,
+                                  "rule": f"one block of all {N_WALKERS} walkers at the sample's walker-moves/s "
+                                          "(extrapolated, not run)"},
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "parallelism": "CPU oracle, OpenMP over walkers",
-                      "step": f"one block of {n_w} walkers; ms_per_step scaled to the full {N_WALKERS}"},
+                      "step": f"one block (100 sweeps, 2 resyncs, a branching) of a {n_w}-walker sample "
+                              f"of the {N_WALKERS} walkers"},
            "cpu_baseline": cpu,
            "e2e": {"value": value, "unit": "walker-moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -721,6 +817,11 @@ def main():
     ap.add_argument("--clocks-dir", default="",
                     help="directory for the raw nvidia-smi clock samples of the timed region (default: /tmp)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-to-target", action="store_true", help="skip the time-to-target legs")
+    ap.add_argument("--ttt-inversions", type=int, default=TTT_INVERSIONS,
+                    help="time to target: inversions of the workload submitted together")
+    ap.add_argument("--no-noise-levels", action="store_true",
+                    help="skip the timed steps at the workload's other noise levels (1e-3, 1e-5)")
     ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision", "versus_fp64"])
     ap.add_argument("--band-sweeps", type=int, default=20000, help="band example: sweep budget per inversion")
     ap.add_argument("--batch-size", type=int, default=256)

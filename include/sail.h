@@ -43,7 +43,9 @@ extern "C" {
 #define SAIL_PREC_FP64 0   /* validation path: FP64 state, explicit rescale of every bin, sums in the
                               oracle's order, no fused multiply-add */
 #define SAIL_PREC_FP32 1   /* production path: FP32 state and residual, lazy common scale,
-                              FP64 residual recomputation and chi2 */
+                              FP64 residual recomputation and chi2; sail_create refuses data whose
+                              weighted terms could leave FP32's range (max_ij K_ij/sigma_i * A or
+                              max_i |F_i|/sigma_i above 1e15) with SAIL_EINVAL */
 
 /* Temperature schedules. */
 #define SAIL_SCHEDULE_GEOMETRIC 0
@@ -79,7 +81,9 @@ typedef struct sail_params {
                                totals appear in sail_info */
     int resync_kind;        /* FP32 state: 0 = FP32-FMA GEMM with FP64 chunk sums, 1 = tensor
                                cores (tcgen05 TF32, three-term split), 2 = tensor cores
-                               (tcgen05 BF16, three pieces per operand and six products) */
+                               (tcgen05 BF16, three pieces per operand and six products),
+                               3 = FP64-FMA GEMM (FP64 products and sums throughout: the plain
+                               FP64 recomputation the mixed-precision forms are compared with) */
     int wait_test;          /* test hook, 0 in use: 1 makes the tensor-core resync withhold its
                                first commit so its bounded wait runs out (sail_anneal then
                                returns SAIL_ETIMEOUT) */
@@ -137,6 +141,9 @@ typedef struct sail_params {
                                drawn and spends columns and reduction on feasible ones only; the
                                same chain bit for bit); 0 = choose: look-ahead when the problem has
                                at least 16 walkers per SM (measured faster there, slower with fewer) */
+    double T_start_abs;     /* > 0: the geometric schedule starts at this absolute temperature
+                               instead of T_start chi2_0 (skip the boiling far above the data's
+                               scale, whatever chi2_0 is); 0 = T_start */
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */
@@ -334,27 +341,64 @@ int sail_batch_destroy(sail_batch_t b);
 /* ---------------------------------------------------------------- serving
  * Continuous batching of inversion requests (no counterpart in the paper, which inverts one
  * data set at a time; the requests are the independent k-vectors of Sec. 2.1).  Requests queue
- * in submission order; sail_server_step admits the head of the queue while a slot is free, the
+ * in submission order; each step admits the head of the queue while a slot is free, the
  * resident walkers stay within max_walkers and the request's workspace fits a free region of
  * d_workspace (first fit: the buffer size is the HBM admission cap), runs one block for every
  * resident problem through the batched sweep, and retires problems that reached their
  * target_chi2 (checked each block on the averaged spectrum) or their last sweep, keeping the
- * averaged spectrum on the host.  A request's result does not depend on which others share
- * the device (see the batch above). */
+ * averaged spectrum on the host.  A step admits only requests submitted before it began, so a
+ * request submitted while a block runs is admitted at the next block boundary.  A request's
+ * result does not depend on which others share the device (see the batch above).
+ *
+ * Steps are driven either by the caller (sail_server_step, blocking for one block) or by the
+ * server's own worker thread (sail_server_start ... sail_server_stop, completions collected
+ * with sail_server_poll).  Submission, polling, results and request information may be called
+ * from any thread at any time, also while a block runs; they never wait for the block. */
 typedef struct sail_server_ctx *sail_server_t;
+
+/* Life of one request, times in seconds on the server's steady clock (0 at creation), steps
+ * counted from 1 (a request submitted after step k began has submit_step = k). */
+typedef struct sail_request_info {
+    int state;              /* 0 queued, 1 resident, 2 completed, < 0 the error that refused it */
+    int converged;          /* completed: the target chi2 was reached */
+    int sweeps;             /* completed: sweeps run */
+    int n_used;             /* completed: walkers in the average */
+    long long submit_step;  /* steps begun when the request was submitted */
+    long long admit_step;   /* the step that admitted it (-1 while queued) */
+    long long done_step;    /* the step that retired it (-1 before) */
+    double t_submit, t_admit, t_done;   /* -1 until reached */
+    double chi2_of_mean;    /* completed: chi2 of the averaged spectrum */
+} sail_request_info;
 
 int sail_server_create(sail_server_t *out, int max_resident, long long max_walkers, int sweeps_per_block,
                        int resync_every, void *d_workspace, size_t ws_bytes, void *stream);
-/* Copies the request (host arrays and parameters; FP32, the server's periods); *id for its result. */
+/* Copies the request (host arrays and parameters; FP32, the server's periods); *id for its
+ * result.  Thread-safe; wakes the worker thread if it runs. */
 int sail_server_submit(sail_server_t s, const sail_problem *req, int *id);
-/* Admission, one block, retirement.  completed[max_completed] receives the ids retired in this
- * step (*n_completed of them); *n_active / *n_queued: resident and waiting requests after it. */
+/* Admission, one block, retirement, on the calling thread.  completed[max_completed] receives
+ * the ids retired in this step (*n_completed of them); *n_active / *n_queued: resident and
+ * waiting requests after it.  SAIL_ESTATE while the worker thread runs. */
 int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
                      int *n_queued);
+/* Starts the worker thread, which runs steps on the device current at this call while any
+ * request is queued or resident and sleeps otherwise.  SAIL_ESTATE if it already runs. */
+int sail_server_start(sail_server_t s);
+/* Ids retired by the worker since the last poll (up to max_completed, oldest first), and the
+ * resident / queued counts now.  Returns the worker's error (and stays in it) if a step failed. */
+int sail_server_poll(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
+                     int *n_queued);
+/* Stops the worker thread after the step it is running, if any. */
+int sail_server_stop(sail_server_t s);
 /* Result of a completed request: averaged spectrum and its standard error (host arrays of
  * n_omega, may be NULL), chi2 of the average, whether the target was reached, sweeps run. */
 int sail_server_result(sail_server_t s, int id, double *S_mean, double *S_err, double *chi2_of_mean, int *converged,
                        int *sweeps_done);
+int sail_server_request_info(sail_server_t s, int id, sail_request_info *info);
+/* Per-sweep accepted counts [n_sweeps][n_walkers], branching multipliers [n_events][n_walkers]
+ * and Deltas [n_events] of a completed request created with params.trace = 1, laid out as
+ * sail_get_trace's (n_sweeps = 0 without trace); any array may be NULL to query the counts. */
+int sail_server_trace(sail_server_t s, int id, int *acc, int *m, double *delta, int *n_sweeps, int *n_events);
+/* Stops the worker thread, then frees the server and its resident requests. */
 int sail_server_destroy(sail_server_t s);
 
 /* Frees the host side of the handle; the workspace stays the caller's. */

@@ -41,6 +41,7 @@ EXPORTS = [
     "sail_batch_workspace_size", "sail_batch_create", "sail_batch_anneal", "sail_batch_handle",
     "sail_batch_tuning", "sail_batch_destroy", "sail_server_create", "sail_server_submit", "sail_server_step",
     "sail_server_result", "sail_server_destroy", "sail_destroy", "sail_last_error",
+    "sail_server_start", "sail_server_poll", "sail_server_stop", "sail_server_request_info", "sail_server_trace",
 ]
 
 
@@ -58,6 +59,7 @@ class CParams(ctypes.Structure):
         ("adaptive_branching", ctypes.c_int), ("cool_begin", ctypes.c_double), ("freeze_begin", ctypes.c_double),
         ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("hastings", ctypes.c_int),
         ("walk_uniform", ctypes.c_double), ("shared_bins", ctypes.c_int), ("sweep_loop", ctypes.c_int),
+        ("T_start_abs", ctypes.c_double),
     ]
 
 
@@ -66,6 +68,15 @@ class CProblem(ctypes.Structure):
         ("tau", ctypes.POINTER(ctypes.c_double)), ("F", ctypes.POINTER(ctypes.c_double)),
         ("sigma", ctypes.POINTER(ctypes.c_double)), ("n_tau", ctypes.c_int),
         ("omega", ctypes.POINTER(ctypes.c_double)), ("n_omega", ctypes.c_int), ("params", CParams),
+    ]
+
+
+class CRequestInfo(ctypes.Structure):
+    _fields_ = [
+        ("state", ctypes.c_int), ("converged", ctypes.c_int), ("sweeps", ctypes.c_int), ("n_used", ctypes.c_int),
+        ("submit_step", ctypes.c_longlong), ("admit_step", ctypes.c_longlong), ("done_step", ctypes.c_longlong),
+        ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+        ("chi2_of_mean", ctypes.c_double),
     ]
 
 
@@ -142,6 +153,11 @@ def load(path: str = LIB_PATH):
     L.sail_server_step.argtypes = [vp, _ip, ctypes.c_int, _ip, _ip, _ip]
     L.sail_server_result.argtypes = [vp, ctypes.c_int, _dp, _dp, _dp, _ip, _ip]
     L.sail_server_destroy.argtypes = [vp]
+    L.sail_server_start.argtypes = [vp]
+    L.sail_server_poll.argtypes = [vp, _ip, ctypes.c_int, _ip, _ip, _ip]
+    L.sail_server_stop.argtypes = [vp]
+    L.sail_server_request_info.argtypes = [vp, ctypes.c_int, ctypes.POINTER(CRequestInfo)]
+    L.sail_server_trace.argtypes = [vp, ctypes.c_int, _ip, _ip, _dp, _ip, _ip]
     L.sail_destroy.argtypes = [vp]
     L.sail_last_error.argtypes = []
     L.sail_last_error.restype = ctypes.c_char_p
@@ -210,6 +226,7 @@ class Params:
     hastings: bool = False
     shared_bins: int = 0
     sweep_loop: int = 0
+    T_start_abs: float = 0.0
 
     def c(self) -> CParams:
         p = CParams()
@@ -446,6 +463,41 @@ class Server:
         _check(self.lib.sail_server_step(self._s, buf, self.max_resident, ctypes.byref(nc), ctypes.byref(na),
                                          ctypes.byref(nq)))
         return [buf[i] for i in range(min(nc.value, self.max_resident))], na.value, nq.value
+
+    def start(self):
+        """Hands the steps to the server's worker thread (poll() then reports completions)."""
+        _check(self.lib.sail_server_start(self._s))
+
+    def stop(self):
+        _check(self.lib.sail_server_stop(self._s))
+
+    def poll(self):
+        """Ids the worker retired since the last poll: (completed ids, active, queued)."""
+        buf = (ctypes.c_int * self.max_resident)()
+        nc, na, nq = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        out = []
+        while True:
+            _check(self.lib.sail_server_poll(self._s, buf, self.max_resident, ctypes.byref(nc), ctypes.byref(na),
+                                             ctypes.byref(nq)))
+            out += [buf[i] for i in range(nc.value)]
+            if nc.value < self.max_resident:
+                return out, na.value, nq.value
+
+    def request_info(self, rid: int) -> dict:
+        ci = CRequestInfo()
+        _check(self.lib.sail_server_request_info(self._s, int(rid), ctypes.byref(ci)))
+        return {f[0]: getattr(ci, f[0]) for f in CRequestInfo._fields_}
+
+    def trace(self, rid: int, n_walkers: int):
+        """(accepted counts [sweeps, walkers], multipliers [events, walkers], Deltas) of a
+        completed request created with trace=True."""
+        ns, ne = ctypes.c_int(0), ctypes.c_int(0)
+        _check(self.lib.sail_server_trace(self._s, int(rid), None, None, None, ctypes.byref(ns), ctypes.byref(ne)))
+        acc = np.zeros((ns.value, n_walkers), dtype=np.int32)
+        m = np.zeros((ne.value, n_walkers), dtype=np.int32)
+        d = np.zeros(ne.value)
+        _check(self.lib.sail_server_trace(self._s, int(rid), _ptr(acc, _ip), _ptr(m, _ip), _ptr(d), None, None))
+        return acc, m, d
 
     def result(self, rid: int):
         n = self.n_omega[rid]

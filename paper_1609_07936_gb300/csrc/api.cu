@@ -3,12 +3,16 @@
 // imprinted branching -> statistics).  Compiled with -ffp-contract=off: host arithmetic
 // rounds every product and sum on its own.
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/sail.h"
@@ -55,6 +59,9 @@ int cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr double kPi = 3.14159265358979323846;
+// largest weighted model term (max Khat_ij * A) and weighted datum an FP32 state accepts: their
+// squares summed over 512 tau points stay below 1e33, far inside FP32's range
+constexpr double kFp32TermMax = 1e15;
 
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -151,6 +158,8 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->T_start > 0) || !(p->T_end > 0) || !std::isfinite(p->T_start) || !std::isfinite(p->T_end))
         return fail(SAIL_EINVAL, "temperatures must be finite and > 0");
     if (!(p->T_end_abs >= 0) || !std::isfinite(p->T_end_abs)) return fail(SAIL_EINVAL, "T_end_abs must be finite, >= 0");
+    if (!(p->T_start_abs >= 0) || !std::isfinite(p->T_start_abs))
+        return fail(SAIL_EINVAL, "T_start_abs must be finite, >= 0");
     if (!(p->branch_fraction >= 0 && p->branch_fraction < 1)) return fail(SAIL_EINVAL, "branch_fraction must be in [0, 1)");
     if (!(p->imprint_t >= 0 && p->imprint_t <= 1)) return fail(SAIL_EINVAL, "imprint_t must be in [0, 1]");
     if (!(p->y_p > 0 && p->y_p <= 1) || !(p->y_m >= 1) || !(p->y_min > 0 && p->y_min <= 1))
@@ -158,7 +167,7 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->move_scale < 1) || std::isnan(p->move_scale)) return fail(SAIL_EINVAL, "move_scale must be < 1");
     if (!std::isfinite(p->B)) return fail(SAIL_EINVAL, "B must be given (Sec. 2.2)");
     if (!(p->avg_chi2_factor >= 1)) return fail(SAIL_EINVAL, "avg_chi2_factor must be >= 1");
-    if (p->resync_kind < 0 || p->resync_kind > 2) return fail(SAIL_EINVAL, "resync_kind must be 0, 1 or 2");
+    if (p->resync_kind < 0 || p->resync_kind > 3) return fail(SAIL_EINVAL, "resync_kind must be 0, 1, 2 or 3");
     if (p->sweep_lanes != 0 && p->sweep_lanes != 8 && p->sweep_lanes != 16)
         return fail(SAIL_EINVAL, "sweep_lanes must be 0, 8 or 16");
     if (p->sweep_lanes == 8 && n_tau > 256) return fail(SAIL_EINVAL, "sweep_lanes = 8 needs n_tau <= 256");
@@ -368,6 +377,17 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         F32[i] = (float)F64[i];
     }
     for (int j = 0; j < n_omega; ++j) beta[j] = (float)(B - A * omega[j]);
+    if (p->precision == SAIL_PREC_FP32) {
+        // FP32 state: a single term Khat_ij a_j of the model is at most max Khat * A, and a move's
+        // residual change and its square summed over tau must stay inside FP32's range (3.4e38)
+        double kmax = 0.0, fmax = 0.0;
+        for (size_t q = 0; q < NO * PAD; ++q) kmax = std::max(kmax, K64[q]);
+        for (int i = 0; i < n_tau; ++i) fmax = std::max(fmax, std::fabs(F64[i]));
+        if (!(kmax * A <= kFp32TermMax) || !(fmax <= kFp32TermMax))
+            return fail(SAIL_EINVAL, "weighted data too large for FP32 state: max Khat * A = %g, max |F / sigma| = %g "
+                                     "(limit %g; sigma too small for the kernel's range, use FP64)",
+                        kmax * A, fmax, kFp32TermMax);
+    }
     // FP32 sweep tables: Khat_{i,32h+l} = Khat_{i,32h} q_i^l (Eq. efficient-correlation-model)
     const int NH = (n_omega + 31) / 32;
     std::vector<float> Qhi((size_t)NH * PAD, 0.0f), Qlo((size_t)32 * PAD, 0.0f), rgap(NO, 0.0f);
@@ -424,13 +444,14 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     // self-cooling one at chi2_0 (later blocks are set as the anneal reaches them)
     std::vector<double> T(p->n_sweeps);
     const double T_end_rel = p->T_end_abs > 0 ? p->T_end_abs / chi2_0 : p->T_end;
+    const double T_start_rel = p->T_start_abs > 0 ? p->T_start_abs / chi2_0 : p->T_start;
     for (int n = 0; n < p->n_sweeps; ++n) {
         if (p->schedule_kind == SAIL_SCHEDULE_SELF_COOLING) {
             T[n] = n < p->sweeps_per_block ? chi2_0 : NAN;
             continue;
         }
         const double t = p->n_sweeps > 1 ? (double)n / (double)(p->n_sweeps - 1) : 0.0;
-        T[n] = chi2_0 * (p->T_start * std::pow(T_end_rel / p->T_start, t));
+        T[n] = chi2_0 * (T_start_rel * std::pow(T_end_rel / T_start_rel, t));
     }
 
     sail_ctx *h = new sail_ctx();
@@ -1250,7 +1271,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 sail_batch_ctx::TcTune *tt = nullptr;
                 for (auto &t : b->tc)
                     if (t.pad == h->pad) tt = &t;
-                if (tt && h->prm.resync_kind >= 1) {
+                if (tt && (h->prm.resync_kind == 1 || h->prm.resync_kind == 2)) {
                     if (tt->next < tt->n_cand) {
                         h->P.tc_cols = tt->cand[tt->next];
                         cudaEventCreate(&t0);
@@ -1340,7 +1361,11 @@ int sail_batch_anneal(sail_batch_t b, int max_blocks, int *n_done) {
 // admitted while its workspace fits a free region of the server's device buffer (first fit;
 // the buffer size is the admission cap) and a slot is free, one block runs for every resident
 // problem through the batched sweep, and problems that reached their target chi2 or the end
-// of their schedule leave, their averaged spectrum kept on the host.
+// of their schedule leave, their averaged spectrum kept on the host.  A step admits only
+// requests submitted before it began, so a request that arrives while a block runs joins at
+// the next block boundary.  Steps are driven either by the caller (sail_server_step) or by a
+// worker thread of the server (sail_server_start): submission, polling and results take a
+// mutex that the block itself does not hold, so they never wait for a block to finish.
 struct sail_server_ctx {
     sail_batch_ctx batch;              // slots: batch.h[k] == nullptr when free
     std::vector<size_t> slot_off, slot_size;
@@ -1358,17 +1383,33 @@ struct sail_server_ctx {
     };
     std::deque<Request> queue;
     struct Result {
-        bool done;
-        int converged, sweeps;
-        double chi2_mean;
-        int n_used;
+        sail_request_info info;
         std::vector<double> mean, err;
-        int n_omega;
+        std::vector<int> acc_trace, m_trace;
+        std::vector<double> delta_trace;
+        int n_omega, trace_sweeps, trace_events;
     };
     std::vector<Result> results;
+    // concurrency: mu guards queue, results, completions and the counters below; step_mu makes
+    // steps one at a time (the slots, regions and the batch belong to the step that holds it)
+    std::mutex mu, step_mu;
+    std::condition_variable cv;
+    std::thread worker;
+    bool worker_on = false, stop = false;
+    std::deque<int> completions;       // ids retired by the worker and not yet polled
+    int worker_rc = SAIL_OK;
+    std::string worker_err;
+    long long steps_started = 0;
+    int n_resident = 0;
+    int device = 0;
+    std::chrono::steady_clock::time_point t0;
 };
 
 namespace {
+
+double server_clock(const sail_server_ctx *s) {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
+}
 
 bool region_take(sail_server_ctx *s, size_t bytes, size_t *off) {
     for (size_t r = 0; r < s->free_regions.size(); ++r) {
@@ -1398,6 +1439,160 @@ void region_give(sail_server_ctx *s, size_t off, size_t bytes) {
         F[r - 1].size += F[r].size;
         F.erase(F.begin() + (long)r);
     }
+}
+
+// One admission / block / retirement round; the caller holds step_mu.  Retired ids go to
+// completed[] (up to max_completed) and, when to_poll, to the poll queue.
+int server_step(sail_server_t s, int *completed, int max_completed, int *n_completed, bool to_poll) {
+    sail_batch_ctx &b = s->batch;
+    const int slots = (int)b.h.size();
+    long long k;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        k = ++s->steps_started;
+    }
+    // admission: the head of the queue while it fits (FIFO order), requests submitted before
+    // this step began only
+    for (;;) {
+        sail_server_ctx::Request r;
+        int slot = -1;
+        size_t off = 0;
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->queue.empty()) break;
+            const sail_server_ctx::Request &f = s->queue.front();
+            if (s->results[f.id].info.submit_step >= k) break;
+            for (int q = 0; q < slots && slot < 0; ++q)
+                if (!b.h[q]) slot = q;
+            const long long pairs = (f.params.n_walkers + 1) / 2;
+            if (slot < 0 || s->resident_pairs + pairs > s->max_pairs || !region_take(s, f.bytes, &off)) break;
+            r = std::move(s->queue.front());
+            s->queue.pop_front();
+        }
+        sail_t h = nullptr;
+        const int rc = sail_create(&h, r.tau.data(), r.F.data(), r.sigma.data(), (int)r.tau.size(), r.omega.data(),
+                                   (int)r.omega.size(), &r.params, b.ws + off, r.bytes, b.stream);
+        if (rc) {
+            region_give(s, off, r.bytes);
+            std::lock_guard<std::mutex> lk(s->mu);
+            auto &res = s->results[r.id].info;
+            res.state = rc;
+            res.done_step = k;
+            res.t_done = server_clock(s);
+            if (to_poll) s->completions.push_back(r.id);
+            return rc;
+        }
+        b.h[slot] = h;
+        size_t &sm = b.smem[batch_class(h->P)];
+        sm = std::max(sm, sweep_fp32_table_bytes(h->P));
+        s->slot_off[slot] = off;
+        s->slot_size[slot] = r.bytes;
+        s->slot_id[slot] = r.id;
+        s->resident_pairs += (r.params.n_walkers + 1) / 2;
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto &res = s->results[r.id].info;
+        res.state = 1;
+        res.admit_step = k;
+        res.t_admit = server_clock(s);
+        s->n_resident += 1;
+    }
+    int active = 0;
+    for (int q = 0; q < slots; ++q) active += b.h[q] != nullptr;
+    if (active > 0) {
+        const int rc = batch_run_blocks(&b, 1, nullptr);
+        if (rc) return rc;
+    }
+    // retirement
+    int nc = 0;
+    for (int q = 0; q < slots; ++q) {
+        sail_ctx *h = b.h[q];
+        if (!h || handle_active(h)) continue;
+        const int id = s->slot_id[q];
+        std::vector<double> mean(h->n_omega, 0.0), err(h->n_omega, 0.0);
+        int n_used = 0;
+        double c2 = 0.0;
+        int rc = average_to_host(h, mean.data(), err.data(), &n_used, &c2);
+        if (rc) return rc;
+        std::vector<int> acc, m;
+        std::vector<double> dl;
+        int n_ev = 0;
+        if (h->prm.trace) {
+            acc.resize((size_t)h->sweeps_done * h->prm.n_walkers);
+            m.resize((size_t)h->events * h->prm.n_walkers);
+            dl.resize((size_t)h->events);
+            rc = sail_get_trace(h, acc.data(), m.data(), dl.data(), &n_ev);
+            if (rc) return rc;
+        }
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            auto &res = s->results[id];
+            res.mean = std::move(mean);
+            res.err = std::move(err);
+            res.acc_trace = std::move(acc);
+            res.m_trace = std::move(m);
+            res.delta_trace = std::move(dl);
+            res.trace_sweeps = h->prm.trace ? h->sweeps_done : 0;
+            res.trace_events = n_ev;
+            res.info.n_used = n_used;
+            res.info.chi2_of_mean = c2;
+            res.info.converged = h->converged ? 1 : 0;
+            res.info.sweeps = h->sweeps_done;
+            res.info.done_step = k;
+            res.info.t_done = server_clock(s);
+            res.info.state = 2;
+            s->n_resident -= 1;
+            if (to_poll) s->completions.push_back(id);
+        }
+        if (completed && nc < max_completed) completed[nc] = id;
+        ++nc;
+        s->resident_pairs -= (h->prm.n_walkers + 1) / 2;
+        sail_destroy(h);
+        b.h[q] = nullptr;
+        region_give(s, s->slot_off[q], s->slot_size[q]);
+        s->slot_id[q] = -1;
+    }
+    if (n_completed) *n_completed = nc;
+    return SAIL_OK;
+}
+
+void server_counts(sail_server_t s, int *n_active, int *n_queued) {
+    if (n_active) *n_active = s->n_resident;
+    if (n_queued) *n_queued = (int)s->queue.size();
+}
+
+void server_worker(sail_server_t s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [s] { return s->stop || !s->queue.empty() || s->n_resident > 0; });
+            if (s->stop) return;
+        }
+        int rc;
+        {
+            std::lock_guard<std::mutex> lk(s->step_mu);
+            rc = server_step(s, nullptr, 0, nullptr, true);
+        }
+        if (rc) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->worker_rc = rc;
+            s->worker_err = g_err;
+            return;
+        }
+    }
+}
+
+void server_stop_worker(sail_server_t s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (!s->worker_on) return;
+        s->stop = true;
+    }
+    s->cv.notify_all();
+    s->worker.join();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->worker_on = false;
+    s->stop = false;
 }
 
 }  // namespace
@@ -1438,6 +1633,9 @@ int sail_server_create(sail_server_t *out, int max_resident, long long max_walke
     s->sweeps_per_block = sweeps_per_block;
     s->resync_every = resync_every;
     s->max_pairs = max_walkers / 2;
+    s->resident_pairs = 0;
+    cudaGetDevice(&s->device);
+    s->t0 = std::chrono::steady_clock::now();
     *out = s;
     return SAIL_OK;
 }
@@ -1455,104 +1653,124 @@ int sail_server_submit(sail_server_t s, const sail_problem *req, int *id) {
     if ((p.n_walkers + 1) / 2 > s->max_pairs) return fail(SAIL_EINVAL, "request has more walkers than the server holds");
     if (align_up(bytes) > s->batch.ws_bytes - s->data_begin) return fail(SAIL_ENOMEM, "request larger than the server");
     sail_server_ctx::Request r;
-    r.id = (int)s->results.size();
-    *id = r.id;
     r.tau.assign(req->tau, req->tau + req->n_tau);
     r.F.assign(req->F, req->F + req->n_tau);
     r.sigma.assign(req->sigma, req->sigma + req->n_tau);
     r.omega.assign(req->omega, req->omega + req->n_omega);
     r.params = p;
     r.bytes = align_up(bytes);
-    s->queue.push_back(std::move(r));
-    sail_server_ctx::Result res{};
-    res.done = false;
-    res.n_omega = req->n_omega;
-    s->results.push_back(res);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        r.id = (int)s->results.size();
+        *id = r.id;
+        sail_server_ctx::Result res{};
+        res.n_omega = req->n_omega;
+        res.info.state = 0;
+        res.info.submit_step = s->steps_started;
+        res.info.admit_step = -1;
+        res.info.done_step = -1;
+        res.info.t_submit = server_clock(s);
+        res.info.t_admit = -1.0;
+        res.info.t_done = -1.0;
+        s->results.push_back(std::move(res));
+        s->queue.push_back(std::move(r));
+    }
+    s->cv.notify_one();
     return SAIL_OK;
 }
 
 int sail_server_step(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
                      int *n_queued) {
     if (!s) return fail(SAIL_EINVAL, "NULL server");
-    sail_batch_ctx &b = s->batch;
-    const int slots = (int)b.h.size();
-    // admission: the head of the queue while it fits (FIFO order)
-    while (!s->queue.empty()) {
-        auto &r = s->queue.front();
-        int slot = -1;
-        for (int k = 0; k < slots && slot < 0; ++k)
-            if (!b.h[k]) slot = k;
-        const long long pairs = (r.params.n_walkers + 1) / 2;
-        size_t off = 0;
-        if (slot < 0 || s->resident_pairs + pairs > s->max_pairs || !region_take(s, r.bytes, &off)) break;
-        sail_t h = nullptr;
-        const int rc = sail_create(&h, r.tau.data(), r.F.data(), r.sigma.data(), (int)r.tau.size(), r.omega.data(),
-                                   (int)r.omega.size(), &r.params, b.ws + off, r.bytes, b.stream);
-        if (rc) {
-            region_give(s, off, r.bytes);
-            return rc;
-        }
-        b.h[slot] = h;
-        size_t &sm = b.smem[batch_class(h->P)];
-        sm = std::max(sm, sweep_fp32_table_bytes(h->P));
-        s->slot_off[slot] = off;
-        s->slot_size[slot] = r.bytes;
-        s->slot_id[slot] = r.id;
-        s->resident_pairs += pairs;
-        s->queue.pop_front();
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->worker_on) return fail(SAIL_ESTATE, "the server's worker thread drives the steps");
     }
-    int active = 0;
-    for (int k = 0; k < slots; ++k) active += b.h[k] != nullptr;
-    if (active > 0) {
-        const int rc = batch_run_blocks(&b, 1, nullptr);
-        if (rc) return rc;
+    int rc;
+    {
+        std::lock_guard<std::mutex> lk(s->step_mu);
+        rc = server_step(s, completed, max_completed, n_completed, false);
     }
-    // retirement
+    std::lock_guard<std::mutex> lk(s->mu);
+    server_counts(s, n_active, n_queued);
+    return rc;
+}
+
+int sail_server_start(sail_server_t s) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->worker_on) return fail(SAIL_ESTATE, "the worker thread is already running");
+    if (s->worker_rc) return fail(s->worker_rc, "the worker thread stopped on an error: %s", s->worker_err.c_str());
+    cudaGetDevice(&s->device);
+    s->stop = false;
+    s->worker_on = true;
+    s->worker = std::thread(server_worker, s);
+    return SAIL_OK;
+}
+
+int sail_server_poll(sail_server_t s, int *completed, int max_completed, int *n_completed, int *n_active,
+                     int *n_queued) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    if (max_completed < 0 || (max_completed > 0 && !completed)) return fail(SAIL_EINVAL, "bad completion buffer");
+    std::lock_guard<std::mutex> lk(s->mu);
     int nc = 0;
-    for (int k = 0; k < slots; ++k) {
-        sail_ctx *h = b.h[k];
-        if (!h || handle_active(h)) continue;
-        auto &res = s->results[s->slot_id[k]];
-        res.mean.assign(h->n_omega, 0.0);
-        res.err.assign(h->n_omega, 0.0);
-        const int rc = average_to_host(h, res.mean.data(), res.err.data(), &res.n_used, &res.chi2_mean);
-        if (rc) return rc;
-        res.converged = h->converged ? 1 : 0;
-        res.sweeps = h->sweeps_done;
-        res.done = true;
-        if (completed && nc < max_completed) completed[nc] = s->slot_id[k];
-        ++nc;
-        s->resident_pairs -= (h->prm.n_walkers + 1) / 2;
-        sail_destroy(h);
-        b.h[k] = nullptr;
-        region_give(s, s->slot_off[k], s->slot_size[k]);
-        s->slot_id[k] = -1;
+    while (nc < max_completed && !s->completions.empty()) {
+        completed[nc++] = s->completions.front();
+        s->completions.pop_front();
     }
     if (n_completed) *n_completed = nc;
-    if (n_active) {
-        int a = 0;
-        for (int k = 0; k < slots; ++k) a += b.h[k] != nullptr;
-        *n_active = a;
-    }
-    if (n_queued) *n_queued = (int)s->queue.size();
+    server_counts(s, n_active, n_queued);
+    if (s->worker_rc) return fail(s->worker_rc, "the worker thread stopped on an error: %s", s->worker_err.c_str());
+    return SAIL_OK;
+}
+
+int sail_server_stop(sail_server_t s) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    server_stop_worker(s);
     return SAIL_OK;
 }
 
 int sail_server_result(sail_server_t s, int id, double *S_mean, double *S_err, double *chi2_of_mean, int *converged,
                        int *sweeps_done) {
-    if (!s || id < 0 || id >= (int)s->results.size()) return fail(SAIL_EINVAL, "unknown request id");
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id < 0 || id >= (int)s->results.size()) return fail(SAIL_EINVAL, "unknown request id");
     const auto &r = s->results[id];
-    if (!r.done) return fail(SAIL_ESTATE, "request %d has not completed", id);
+    if (r.info.state < 0) return fail(r.info.state, "request %d failed at admission", id);
+    if (r.info.state != 2) return fail(SAIL_ESTATE, "request %d has not completed", id);
     if (S_mean) std::memcpy(S_mean, r.mean.data(), r.mean.size() * 8);
     if (S_err) std::memcpy(S_err, r.err.data(), r.err.size() * 8);
-    if (chi2_of_mean) *chi2_of_mean = r.chi2_mean;
-    if (converged) *converged = r.converged;
-    if (sweeps_done) *sweeps_done = r.sweeps;
+    if (chi2_of_mean) *chi2_of_mean = r.info.chi2_of_mean;
+    if (converged) *converged = r.info.converged;
+    if (sweeps_done) *sweeps_done = r.info.sweeps;
+    return SAIL_OK;
+}
+
+int sail_server_request_info(sail_server_t s, int id, sail_request_info *info) {
+    if (!s || !info) return fail(SAIL_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id < 0 || id >= (int)s->results.size()) return fail(SAIL_EINVAL, "unknown request id");
+    *info = s->results[id].info;
+    return SAIL_OK;
+}
+
+int sail_server_trace(sail_server_t s, int id, int *acc, int *m, double *delta, int *n_sweeps, int *n_events) {
+    if (!s) return fail(SAIL_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (id < 0 || id >= (int)s->results.size()) return fail(SAIL_EINVAL, "unknown request id");
+    const auto &r = s->results[id];
+    if (r.info.state != 2) return fail(SAIL_ESTATE, "request %d has not completed", id);
+    if (n_sweeps) *n_sweeps = r.trace_sweeps;
+    if (n_events) *n_events = r.trace_events;
+    if (acc && !r.acc_trace.empty()) std::memcpy(acc, r.acc_trace.data(), r.acc_trace.size() * 4);
+    if (m && !r.m_trace.empty()) std::memcpy(m, r.m_trace.data(), r.m_trace.size() * 4);
+    if (delta && !r.delta_trace.empty()) std::memcpy(delta, r.delta_trace.data(), r.delta_trace.size() * 8);
     return SAIL_OK;
 }
 
 int sail_server_destroy(sail_server_t s) {
     if (!s) return fail(SAIL_EINVAL, "NULL server");
+    server_stop_worker(s);
     cudaStreamSynchronize(s->batch.stream);
     for (sail_t h : s->batch.h)
         if (h) sail_destroy(h);

@@ -922,6 +922,10 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
+    if (kind == 3) {                  // FP64 GEMM
+        *launches += 1;
+        return launch_resync_fp64(P, S, st);
+    }
     *launches += kind >= 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
     return kind >= 1 ? launch_resync_tc(P, S, status, kind == 2, st) : launch_resync_fp32(P, S, st);
 }

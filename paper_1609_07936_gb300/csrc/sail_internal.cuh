@@ -110,6 +110,7 @@ cudaError_t launch_sweep_hastings(const DevProblem &P, const DevState &S, int sw
 // restoration (restore != 0), then the tiled GEMM of resync_fp32.cu or the tensor cores.
 cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision, int restore, int kind,
                           int *status, cudaStream_t st, int *launches);
+cudaError_t launch_resync_fp64(const DevProblem &P, const DevState &S, cudaStream_t st);
 cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStream_t st);
 // Tensor-core (tcgen05) residual recomputation for FP32 state, TF32 with a three-term split or
 // (bf16) BF16 with three pieces and six products; status[0] <- 1 on a timed-out wait.

@@ -22,7 +22,7 @@ def test_reference_arm_prints_the_contract_line():
     lines = _run({"RANK": "0", "WORLD_SIZE": "1"})
     assert len(lines) == 1
     d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["metric"] == "walker-moves/sec" and d["unit"] == "walker-moves/s"
+    assert d["impl"] == "reference" and d["metric"] == "walker-moves/s" and d["unit"] == "walker-moves/s"
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 3
     assert d["n_gpus"] == 1 and d["dtype"] == "f64" and d["data"] == "synthetic"
     assert "paper_scale_double_lorentz" in d["config"]["workload"]
@@ -31,7 +31,9 @@ def test_reference_arm_prints_the_contract_line():
     assert "of the 4096 walkers, 3 untimed + 2 timed blocks" in cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "walker-moves/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    # the step time is that of the blocks actually run; the scaling to all walkers is separate
     assert d["ms_per_step"] > 0
+    assert d["ms_per_step_scaled"]["value"] > d["ms_per_step"]
 
 
 def test_reference_arm_prints_nothing_on_other_ranks():

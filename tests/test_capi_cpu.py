@@ -53,7 +53,8 @@ def _c_layout(struct, fields):
 
 
 @pytest.mark.parametrize("struct,cls", [("sail_params", "CParams"), ("sail_block_stats", "CBlockStats"),
-                                        ("sail_info", "CInfo"), ("sail_problem", "CProblem")])
+                                        ("sail_info", "CInfo"), ("sail_problem", "CProblem"),
+                                        ("sail_request_info", "CRequestInfo")])
 def test_struct_layouts_match_the_header(struct, cls):
     """Every ctypes mirror has the C compiler's size and field offsets."""
     C = getattr(_capi, cls)

@@ -3,7 +3,8 @@
 All paths compute R = Fhat - Khat a and chi2 = sum R^2 for every walker: the FP32-FMA GEMM
 with FP64 sums over 32-bin chunks (resync_kind 0), the tcgen05 tensor-core GEMM in TF32
 with a three-term operand split and an FP32 tensor-memory accumulator (resync_kind 1), and
-the same in BF16 with three pieces per operand and six products (resync_kind 2).
+the same in BF16 with three pieces per operand and six products (resync_kind 2), and the
+plain FP64-FMA GEMM (resync_kind 3, the comparison path).
 The error bound per element is relative to the model value m_i = sum_j Khat_ij a_j (all
 terms are positive): 2e-6 m_i covers the FP32 accumulation of ~1000 terms and the ~2^-21
 operand precision of the split, plus the FP32 storage of R (6e-8 |R_i|).
@@ -18,7 +19,7 @@ from workloads import paper_scale_double_lorentz, precision_random_peaks, tiny_d
 pytestmark = pytest.mark.gpu
 
 
-def _check(P, W, kind, seed):
+def _check(P, W, kind, seed, rel=2e-6):
     rng = np.random.default_rng(seed)
     K, Fh, _ = O.tables(P.tau, P.F, P.sigma, P.omega)
     a0, _ = O.initial_spectrum(P.omega, P.A, P.B)
@@ -34,7 +35,7 @@ def _check(P, W, kind, seed):
     for w in range(W):
         model = K @ a32[w]
         R_ref = Fh - model
-        tol = 2e-6 * model + 6e-8 * np.abs(R_ref) + 1e-6
+        tol = rel * model + 6e-8 * np.abs(R_ref) + 1e-6
         assert np.all(np.abs(R[w] - R_ref) <= tol), (w, np.max(np.abs(R[w] - R_ref) / tol))
         c2 = np.sum(R_ref ** 2)
         assert abs(chi2[w] - c2) <= 2 * np.sum(np.abs(R_ref) * tol) + 1e-9 * c2
@@ -75,3 +76,12 @@ def test_anneal_with_tensor_core_resync():
     # the two paths see the same statistics to within the rounding-driven divergence of chains
     assert abs(out[0][0][-1]["acceptance"] - out[1][0][-1]["acceptance"]) < 0.02
     assert abs(out[0][0][-1]["acceptance"] - out[2][0][-1]["acceptance"]) < 0.02
+
+
+def test_fp64_resync_of_fp32_state():
+    """resync_kind 3 multiplies and sums in FP64: only the FP32 storage of R and FP64 rounding
+    (order of 1e-16 per term over 1000-2048 terms) remain, on the paper grid, the tiny grid and
+    the 512 x 2048 grid with ragged walker counts."""
+    _check(paper_scale_double_lorentz(1e-4, n_walkers=300), 300, 3, 1, rel=1e-12)
+    _check(tiny_double_lorentz(), 70, 3, 2, rel=1e-12)
+    _check(precision_random_peaks(3, n_walkers=130), 130, 3, 3, rel=1e-12)

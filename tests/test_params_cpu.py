@@ -16,7 +16,7 @@ BAD = [
     ("branch_fraction", 1.0, "branch_fraction"), ("imprint_t", 1.5, "imprint_t"),
     ("y_p", 0.0, "amplitude"), ("y_m", 0.5, "amplitude"), ("y_min", 0.0, "amplitude"),
     ("move_scale", 1.0, "move_scale"), ("avg_chi2_factor", 0.9, "avg_chi2_factor"),
-    ("resync_kind", 3, "resync_kind"), ("sweep_lanes", 4, "sweep_lanes"), ("schedule_kind", 2, "schedule_kind"),
+    ("resync_kind", 4, "resync_kind"), ("T_start_abs", -1.0, "T_start_abs"), ("sweep_lanes", 4, "sweep_lanes"), ("schedule_kind", 2, "schedule_kind"),
     ("adaptive_branching", 2, "adaptive_branching"), ("cool_begin", math.nan, "cool_begin"),
     ("smooth_s", 0.5, "smooth_s"), ("index_walk_len", 8, "index_walk_len"), ("walk_uniform", 1.5, "walk_uniform"),
     ("hastings", 2, "hastings"), ("shared_bins", 3, "shared_bins"), ("sweep_loop", 3, "sweep_loop"),

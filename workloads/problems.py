@@ -9,7 +9,8 @@ Readings fixed here (the paper does not state them):
     (Sec. 2.1 sets S = 0 above w_max = N_w * dw; a Lorentzian's first moment
     diverges without the upper cut);
   * sigma_i = level * F_exact(tau_i) and F_i = F_exact(tau_i) + sigma_i * z_i
-    with z_i independent standard normals;
+    with z_i independent standard normals (the random recipes hold sigma constant
+    where F_exact falls below 1e-8 of its largest value, RANDOM_NOISE_FLOOR);
   * A = int_0^W S dw / dw and B = int_0^W w S dw / dw, the sum constants of
     Sec. 2.2 evaluated on the true spectrum;
   * omega is passed as the bin centres x_j = (j + 1/2) dw.
@@ -53,18 +54,19 @@ class Problem:
 
 
 def make_problem(name: str, tau: np.ndarray, n_omega: int, W: float, peaks: List[Peak],
-                 noise_level: float, seed: int, n_walkers: int) -> Problem:
+                 noise_level: float, seed: int, n_walkers: int, noise_floor: float = 0.0) -> Problem:
+    """sigma_i = noise_level * max(F_exact(tau_i), noise_floor * max_k F_exact(tau_k))."""
     tau = np.asarray(tau, dtype=np.float64)
     omega = (np.arange(n_omega, dtype=np.float64) + 0.5) * (W / n_omega)
     F_exact = laplace(peaks, W, tau)
-    sigma = noise_level * F_exact
+    sigma = noise_level * np.maximum(F_exact, noise_floor * F_exact.max())
     z = np.random.default_rng(seed).standard_normal(tau.size)
     F = F_exact + sigma * z
     dw = W / n_omega
     return Problem(name=name, tau=tau, F=F, sigma=sigma, omega=omega,
                    A=mass(peaks, W) / dw, B=first_moment(peaks, W) / dw, W=W,
                    peaks=list(peaks), F_exact=F_exact, n_walkers=n_walkers,
-                   extra={"noise_level": noise_level, "seed": seed})
+                   extra={"noise_level": noise_level, "seed": seed, "noise_floor": noise_floor})
 
 
 def _double_lorentz() -> List[Peak]:
@@ -99,6 +101,13 @@ def random_peaks(rng: np.random.Generator) -> List[Peak]:
     return [Peak(kd, float(c), float(w), float(a)) for kd, c, w, a in zip(kinds, centres, widths, weights)]
 
 
+# Random peaks reach omega = 15 on tau in [0, 8], where F(8) / F(0) falls to 1e-40: a purely
+# relative sigma would then weight the kernel's low-frequency columns by up to 1e43, past the
+# range of an FP32 state.  The random recipes keep the noise relative down to 1e-8 of F's
+# largest value and constant below it (reading of "noise sigma = level * F").
+RANDOM_NOISE_FLOOR = 1e-8
+
+
 def precision_random_peaks(seed: int = 0, n_tau: int = 512, n_omega: int = 2048,
                            n_walkers: int = 16384, noise_level: float = 1e-4) -> Problem:
     """512 tau points on [0, 8], 2048 bins on [0, 20], 1-4 random peaks."""
@@ -106,7 +115,7 @@ def precision_random_peaks(seed: int = 0, n_tau: int = 512, n_omega: int = 2048,
     peaks = random_peaks(rng)
     tau = 8.0 * np.arange(n_tau, dtype=np.float64) / (n_tau - 1)
     return make_problem(f"precision_random_peaks_{seed}", tau, n_omega, 20.0, peaks,
-                        noise_level, seed + 1, n_walkers)
+                        noise_level, seed + 1, n_walkers, noise_floor=RANDOM_NOISE_FLOOR)
 
 
 def random_batch_problem(index: int, seed: int = 0, rng: Optional[np.random.Generator] = None,
@@ -122,7 +131,7 @@ def random_batch_problem(index: int, seed: int = 0, rng: Optional[np.random.Gene
     peaks = random_peaks(rng)
     tau = 8.0 * np.arange(n_tau, dtype=np.float64) / (n_tau - 1)
     return make_problem(f"batch_{seed}_{index}", tau, n_omega, 20.0, peaks, level,
-                        int(rng.integers(0, 2**31)), n_walkers)
+                        int(rng.integers(0, 2**31)), n_walkers, noise_floor=RANDOM_NOISE_FLOOR)
 
 
 def lorentzian_band_peaks() -> List[Peak]:
