@@ -237,6 +237,22 @@ int sail_get_state(sail_t h, double *a, double *R, double *chi2, int *acc_prev, 
 int sail_set_state(sail_t h, const double *a, const int *acc_prev);
 
 /*
+ * Checkpoint and resume mid-schedule.  sail_checkpoint writes into a caller's host buffer of
+ * sail_checkpoint_size() bytes everything the rest of the schedule depends on: the walkers'
+ * spectra (and FP32 common scales), residuals exactly as stored, chi2, last-sweep acceptance,
+ * move hashes and counters, the trace so far (trace = 1), the sweep and block position, the
+ * temperature table (self-cooling fills it block by block) and the adaptive-branching and
+ * freeze-out state.  Counter-based random numbers (keyed by walker, sweep and move) need no
+ * generator state.  sail_restore loads such a buffer into a handle created from the same data
+ * and parameters (SAIL_EINVAL if the sizes, precision, schedule or seed differ): its next
+ * sail_anneal continues exactly where the checkpointed handle stopped, so an interrupted and
+ * resumed run ends bit for bit like the uninterrupted one.  Taken between sail_anneal calls.
+ */
+int sail_checkpoint_size(sail_t h, size_t *bytes);
+int sail_checkpoint(sail_t h, void *buf, size_t bytes);
+int sail_restore(sail_t h, const void *buf, size_t bytes);
+
+/*
  * Trace of a handle created with trace = 1: acc[sweeps_done * n_walkers] accepted
  * moves per sweep and walker; m[n_events * n_walkers] branching multipliers and
  * delta[n_events] (each may be NULL; n_events = number of branchings so far).

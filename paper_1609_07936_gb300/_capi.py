@@ -42,6 +42,7 @@ EXPORTS = [
     "sail_batch_tuning", "sail_batch_destroy", "sail_server_create", "sail_server_submit", "sail_server_step",
     "sail_server_result", "sail_server_destroy", "sail_destroy", "sail_last_error",
     "sail_server_start", "sail_server_poll", "sail_server_stop", "sail_server_request_info", "sail_server_trace",
+    "sail_checkpoint_size", "sail_checkpoint", "sail_restore",
 ]
 
 
@@ -135,6 +136,9 @@ def load(path: str = LIB_PATH):
     L.sail_get_state.argtypes = [vp, _dp, _dp, _dp, _ip, _u64p]
     L.sail_set_state.argtypes = [vp, _dp, _ip]
     L.sail_get_trace.argtypes = [vp, _ip, _ip, _dp, _ip]
+    L.sail_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.sail_checkpoint.argtypes = [vp, vp, ctypes.c_size_t]
+    L.sail_restore.argtypes = [vp, vp, ctypes.c_size_t]
     L.sail_delta_probe.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip, _dp, _dp, _ip]
     L.sail_philox.argtypes = [ctypes.c_int, vp, ctypes.c_uint64, vp, vp]
     L.sail_probe_read_bandwidth.argtypes = [vp, ctypes.c_size_t, ctypes.c_int, vp, vp]
@@ -348,6 +352,19 @@ class Sail:
         ne = ctypes.c_int(0)
         _check(self.lib.sail_get_trace(self._h, _ptr(acc, _ip), _ptr(m, _ip), _ptr(d), ctypes.byref(ne)))
         return acc[: inf["sweeps_done"]], m[: ne.value], d[: ne.value]
+
+    def checkpoint(self) -> bytes:
+        """Everything the rest of the schedule depends on, as bytes (sail_checkpoint)."""
+        n = ctypes.c_size_t(0)
+        _check(self.lib.sail_checkpoint_size(self._h, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self.lib.sail_checkpoint(self._h, buf, n.value))
+        return buf.raw
+
+    def restore(self, blob: bytes) -> None:
+        """Loads a checkpoint of a handle created from the same data and parameters."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self.lib.sail_restore(self._h, buf, len(blob)))
 
     def probe(self, walker, p, s, eps):
         """Delta chi2 of proposals on the current state: (delta [n], ok [n])."""
