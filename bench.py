@@ -615,7 +615,9 @@ def run_precision(args):
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(P.n_walkers, 256, replace=False))
     kinds, moves, sweep_ms = [], 0.0, 0.0
-    for kind, name in ((0, "fp32-fma"), (1, "tcgen05-tf32x3"), (2, "tcgen05-bf16x6")):
+    names = {0: "fp32-fma", 1: "tcgen05-tf32x3", 2: "tcgen05-bf16x6", 3: "fp64-fma"}
+    for kind in [int(k) for k in args.resync_kinds.split(",")]:
+        name = names[kind]
         prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=100, sweeps_per_block=50,
                           resync_every=10, branching=False, T_start=10.0, T_end=1e-3, A=P.A, B=P.B, seed=3,
                           resync_kind=kind, timing=True, shared_bins=args.shared_bins)
@@ -847,6 +849,8 @@ def main():
                     help="walkers per group proposing the same bins (0: every walker its own, the paper's move)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
                     help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")
+    ap.add_argument("--resync-kinds", default="0,1,2",
+                    help="precision workload: residual recomputations to run (0 FP32-FMA, 1 TF32 x3, 2 BF16 x6, 3 FP64)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,
                     help="sweeps per sweep-kernel launch; smaller values give short launches for profiling")
     args = ap.parse_args()

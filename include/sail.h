@@ -144,6 +144,16 @@ typedef struct sail_params {
     double T_start_abs;     /* > 0: the geometric schedule starts at this absolute temperature
                                instead of T_start chi2_0 (skip the boiling far above the data's
                                scale, whatever chi2_0 is); 0 = T_start */
+    /* A shard of a larger population (one inversion's walkers split over several handles, e.g.
+     * one per GPU; see sail_branch_solve).  walker_offset is the population index of this
+     * handle's walker 0: every random counter uses offset + w as its walker word, so a shard
+     * draws exactly what the whole population would for those walkers (a multiple of
+     * shared_bins when bins are shared).  walker_total (0: n_walkers) sizes the branching
+     * scratch for sail_branch_solve over the whole population (at most 16384 walkers).  A
+     * shard runs with branching = 0: the population branches through sail_branch_solve,
+     * sail_walker_rows and sail_imprint_rows. */
+    int walker_offset;
+    int walker_total;
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */
@@ -235,6 +245,26 @@ int sail_get_state(sail_t h, double *a, double *R, double *chi2, int *acc_prev, 
  * the residuals and chi2 are recomputed from them.  Sum rules are not enforced.
  */
 int sail_set_state(sail_t h, const double *a, const int *acc_prev);
+
+/*
+ * Branching of a population split over several handles (Sec. 2.5, the same solve as
+ * sail_anneal's).  sail_branch_solve runs the multiplier solve on the device of handle h for
+ * the n_total chi2 values chi2_all (host array, the whole population in index order; draws
+ * xi_l from Philox counter (l, block, 0, 1)): multipliers m[n_total], Delta, and the imprint
+ * pairs zero_l[k] <- donor_l[k] (population indices, k < *n_pairs; host arrays of n_total).
+ * Every handle of the population computes the same result from the same chi2.  h needs
+ * walker_total >= n_total.
+ * sail_walker_rows copies walkers idx[0..n) (this handle's indices) into device arrays
+ * a_rows[n][n_omega] and R_rows[n][n_tau] in FP64 (exact for either state precision), e.g. to
+ * send donors to the GPU that holds their receivers; sail_imprint_rows imprints this handle's
+ * walkers idx[0..n) with donor rows in this GPU's memory, a <- t a_donor + (1 - t) a and
+ * R likewise, in the arithmetic sail_anneal's imprint uses, and sums their chi2 anew.
+ * n <= 65536; idx is a host array.
+ */
+int sail_branch_solve(sail_t h, int n_total, const double *chi2_all, int block, double fraction, int *m,
+                      double *delta, int *zero_l, int *donor_l, int *n_pairs);
+int sail_walker_rows(sail_t h, int n, const int *idx, double *d_a_rows, double *d_R_rows);
+int sail_imprint_rows(sail_t h, int n, const int *idx, const double *d_a_rows, const double *d_R_rows, double t);
 
 /*
  * Checkpoint and resume mid-schedule.  sail_checkpoint writes into a caller's host buffer of

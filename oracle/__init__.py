@@ -62,6 +62,7 @@ class OrParams(ctypes.Structure):
         ("walk_uniform", ctypes.c_double),
         ("hastings", ctypes.c_int),
         ("shared_bins", ctypes.c_int),
+        ("walker_base", ctypes.c_int),
     ]
 
 
@@ -128,6 +129,8 @@ def lib():
         L.or_anneal.restype = ctypes.c_int
         L.or_average.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp, _dp]
         L.or_average.restype = ctypes.c_int
+        L.or_imprint.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]
+        L.or_imprint.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -223,6 +226,14 @@ def average(a, chi2, factor):
     err = np.zeros(a.shape[1])
     used = lib().or_average(a.shape[0], a.shape[1], _p(a), _p(chi2), float(factor), _p(mean), _p(err))
     return mean, err, used
+
+
+def imprint(t: float, a1, R1, a2, R2):
+    """Walker 1 imprinted by walker 2 with strength t (Sec. 2.5): (a1', R1', chi2 of R1')."""
+    a1, R1 = _f64(a1).copy(), _f64(R1).copy()
+    a2, R2 = _f64(a2), _f64(R2)
+    c2 = lib().or_imprint(a1.size, R1.size, float(t), _p(a1), _p(R1), _p(a2), _p(R2))
+    return a1, R1, c2
 
 
 def smooth(x, B: float, s: float, a) -> np.ndarray:
@@ -321,6 +332,7 @@ class Schedule:
     walk_uniform: float = 0.0    # probability an index skips its walk
     hastings: bool = False       # Metropolis-Hastings acceptance with the move's Jacobian
     shared_bins: int = 0         # W > 1: the walkers of each group of W propose the same bins
+    walker_base: int = 0         # population index of walker 0 (a shard of a larger population)
 
     def c(self) -> OrParams:
         return OrParams(self.n_sweeps, self.sweeps_per_block, self.resync_every, int(self.branching),
@@ -328,7 +340,7 @@ class Schedule:
                         self.move_scale, self.y_p, self.y_m, self.y_min, self.seed,
                         int(self.schedule_kind), int(self.adaptive), self.cool_begin, self.freeze_begin,
                         self.smooth_s, int(self.walk_len), self.walk_uniform, int(self.hastings),
-                        int(self.shared_bins))
+                        int(self.shared_bins), int(self.walker_base))
 
 
 class Anneal:

@@ -337,6 +337,9 @@ typedef struct {
     double walk_uniform;   /* rho: probability that an index skips its walk (uniform admixture) */
     int hastings;          /* 1: Metropolis-Hastings acceptance with the move's Jacobian */
     int shared_bins;       /* W > 1: walkers w with equal w / W propose the bins of walker W (w / W) */
+    int walker_base;       /* index in the whole population of this run's walker 0: the walker word of
+                              every move counter is walker_base + w (a shard of a population split
+                              over several runs draws exactly the words the whole run would) */
 } or_params;
 
 /* What the anneal carries from block to block besides the walkers. */
@@ -560,13 +563,14 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
     double y = or_amplitude(*acc_prev, n_omega, prm->y_p, prm->y_m, prm->y_min);
     double dmove = prm->move_scale > 0.0 ? prm->move_scale : 1.0 / n_omega;
     int accepted = 0;
+    const int wg = w + prm->walker_base;   /* the walker's index in the whole population */
     for (int mv = 0; mv < n_omega; ++mv) {
         uint32_t rnd[4];
-        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u, rnd);
+        draw(prm->seed, (uint32_t)mv, (uint32_t)n, (uint32_t)wg, 0u, rnd);
         uint32_t w0, w1;
-        bin_words(prm, mv, n, w, rnd, &w0, &w1);
+        bin_words(prm, mv, n, wg, rnd, &w0, &w1);
         int p, s;
-        or_move_bins(prm, n_omega, a, w0, w1, mv, n, w, &p, &s);
+        or_move_bins(prm, n_omega, a, w0, w1, mv, n, wg, &p, &s);
         double eps = (y * dmove) * (2.0 * unit(rnd[2]) - 1.0);
         double u = unit(rnd[3]);
         double D, ap, as;
@@ -590,6 +594,19 @@ static void sweep_walker(int n_tau, int n_omega, const double *Khat, const doubl
     }
     *acc_prev = accepted;
     *n_acc += accepted;
+}
+
+/* Imprinting, Sec. 2.5: a^(l1) <- t a^(l2) + (1 - t) a^(l1); by linearity the residual
+ * mixes the same way, and chi2 of l1 is summed again from the mixed residual.  Returns it. */
+double or_imprint(int n_omega, int n_tau, double t, double *a1, double *R1, const double *a2, const double *R2) {
+    double omt = 1.0 - t;
+    for (int j = 0; j < n_omega; ++j) a1[j] = t * a2[j] + omt * a1[j];
+    double c2 = 0.0;
+    for (int i = 0; i < n_tau; ++i) {
+        R1[i] = t * R2[i] + omt * R1[i];
+        c2 += R1[i] * R1[i];
+    }
+    return c2;
 }
 
 /* Runs sweeps [sweep_begin, sweep_end) of the schedule on all walkers.
@@ -661,22 +678,10 @@ int or_anneal(int n_tau, int n_omega, int n_walkers, const double *Khat, const d
             }
             double Delta = or_branch_multipliers(n_walkers, chi2, xi, prm->branch_fraction * scale, m);
             int np = or_pairs(n_walkers, m, zl, dl);
-            /* Imprinting, Sec. 2.5: a^(l1) <- t a^(l2) + (1 - t) a^(l1); by
-             * linearity the residual mixes the same way. */
-            double t = prm->imprint_t * scale, omt = 1.0 - t;
-            for (int q = 0; q < np; ++q) {
-                double *a1 = a + (size_t)zl[q] * n_omega;
-                const double *a2 = a + (size_t)dl[q] * n_omega;
-                double *R1 = R + (size_t)zl[q] * n_tau;
-                const double *R2 = R + (size_t)dl[q] * n_tau;
-                for (int j = 0; j < n_omega; ++j) a1[j] = t * a2[j] + omt * a1[j];
-                double c2 = 0.0;
-                for (int i = 0; i < n_tau; ++i) {
-                    R1[i] = t * R2[i] + omt * R1[i];
-                    c2 += R1[i] * R1[i];
-                }
-                chi2[zl[q]] = c2;
-            }
+            double t = prm->imprint_t * scale;
+            for (int q = 0; q < np; ++q)
+                chi2[zl[q]] = or_imprint(n_omega, n_tau, t, a + (size_t)zl[q] * n_omega, R + (size_t)zl[q] * n_tau,
+                                         a + (size_t)dl[q] * n_omega, R + (size_t)dl[q] * n_tau);
             if (m_trace) memcpy(m_trace + (size_t)events * n_walkers, m, sizeof(int) * n_walkers);
             if (delta_trace) delta_trace[events] = Delta;
             events += 1;

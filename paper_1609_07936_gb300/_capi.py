@@ -28,6 +28,7 @@ SAIL_ETIMEOUT = -5
 RESYNC_FP32 = 0
 RESYNC_TENSOR = 1
 RESYNC_TENSOR_BF16 = 2
+RESYNC_FP64 = 3
 SCHEDULE_GEOMETRIC = 0
 SCHEDULE_SELF_COOLING = 1
 PREC_FP64 = 0
@@ -43,6 +44,7 @@ EXPORTS = [
     "sail_server_result", "sail_server_destroy", "sail_destroy", "sail_last_error",
     "sail_server_start", "sail_server_poll", "sail_server_stop", "sail_server_request_info", "sail_server_trace",
     "sail_checkpoint_size", "sail_checkpoint", "sail_restore",
+    "sail_branch_solve", "sail_walker_rows", "sail_imprint_rows",
 ]
 
 
@@ -60,7 +62,7 @@ class CParams(ctypes.Structure):
         ("adaptive_branching", ctypes.c_int), ("cool_begin", ctypes.c_double), ("freeze_begin", ctypes.c_double),
         ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("hastings", ctypes.c_int),
         ("walk_uniform", ctypes.c_double), ("shared_bins", ctypes.c_int), ("sweep_loop", ctypes.c_int),
-        ("T_start_abs", ctypes.c_double),
+        ("T_start_abs", ctypes.c_double), ("walker_offset", ctypes.c_int), ("walker_total", ctypes.c_int),
     ]
 
 
@@ -136,6 +138,9 @@ def load(path: str = LIB_PATH):
     L.sail_get_state.argtypes = [vp, _dp, _dp, _dp, _ip, _u64p]
     L.sail_set_state.argtypes = [vp, _dp, _ip]
     L.sail_get_trace.argtypes = [vp, _ip, _ip, _dp, _ip]
+    L.sail_branch_solve.argtypes = [vp, ctypes.c_int, _dp, ctypes.c_int, ctypes.c_double, _ip, _dp, _ip, _ip, _ip]
+    L.sail_walker_rows.argtypes = [vp, ctypes.c_int, _ip, vp, vp]
+    L.sail_imprint_rows.argtypes = [vp, ctypes.c_int, _ip, vp, vp, ctypes.c_double]
     L.sail_checkpoint_size.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     L.sail_checkpoint.argtypes = [vp, vp, ctypes.c_size_t]
     L.sail_restore.argtypes = [vp, vp, ctypes.c_size_t]
@@ -231,6 +236,8 @@ class Params:
     shared_bins: int = 0
     sweep_loop: int = 0
     T_start_abs: float = 0.0
+    walker_offset: int = 0
+    walker_total: int = 0
 
     def c(self) -> CParams:
         p = CParams()
@@ -336,6 +343,12 @@ class Sail:
         _check(self.lib.sail_get_state(self._h, _ptr(a), _ptr(R), _ptr(chi2), _ptr(acc, _ip), _ptr(h, _u64p)))
         return a, R, chi2, acc, h
 
+    def chi2(self) -> np.ndarray:
+        """chi2 of every walker [W]."""
+        chi2 = np.zeros(self.n_walkers)
+        _check(self.lib.sail_get_state(self._h, None, None, _ptr(chi2), None, None))
+        return chi2
+
     def set_state(self, a, acc_prev=None):
         a = _f64(a)
         acc = None if acc_prev is None else np.ascontiguousarray(acc_prev, dtype=np.int32)
@@ -352,6 +365,38 @@ class Sail:
         ne = ctypes.c_int(0)
         _check(self.lib.sail_get_trace(self._h, _ptr(acc, _ip), _ptr(m, _ip), _ptr(d), ctypes.byref(ne)))
         return acc[: inf["sweeps_done"]], m[: ne.value], d[: ne.value]
+
+    def branch_solve(self, chi2_all, block: int, fraction: float):
+        """The branching solve over a whole population's chi2 (sail_branch_solve):
+        (multipliers, Delta, receivers, donors) with population indices."""
+        c = _f64(chi2_all)
+        n = c.size
+        m = np.zeros(n, dtype=np.int32)
+        zl = np.zeros(n, dtype=np.int32)
+        dl = np.zeros(n, dtype=np.int32)
+        delta, npairs = ctypes.c_double(0), ctypes.c_int(0)
+        _check(self.lib.sail_branch_solve(self._h, n, _ptr(c), int(block), float(fraction), _ptr(m, _ip),
+                                          ctypes.byref(delta), _ptr(zl, _ip), _ptr(dl, _ip), ctypes.byref(npairs)))
+        return m, delta.value, zl[: npairs.value].copy(), dl[: npairs.value].copy()
+
+    def walker_rows(self, idx):
+        """Spectra and residuals of this handle's walkers idx, as FP64 device tensors."""
+        import torch
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        a = torch.empty((idx.size, self.n_omega), dtype=torch.float64, device="cuda")
+        R = torch.empty((idx.size, self.n_tau), dtype=torch.float64, device="cuda")
+        if idx.size:
+            _check(self.lib.sail_walker_rows(self._h, idx.size, _ptr(idx, _ip), ctypes.c_void_p(a.data_ptr()),
+                                             ctypes.c_void_p(R.data_ptr())))
+        return a, R
+
+    def imprint_rows(self, idx, a_rows, R_rows, t: float) -> None:
+        """Imprints this handle's walkers idx with donor rows held on this GPU (FP64 tensors)."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.size:
+            a_rows, R_rows = a_rows.contiguous(), R_rows.contiguous()
+            _check(self.lib.sail_imprint_rows(self._h, idx.size, _ptr(idx, _ip), ctypes.c_void_p(a_rows.data_ptr()),
+                                              ctypes.c_void_p(R_rows.data_ptr()), float(t)))
 
     def checkpoint(self) -> bytes:
         """Everything the rest of the schedule depends on, as bytes (sail_checkpoint)."""

@@ -32,6 +32,7 @@ UNITS = {
     "sweep_batch16.cu": [],
     "resync_fp32.cu": [],
     "resync_tc.cu": [],
+    "resync_tma.cu": [],
     "noalloc.cu": ["-fmad=false"],
 }
 

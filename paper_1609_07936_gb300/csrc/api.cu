@@ -75,6 +75,8 @@ struct Layout {
     size_t m, zero_l, donor_l, n_pairs, delta, counters, bz, bxi, cand, cand_Z, ctl;
     size_t mean, err, R_mean, chi2_mean, n_used, cut;
     size_t pr_walker, pr_p, pr_s, pr_eps, pr_delta, pr_ok;
+    size_t tma_a, tma_b;     // pre-tiled BF16 pieces of the spectra and the kernel table (resync kind 2)
+    size_t chi2_all;         // chi2 of the whole population (sail_branch_solve)
     size_t total;
     int max_events;
 };
@@ -109,6 +111,10 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
         L.g2 = take(W * 2 * 4);
         L.R32 = take(W * PAD * 4);
     }
+    if (p.precision == SAIL_PREC_FP32 && p.resync_kind == 2) {
+        L.tma_a = take(tma_spectra_bytes(p.n_walkers, n_omega));
+        L.tma_b = take(tma_table_bytes((int)PAD, n_omega));
+    }
     L.chi2 = take(W * 8);
     L.acc_prev = take(W * 4);
     L.hash = take(W * 8);
@@ -120,13 +126,16 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
         L.m_trace = take((size_t)L.max_events * W * 4);
         L.delta_trace = take((size_t)L.max_events * 8);
     }
-    L.m = take(W * 4);
-    L.zero_l = take(W * 4);
-    L.donor_l = take(W * 4);
+    // branching scratch: this handle's walkers, or the whole population of a shard
+    const size_t WB = std::max(W, (size_t)p.walker_total);
+    L.m = take(WB * 4);
+    L.zero_l = take(WB * 4);
+    L.donor_l = take(WB * 4);
     L.n_pairs = take(4);
     L.delta = take(8);
-    L.bz = take(W * 8);
-    L.bxi = take(W * 8);
+    L.bz = take(WB * 8);
+    L.bxi = take(WB * 8);
+    L.chi2_all = take(WB * 8);
     L.cand = take(128 * 8);
     L.cand_Z = take(128 * 4);
     L.ctl = take(64);
@@ -162,6 +171,12 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
     if (!(p->T_end_abs >= 0) || !std::isfinite(p->T_end_abs)) return fail(SAIL_EINVAL, "T_end_abs must be finite, >= 0");
     if (!(p->T_start_abs >= 0) || !std::isfinite(p->T_start_abs))
         return fail(SAIL_EINVAL, "T_start_abs must be finite, >= 0");
+    if (p->walker_offset < 0 || p->walker_total < 0 || p->walker_total > kMaxWalkers ||
+        (p->walker_total > 0 && p->walker_offset + p->n_walkers > p->walker_total))
+        return fail(SAIL_EINVAL, "a shard needs 0 <= walker_offset, offset + n_walkers <= walker_total <= %d",
+                    kMaxWalkers);
+    if (p->shared_bins > 1 && p->walker_offset % p->shared_bins != 0)
+        return fail(SAIL_EINVAL, "walker_offset must be a multiple of shared_bins");
     if (!(p->branch_fraction >= 0 && p->branch_fraction < 1)) return fail(SAIL_EINVAL, "branch_fraction must be in [0, 1)");
     if (!(p->imprint_t >= 0 && p->imprint_t <= 1)) return fail(SAIL_EINVAL, "imprint_t must be in [0, 1]");
     if (!(p->y_p > 0 && p->y_p <= 1) || !(p->y_m >= 1) || !(p->y_min > 0 && p->y_min <= 1))
@@ -222,6 +237,7 @@ struct sail_ctx {
     double acc_ref;          // acceptance of the first block (< 0 until known)
     double T_freeze;         // smallest residue when the freeze-out began (< 0 until then)
     std::vector<double> chi2_host;
+    TmaPlan tma;             // resync kind 2: tensor maps of the pre-tiled operands
     int *status;             // device status word: nonzero after a timed-out device wait
     bool converged;          // chi2 of the averaged spectrum reached target_chi2
     double chi2_of_mean;
@@ -518,6 +534,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.walk_rho = p->walk_uniform;
     P.hastings = p->hastings;
     P.shared_bins = p->shared_bins > 1 ? p->shared_bins : 0;
+    P.walker_base = p->walker_offset;
     {
         // the look-ahead loop pays where several warps share each scheduler (4096 walkers on
         // 152 SMs: +12%); with few walkers per SM its longer chain per move costs more (1500:
@@ -578,6 +595,11 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     if (e == cudaSuccess) e = up(L.R0, R0.data(), PAD * 8);
     if (e == cudaSuccess && p->trace)
         e = cudaMemsetAsync(ws + L.acc_trace, 0, (size_t)p->n_sweeps * p->n_walkers * 4, st);
+    P.tma = nullptr;
+    if (e == cudaSuccess && p->precision == SAIL_PREC_FP32 && p->resync_kind == 2) {
+        e = tma_plan_init(h->tma, P, ws + L.tma_a, ws + L.tma_b, st);
+        P.tma = &h->tma;
+    }
     if (e == cudaSuccess)
         e = launch_init_state(P, S, p->precision, (const double *)(ws + L.a0), (const double *)(ws + L.R0), chi2_0, st);
     h->launches = 1;
@@ -1039,6 +1061,85 @@ CkptHeader ckpt_header(const sail_ctx *h) {
 
 }  // namespace
 
+int sail_branch_solve(sail_t h, int n_total, const double *chi2_all, int block, double fraction, int *m,
+                      double *delta, int *zero_l, int *donor_l, int *n_pairs) {
+    if (!h || !chi2_all || !m || !delta || !zero_l || !donor_l || !n_pairs) return fail(SAIL_EINVAL, "NULL argument");
+    const int cap = std::max(h->prm.n_walkers, h->prm.walker_total);
+    if (n_total < 2 || n_total > cap) return fail(SAIL_EINVAL, "n_total must be in [2, %d] (walker_total)", cap);
+    if (block < 0) return fail(SAIL_EINVAL, "block must be >= 0");
+    if (!(fraction >= 0.0 && fraction < 1.0)) return fail(SAIL_EINVAL, "fraction must be in [0, 1)");
+    for (int l = 0; l < n_total; ++l)
+        if (!std::isfinite(chi2_all[l]) || chi2_all[l] < 0) return fail(SAIL_EINVAL, "chi2_all[%d] is not a residue", l);
+    cudaStream_t st = h->stream;
+    double *d_chi2 = (double *)(h->ws + h->L.chi2_all);
+    SAIL_CUDA(cudaMemcpyAsync(d_chi2, chi2_all, (size_t)n_total * 8, cudaMemcpyHostToDevice, st), "solve H2D");
+    DevProblem P = h->P;
+    P.n_walkers = n_total;
+    P.walker_base = 0;
+    DevState S = h->S;
+    S.chi2 = d_chi2;
+    BranchScratch B = h->Bs;
+    B.m_trace = nullptr;
+    B.delta_trace = nullptr;
+    int l = 0;
+    SAIL_CUDA(launch_branch_solve(P, S, B, block, fraction, st, &l), "solve launch");
+    h->launches += l;
+    int np = 0;
+    SAIL_CUDA(cudaMemcpyAsync(m, B.m, (size_t)n_total * 4, cudaMemcpyDeviceToHost, st), "solve D2H");
+    SAIL_CUDA(cudaMemcpyAsync(delta, B.delta, 8, cudaMemcpyDeviceToHost, st), "solve D2H");
+    SAIL_CUDA(cudaMemcpyAsync(&np, B.n_pairs, 4, cudaMemcpyDeviceToHost, st), "solve D2H");
+    SAIL_CUDA(cudaStreamSynchronize(st), "solve sync");
+    if (np > 0) {
+        SAIL_CUDA(cudaMemcpyAsync(zero_l, B.zero_l, (size_t)np * 4, cudaMemcpyDeviceToHost, st), "solve D2H");
+        SAIL_CUDA(cudaMemcpyAsync(donor_l, B.donor_l, (size_t)np * 4, cudaMemcpyDeviceToHost, st), "solve D2H");
+        SAIL_CUDA(cudaStreamSynchronize(st), "solve sync");
+    }
+    *n_pairs = np;
+    return SAIL_OK;
+}
+
+namespace {
+
+int rows_index(sail_t h, int n, const int *idx, int **d_idx) {
+    if (n < 0 || n > kProbeMax) return fail(SAIL_EINVAL, "n must be in [0, %d]", kProbeMax);
+    for (int q = 0; q < n; ++q)
+        if (idx[q] < 0 || idx[q] >= h->prm.n_walkers) return fail(SAIL_EINVAL, "idx[%d] = %d is not a walker", q, idx[q]);
+    *d_idx = (int *)(h->ws + h->L.pr_walker);
+    SAIL_CUDA(cudaMemcpyAsync(*d_idx, idx, (size_t)n * 4, cudaMemcpyHostToDevice, h->stream), "rows H2D");
+    return SAIL_OK;
+}
+
+}  // namespace
+
+int sail_walker_rows(sail_t h, int n, const int *idx, double *d_a_rows, double *d_R_rows) {
+    if (!h || (n > 0 && (!idx || !d_a_rows || !d_R_rows))) return fail(SAIL_EINVAL, "NULL argument");
+    if (n == 0) return SAIL_OK;
+    int *d_idx = nullptr;
+    const int rc = rows_index(h, n, idx, &d_idx);
+    if (rc) return rc;
+    SAIL_CUDA(launch_walker_rows(h->P, h->S, h->prm.precision, n, d_idx, d_a_rows, d_R_rows, h->stream), "rows launch");
+    h->launches += 1;
+    SAIL_CUDA(cudaStreamSynchronize(h->stream), "rows sync");
+    return SAIL_OK;
+}
+
+int sail_imprint_rows(sail_t h, int n, const int *idx, const double *d_a_rows, const double *d_R_rows, double t) {
+    if (!h || (n > 0 && (!idx || !d_a_rows || !d_R_rows))) return fail(SAIL_EINVAL, "NULL argument");
+    if (!(t >= 0.0 && t <= 1.0)) return fail(SAIL_EINVAL, "t must be in [0, 1]");
+    if (n == 0) return SAIL_OK;
+    for (int q = 0; q < n; ++q)
+        for (int r = 0; r < q; ++r)
+            if (idx[r] == idx[q]) return fail(SAIL_EINVAL, "walker %d imprinted twice", idx[q]);
+    int *d_idx = nullptr;
+    const int rc = rows_index(h, n, idx, &d_idx);
+    if (rc) return rc;
+    SAIL_CUDA(launch_imprint_rows(h->P, h->S, h->prm.precision, n, d_idx, d_a_rows, d_R_rows, t, h->stream),
+              "imprint launch");
+    h->launches += 1;
+    SAIL_CUDA(cudaStreamSynchronize(h->stream), "imprint sync");
+    return SAIL_OK;
+}
+
 int sail_checkpoint_size(sail_t h, size_t *bytes) {
     if (!h || !bytes) return fail(SAIL_EINVAL, "NULL argument");
     *bytes = ckpt_bytes(h);
@@ -1436,7 +1537,7 @@ int batch_run_blocks(sail_batch_ctx *b, int max_blocks, int *n_done) {
                 sail_batch_ctx::TcTune *tt = nullptr;
                 for (auto &t : b->tc)
                     if (t.pad == h->pad) tt = &t;
-                if (tt && (h->prm.resync_kind == 1 || h->prm.resync_kind == 2)) {
+                if (tt && h->prm.resync_kind == 1) {
                     if (tt->next < tt->n_cand) {
                         h->P.tc_cols = tt->cand[tt->next];
                         cudaEventCreate(&t0);

@@ -103,22 +103,23 @@ __global__ void __launch_bounds__(128) sweep_fp64_kernel(DevProblem P, DevState 
     unsigned long long h = S.hash[w], nacc = 0, npos = 0;
     const uint2 key = philox_key(P.seed);
     const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
+    const int wg = w + P.walker_base;   // the walker's index in the whole population
 
     for (int n = n0; n < n1; ++n) {
         const double T = P.Tsweep[n];
         const double y = amplitude(accp, NO, P.y_p, P.y_m, P.y_min);
         int acc = 0;
         for (int mv = 0; mv < NO; ++mv) {
-            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)w, 0u), key);
+            const uint4 rnd = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)wg, 0u), key);
             // shared bins: the group's first walker's words 0 and 1 (its own counter)
             uint2 bw = make_uint2(rnd.x, rnd.y);
-            if (P.shared_bins > 1 && w % P.shared_bins != 0) {
+            if (P.shared_bins > 1 && wg % P.shared_bins != 0) {
                 const uint4 g = philox4x32_10(
-                    make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)(w - w % P.shared_bins), 0u), key);
+                    make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)(wg - wg % P.shared_bins), 0u), key);
                 bw = make_uint2(g.x, g.y);
             }
             int p, s;
-            walk_bins64(P, a, bw.x, bw.y, mv, n, w, key, p, s);
+            walk_bins64(P, a, bw.x, bw.y, mv, n, wg, key, p, s);
             const double eps = (y * dmove) * (2.0 * unit64(rnd.z) - 1.0);
             const double u = unit64(rnd.w);
             const double r = 1.0 - eps;
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(kSolveThreads) branch_prep_kernel(DevProblem P
     const uint2 key = philox_key(P.seed);
     for (int l = tid; l < N; l += blockDim.x) {
         B.z[l] = spread > 0.0 ? (s_chi2[l] - cmin) / spread : 0.0;
-        B.xi[l] = unit64(philox4x32_10(make_uint4((uint32_t)l, (uint32_t)block_index, 0u, 1u), key).x);
+        B.xi[l] = unit64(philox4x32_10(make_uint4((uint32_t)(l + P.walker_base), (uint32_t)block_index, 0u, 1u), key).x);
     }
 }
 
@@ -679,6 +680,52 @@ __global__ void __launch_bounds__(128) imprint_kernel(DevProblem P, DevState S, 
     if (threadIdx.x == 0) {
         double c2 = 0.0;
         for (int i = 0; i < P.n_tau; ++i) c2 = c2 + Rs[i] * Rs[i];
+        S.chi2[l1] = c2;
+    }
+}
+
+// Walker rows for another handle of the population: spectrum and residual of idx[q] in FP64.
+__global__ void walker_rows_kernel(DevProblem P, DevState S, int precision, const int *idx, double *a_rows,
+                                   double *R_rows) {
+    const int q = blockIdx.x, l = idx[q];
+    const int NO = P.n_omega, NT = P.n_tau, PAD = P.n_tau_pad;
+    for (int j = threadIdx.x; j < NO; j += blockDim.x)
+        a_rows[(size_t)q * NO + j] = precision == 0 ? S.a64[(size_t)l * NO + j] : (double)S.b32[(size_t)l * NO + j];
+    for (int i = threadIdx.x; i < NT; i += blockDim.x)
+        R_rows[(size_t)q * NT + i] = precision == 0 ? S.R64[(size_t)l * PAD + i] : (double)S.R32[(size_t)l * PAD + i];
+}
+
+// Imprinting from donor rows (Sec. 2.5), the arithmetic of imprint_kernel with the donor's
+// values read from rows in this device's memory: walker idx[q] <- t row q + (1 - t) itself.
+__global__ void __launch_bounds__(128) imprint_rows_kernel(DevProblem P, DevState S, int precision, const int *idx,
+                                                           const double *a_rows, const double *R_rows, double t) {
+    __shared__ double Rs[kMaxTau];
+    const int q = blockIdx.x, l1 = idx[q];
+    const double omt = 1.0 - t;
+    const int NO = P.n_omega, NT = P.n_tau, PAD = P.n_tau_pad;
+    const double *a2 = a_rows + (size_t)q * NO, *R2 = R_rows + (size_t)q * NT;
+    if (precision == 0) {
+        double *a1 = S.a64 + (size_t)l1 * NO;
+        for (int j = threadIdx.x; j < NO; j += blockDim.x) a1[j] = t * a2[j] + omt * a1[j];
+        for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+            const double r = t * (i < NT ? R2[i] : 0.0) + omt * S.R64[(size_t)l1 * PAD + i];
+            S.R64[(size_t)l1 * PAD + i] = r;
+            Rs[i] = r;
+        }
+    } else {
+        float *b1 = S.b32 + (size_t)l1 * NO;
+        const float tf = (float)t, omtf = (float)omt;
+        for (int j = threadIdx.x; j < NO; j += blockDim.x) b1[j] = tf * (float)a2[j] + omtf * b1[j];
+        for (int i = threadIdx.x; i < PAD; i += blockDim.x) {
+            const double r = t * (i < NT ? R2[i] : 0.0) + omt * (double)S.R32[(size_t)l1 * PAD + i];
+            S.R32[(size_t)l1 * PAD + i] = (float)r;
+            Rs[i] = (double)(float)r;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double c2 = 0.0;
+        for (int i = 0; i < NT; ++i) c2 = c2 + Rs[i] * Rs[i];
         S.chi2[l1] = c2;
     }
 }
@@ -926,8 +973,13 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         *launches += 1;
         return launch_resync_fp64(P, S, st);
     }
-    *launches += kind >= 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
-    return kind >= 1 ? launch_resync_tc(P, S, status, kind == 2, st) : launch_resync_fp32(P, S, st);
+    if (kind == 2) {                  // spectra pre-tiling, tensor-copy GEMM, chi2 pass
+        if (!P.tma) return cudaErrorInvalidValue;
+        *launches += 3;
+        return launch_resync_tma(P, S, *P.tma, status, st);
+    }
+    *launches += kind == 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
+    return kind == 1 ? launch_resync_tc(P, S, status, false, st) : launch_resync_fp32(P, S, st);
 }
 
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B, int precision,
@@ -940,6 +992,25 @@ cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchSc
     if (e != cudaSuccess) return e;
     imprint_kernel<<<P.n_walkers, 128, 0, st>>>(P, S, B, precision, imprint_t);
     *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch_solve(const DevProblem &P, const DevState &S, const BranchScratch &B, int block_index,
+                                double fraction, cudaStream_t st, int *launches) {
+    if (P.n_walkers <= kSolveThreads * 4) return launch_solve<4>(P, S, B, block_index, fraction, 0, st, launches);
+    if (P.n_walkers <= kSolveThreads * 8) return launch_solve<8>(P, S, B, block_index, fraction, 0, st, launches);
+    return launch_solve<16>(P, S, B, block_index, fraction, 0, st, launches);
+}
+
+cudaError_t launch_walker_rows(const DevProblem &P, const DevState &S, int precision, int n, const int *idx,
+                               double *a_rows, double *R_rows, cudaStream_t st) {
+    walker_rows_kernel<<<n, 128, 0, st>>>(P, S, precision, idx, a_rows, R_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_imprint_rows(const DevProblem &P, const DevState &S, int precision, int n, const int *idx,
+                                const double *a_rows, const double *R_rows, double t, cudaStream_t st) {
+    imprint_rows_kernel<<<n, 128, 0, st>>>(P, S, precision, idx, a_rows, R_rows, t);
     return cudaGetLastError();
 }
 

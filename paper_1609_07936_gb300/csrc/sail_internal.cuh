@@ -14,6 +14,7 @@
 //   R64 / R32        [n_walkers][n_tau_pad] residuals, zero past n_tau
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace sail {
@@ -26,6 +27,14 @@ constexpr int kSolvePerThread = 16;   // walkers per solve thread: n_walkers <= 
 constexpr int kMaxWalkers = kSolveThreads * kSolvePerThread;
 constexpr unsigned long long kFnvOffset = 0xCBF29CE484222325ull;
 constexpr unsigned long long kFnvPrime = 0x100000001B3ull;
+
+// The tensor-copy (TMA) residual recomputation of a handle: the tensor maps of its pre-tiled
+// spectra and kernel-table buffers (resync_tma.cu) and the block shape.
+struct TmaPlan {
+    CUtensorMap map_a, map_b;
+    void *At, *Bt;
+    int n, n_kt, n_blocks_tau, n_blocks_walkers;
+};
 
 struct DevProblem {
     int n_tau, n_omega, n_walkers, n_tau_pad, n_sweeps;
@@ -53,6 +62,8 @@ struct DevProblem {
     int shared_bins;       // W > 1: walkers in groups of W propose their first walker's bins
     int ahead;             // FP32, up to 8 chunks: the look-ahead move loop (else one move at a time)
     const double *Tsweep;
+    const TmaPlan *tma;    // host pointer (launchers only): the BF16 tensor-copy recomputation, or null
+    int walker_base;       // population index of walker 0: the walker word of every random counter
 };
 
 struct DevState {
@@ -115,9 +126,27 @@ cudaError_t launch_resync_fp32(const DevProblem &P, const DevState &S, cudaStrea
 // Tensor-core (tcgen05) residual recomputation for FP32 state, TF32 with a three-term split or
 // (bf16) BF16 with three pieces and six products; status[0] <- 1 on a timed-out wait.
 cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, bool bf16, cudaStream_t st);
+// The BF16 x6 recomputation as a pipelined GEMM fed by tensor copies (resync_tma.cu): tau
+// columns per block for a padded tau count, workspace bytes of the pre-tiled spectra and
+// kernel table, the plan (tensor maps; pre-tiles the kernel table on st) and the launch
+// (pre-tiles the spectra, GEMM, chi2); status[0] <- 1 on a timed-out wait.
+int tma_tau_block(int n_tau_pad);
+size_t tma_spectra_bytes(int n_walkers, int n_omega);
+size_t tma_table_bytes(int n_tau_pad, int n_omega);
+cudaError_t tma_plan_init(TmaPlan &T, const DevProblem &P, void *At, void *Bt, cudaStream_t st);
+cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status, cudaStream_t st);
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);
+// The branching solve alone (multipliers, Delta, imprint pairs into B) over P.n_walkers chi2
+// values in S.chi2, draws keyed by population index (P.walker_base + l); no imprint, no trace.
+cudaError_t launch_branch_solve(const DevProblem &P, const DevState &S, const BranchScratch &B, int block_index,
+                                double fraction, cudaStream_t st, int *launches);
+// Rows of walkers idx[0..n) (device array) in FP64, and imprinting of walkers idx from donor rows.
+cudaError_t launch_walker_rows(const DevProblem &P, const DevState &S, int precision, int n, const int *idx,
+                               double *a_rows, double *R_rows, cudaStream_t st);
+cudaError_t launch_imprint_rows(const DevProblem &P, const DevState &S, int precision, int n, const int *idx,
+                                const double *a_rows, const double *R_rows, double t, cudaStream_t st);
 // Smoothing (Sec. smoothing) of every walker's spectrum with strength s and the tilt that
 // restores the second sum rule; one thread per walker, sums in bin order (FP64 arithmetic for
 // either state precision).  The residuals are stale afterwards.

@@ -331,7 +331,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
         const float yd = (float)(amplitude(accp, NO, P.y_p, P.y_m, P.y_min) * dmove);
         int acc = 0, pos = 0;
         float dchi = 0.0f;
-        MoveDraw mine = draw_move<MODE>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        MoveDraw mine = draw_move<MODE>(gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
         MoveDraw cur = take_move(mine, 0, G);
         f2 dcur[PIPE ? C : 1][H];
         if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
@@ -346,7 +346,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
                 // the index walk (Sec. 2.3) on the spectrum as it is now: lane t of the group
                 // draws step t + 1's words (counter (mv, n, w, 2 + t)), lane L the admixture's
                 const int L = P.walk_len;
-                const uint4 wr4 = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)wr, 2u + gl), key);
+                const uint4 wr4 = philox4x32_10(make_uint4((uint32_t)mv, (uint32_t)n, (uint32_t)(wr + P.walker_base), 2u + gl), key);
                 const bool walk_p = !(unit32(__shfl_sync(kFull, wr4.x, L, G)) < rho);
                 const bool walk_s = !(unit32(__shfl_sync(kFull, wr4.y, L, G)) < rho);
                 int wp = cur.ps & 0xFFFF;
@@ -461,7 +461,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             }
             // the next batch of G moves, one per lane, before its first move is taken
             if (((mv + 2) & (G - 1)) == 0 && mv + 2 < NO)
-                mine = draw_move<MODE>(mv + 2 + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+                mine = draw_move<MODE>(mv + 2 + gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
         }
         chi2 += (double)dchi;
         accp = acc;
@@ -583,14 +583,14 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
         acc = pos = 0;
         dchi = 0.0f;
         wb = lo = 0;
-        pa = draw_move<MODE>(gl, n, wr, key, NO, yd, T, sBeta, sRgap);
-        pb = draw_move<MODE>(G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        pa = draw_move<MODE>(gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
+        pb = draw_move<MODE>(G + gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
     };
     // slide the windows by G once the current move lies in window B
     auto slide = [&]() {
         pa = pb;
         wb += G;
-        pb = draw_move<MODE>(wb + G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+        pb = draw_move<MODE>(wb + G + gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
     };
     if (!done) start_sweep();
 
@@ -664,8 +664,8 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
                 } else {
                     wb += 2 * G;
                     lo = wb;
-                    pa = draw_move<MODE>(wb + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
-                    pb = draw_move<MODE>(wb + G + gl, n, wr, key, NO, yd, T, sBeta, sRgap);
+                    pa = draw_move<MODE>(wb + gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
+                    pb = draw_move<MODE>(wb + G + gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
                 }
             }
         }

@@ -153,9 +153,9 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
         float dchi = 0.0f;
         // lane (v, q) holds walker v's words of move mv0 + q of the current round, and of the
         // next round
-        SharedDraw cur = shared_draw<MODE>(q, n, w, key, NO, yd, T);
+        SharedDraw cur = shared_draw<MODE>(q, n, w + P.walker_base, key, NO, yd, T);
         SharedDraw nxt = cur;
-        if (MPD < NO) nxt = shared_draw<MODE>(MPD + q, n, w, key, NO, yd, T);
+        if (MPD < NO) nxt = shared_draw<MODE>(MPD + q, n, w + P.walker_base, key, NO, yd, T);
         f2 Ga[C], Gb[C];
         float cpa, csa, gga, cpb = 0.0f, csb = 0.0f, ggb = 0.0f;
         const int ps0 = __shfl_sync(kFull, cur.ps, 0);
@@ -168,7 +168,7 @@ __device__ __forceinline__ void run_shared(const DevProblem &P, const DevState &
             const int m = mv & (MPD - 1);
             if (m == 0 && mv > 0) {
                 cur = nxt;
-                if (mv + MPD < NO) nxt = shared_draw<MODE>(mv + MPD + q, n, w, key, NO, yd, T);
+                if (mv + MPD < NO) nxt = shared_draw<MODE>(mv + MPD + q, n, w + P.walker_base, key, NO, yd, T);
             }
             // this move: the shared bins, every walker's amplitude, this lane's walker's threshold
             const int ps = __shfl_sync(kFull, cur.ps, W * m);

@@ -26,8 +26,8 @@ MUTATIONS = {
     "branch_sign": ("heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) - xi[top.l]);",
                     "heap[0].b = Delta * z[top.l] + log((double)(top.k + 1) + xi[top.l]);"),
     # adaptive branching that forgets to scale the imprint strength
-    "imprint_unscaled": ("double t = prm->imprint_t * scale, omt = 1.0 - t;",
-                         "double t = prm->imprint_t, omt = 1.0 - t;"),
+    "imprint_unscaled": ("double t = prm->imprint_t * scale;",
+                         "double t = prm->imprint_t;"),
     # smoothing stencil with the end weight in the interior
     "stencil_weight": ("double c = 1.0 - 2.0 * s, e = 1.0 - s;", "double c = 1.0 - s, e = 1.0 - s;"),
     # self-cooling ramp running from the minimum to the mean
