@@ -602,18 +602,24 @@ def run_reference(args, rank, world):
 def run_precision(args):
     """The precision configuration: 512 tau x 2048 bins, 16384 walkers, a 1-4 peak random
     spectrum, FP32 moves.  For each residual recomputation (FP32-FMA GEMM, tcgen05 TF32 x3,
-    tcgen05 BF16 x6): two blocks of 50 sweeps with a recomputation every 10, its time per call
-    from CUDA events, and the error of the residual it leaves against an FP64 recomputation
-    from the same spectra on 256 sampled walkers (relative to the model value sum_j K_ij a_j)."""
+    tcgen05 BF16 x6 fed by tensor copies, FP64-FMA): two blocks of 50 sweeps with a
+    recomputation every 10, its time per call from CUDA events, and the error of the residual
+    it leaves against the FP64 validation path's sequential recomputation from the same spectra
+    on 256 sampled walkers (relative to the model value sum_j K_ij a_j).  Then the error of a
+    result: 256 walkers of the same problem annealed with the same seed by the FP64 validation
+    path (the oracle's arithmetic) and by the mixed-precision path (FP32 moves, BF16 x6
+    recomputation), their averaged spectra and chi2 of the averages compared, beside the same
+    comparison between two seeds of the mixed path (the method's own spread)."""
     import torch
-    import oracle as O
     import paper_1609_07936_gb300 as sail
     from workloads import precision_random_peaks
     sail.load()
     P = precision_random_peaks(0)
-    K, Fh, _ = O.tables(P.tau, P.F, P.sigma, P.omega)
+    Fh = P.F / P.sigma
     rng = np.random.default_rng(0)
     sample = np.sort(rng.choice(P.n_walkers, 256, replace=False))
+    ref = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                    sail.Params(n_walkers=sample.size, precision=sail.PREC_FP64, n_sweeps=10, A=P.A, B=P.B))
     kinds, moves, sweep_ms = [], 0.0, 0.0
     names = {0: "fp32-fma", 1: "tcgen05-tf32x3", 2: "tcgen05-bf16x6", 3: "fp64-fma"}
     for kind in [int(k) for k in args.resync_kinds.split(",")]:
@@ -626,8 +632,10 @@ def run_precision(args):
         torch.cuda.synchronize()
         inf = g.info()
         a, R, chi2, _, _ = g.state()
-        model = a[sample] @ K.T
-        err = np.abs(R[sample] - (Fh[None, :] - model))
+        ref.set_state(a[sample])
+        R64 = ref.state()[1]
+        model = Fh[None, :] - R64
+        err = np.abs(R[sample] - R64)
         rel = err / np.maximum(model, 1e-300)
         kinds.append({"resync": name, "ms_per_call": inf["resync_ms"] / max(inf["resync_launches"], 1),
                       "max_err_rel_model": float(rel.max()), "rms_err_rel_model": float(np.sqrt(np.mean(rel ** 2))),
@@ -635,9 +643,36 @@ def run_precision(args):
         moves += inf["moves"]
         sweep_ms += inf["sweep_ms"]
         g.close()
+    ref.close()
     flop = 2.0 * P.n_walkers * P.n_omega * P.n_tau
     for k in kinds:
         k["useful_tflops"] = flop / (k["ms_per_call"] * 1e-3) / 1e12
+
+    result_error = None
+    if not args.no_result_error:
+        W = 256
+        sched = dict(n_walkers=W, n_sweeps=args.result_sweeps, sweeps_per_block=SWEEPS_PER_BLOCK,
+                     resync_every=RESYNC_EVERY, branching=True, T_start_abs=TTT_T_START, T_end_abs=TTT_T_END,
+                     move_scale=TTT_D_FACTOR / P.n_omega, A=P.A, B=P.B)
+        runs = {}
+        for tag, precision, seed in (("fp64", sail.PREC_FP64, 5), ("mixed", sail.PREC_FP32, 5),
+                                     ("mixed_other_seed", sail.PREC_FP32, 6)):
+            h = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                          sail.Params(precision=precision, seed=seed, resync_kind=RESYNC_KIND, **sched))
+            h.anneal()
+            mean, err_, used, c2 = h.average()
+            runs[tag] = (mean, c2)
+            h.close()
+        l2 = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+        result_error = {
+            "walkers": W, "sweeps": args.result_sweeps,
+            "schedule": f"geometric T {TTT_T_START:g} -> {TTT_T_END:g} absolute, branching every {SWEEPS_PER_BLOCK}",
+            "spectrum_rel_l2_mixed_vs_fp64": l2(runs["mixed"][0], runs["fp64"][0]),
+            "spectrum_rel_l2_mixed_seed_vs_seed": l2(runs["mixed_other_seed"][0], runs["mixed"][0]),
+            "chi2_of_mean": {k: v[1] for k, v in runs.items()},
+            "reading": "same seed: the FP64 path takes the oracle's decisions; the mixed path parts from it as "
+                       "FP32 rounding flips decisions, so its distance to the FP64 result is compared with the "
+                       "distance between two seeds of the mixed path"}
     out = {"metric": METRIC, "value": moves / (sweep_ms * 1e-3), "unit": "walker-moves/s", "n_gpus": 1,
            "steps": 3, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
@@ -645,7 +680,7 @@ def run_precision(args):
                                   "residual recomputation every 10 sweeps by each method"
                                   + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""),
                       "step": "two blocks of 50 sweeps per recomputation method"},
-           "resync": kinds}
+           "resync": kinds, "result_error": result_error}
     print(json.dumps(out), flush=True)
 
 
@@ -849,6 +884,10 @@ def main():
                     help="walkers per group proposing the same bins (0: every walker its own, the paper's move)")
     ap.add_argument("--sweep-lanes", type=int, default=0, choices=[0, 8, 16],
                     help="GPU lanes per walker in the FP32 sweep (0: the library's choice)")
+    ap.add_argument("--no-result-error", action="store_true",
+                    help="precision workload: skip the mixed-vs-FP64 comparison of a result")
+    ap.add_argument("--result-sweeps", type=int, default=1000,
+                    help="precision workload: sweeps of the mixed-vs-FP64 result comparison")
     ap.add_argument("--resync-kinds", default="0,1,2",
                     help="precision workload: residual recomputations to run (0 FP32-FMA, 1 TF32 x3, 2 BF16 x6, 3 FP64)")
     ap.add_argument("--resync-every", type=int, default=RESYNC_EVERY,

@@ -15,7 +15,9 @@
 // float pair (TwoSum, round to nearest), so the bias is that of 4 MMAs per tile and the sum
 // over tiles carries ~2^-44 relative error.
 //
-// BF16 variant (resync kind 2): each operand is split into three BF16 pieces,
+// The library launches this kernel for the TF32 form (resync kind 1); the BF16 form (kind 2)
+// runs as the tensor-copy pipeline of resync_tma.cu.  The template's BF16 operand format:
+// each operand is split into three BF16 pieces,
 // x = x1 + x2 + x3 (each the round-to-nearest BF16 of what is left), and the products kept are
 // x1 y1 (main accumulator) and x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1 (correction accumulator);
 // the dropped terms are ~2^-24 of a product.  kind::f16 with BF16 A and B (both operands of
@@ -392,7 +394,9 @@ cudaError_t launch_tc(const DevProblem &P, const DevState &S, int *status, cudaS
 // the widest such width.  Every width gives the same result bit for bit: each column's sum
 // runs over the same tiles in the same order.
 cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status, bool bf16, cudaStream_t st) {
-    return bf16 ? launch_tc<true>(P, S, status, st) : launch_tc<false>(P, S, status, st);
+    // the BF16 x6 recomputation runs as the tensor-copy pipeline of resync_tma.cu
+    if (bf16) return cudaErrorInvalidValue;
+    return launch_tc<false>(P, S, status, st);
 }
 
 }  // namespace sail

@@ -5,23 +5,22 @@
 // Operands.  Each FP32 value x is split into three BF16 pieces, x = x1 + x2 + x3 (each the
 // round-to-nearest BF16 of what is left), and the products kept are x1 y1 (main accumulator)
 // and x1 y2 + x2 y1 + x1 y3 + x2 y2 + x3 y1 (correction accumulator); the dropped terms are
-// ~2^-24 of a product.  The pieces are written once per recomputation (spectra) or once per
-// handle (kernel table) into "pre-tiled" buffers: for every block of 128 walkers (or N tau
-// rows) and every 32 bins, each piece's tile is one contiguous run of bytes already in the
-// MMA's canonical K-major layout without swizzle (core matrices of 8 rows x 16 bytes; the next
-// core matrix along K 128 bytes on, the next 8-row group 512 bytes on).  A tile then moves to
-// shared memory as one 2D tensor copy (cp.async.bulk.tensor over the buffer viewed as rows of
-// 128 bytes) whose bytes land in the same order.
+// ~2^-24 of a product.  The pieces are written once per recomputation (spectra, an elementwise
+// pass) or once per handle (kernel table) as plain row-major BF16 arrays [piece][row][bin],
+// rows of 64-bin multiples.  A tile of 64 bins (128 bytes per row) moves to shared memory as
+// one 3D tensor copy (cp.async.bulk.tensor) with the 128-byte swizzle, which is the K-major
+// operand layout the MMA reads with a SWIZZLE_128B descriptor (8-row groups 1024 bytes apart;
+// the K steps of 16 bins advance the start address by 32 bytes inside the swizzle atom).
 //
 // Block: 128 walkers (the MMA's M) x N tau columns (N <= 64, a multiple of 16 dividing the
 // padded tau count), 10 warps with fixed roles:
 //   warp 0: one thread issues the tensor copies of stage s (3 spectra tiles, 3 kernel tiles)
 //           once the MMAs have released it (mbarrier empty[s]) and arms full[s] with the byte
 //           count;
-//   warp 1: one thread waits full[s], issues the stage's 12 MMAs (two K steps of 16 bins, six
-//           products each) and commits them to empty[s]; every two stages (64 bins) it
-//           commits the accumulator buffer to accfull[b] and starts the next period in the
-//           other buffer once the epilogue has drained it (accempty[b]);
+//   warp 1: one thread waits full[s], issues the stage's 24 MMAs (four K steps of 16 bins,
+//           six products each), commits them to empty[s] and the accumulator buffer to
+//           accfull[b], and starts the next stage in the other buffer once the epilogue has
+//           drained it (accempty[b]);
 //   warps 2-9: drain the accumulators of each 64-bin period with tcgen05.ld and add them to
 //           per-thread float pairs (TwoSum, round to nearest), two warps per 32-lane quarter
 //           of tensor memory (each half of the columns), then write R.
@@ -30,7 +29,7 @@
 // 64 bins (four MMAs in the main chain) keeps that bias near 2^-22 of a product, and the
 // periods are summed in float pairs.  Tensor memory holds two buffers of (main, correction) x N
 // columns, so the MMAs of one period overlap the draining of the previous one; shared memory
-// holds six stages.  Every wait is bounded: on time-out a thread sets the status word and the
+// holds three stages of 64 bins.  Every wait is bounded: on time-out a thread sets the status word and the
 // block's abort flag, the roles leave their loops, the copy thread waits (bounded) for the
 // copies it issued, the MMA thread for its MMAs, and tensor memory is freed before the block
 // returns.
@@ -47,20 +46,22 @@ namespace sail {
 namespace {
 
 constexpr int kM = 128;                      // walkers per block (MMA M)
-constexpr int kKT = 32;                      // bins per stage
-constexpr int kStages = 6;                   // 6 x 36 KB at N = 64: six tiles of 32 bins in flight
-constexpr int kPeriodTiles = 2;              // stages per accumulation period (64 bins)
-constexpr int kEpiWarps = 8;
+constexpr int kKT = 64;                      // bins per stage (one 128-byte swizzle atom of BF16)
+constexpr int kPeriodTiles = 1;              // stages per accumulation period (64 bins)
+constexpr int kEpiWarps = 16;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr uint32_t kTileA = kM * kKT * 2;    // bytes of one piece of the spectra tile
-constexpr uint32_t kLBO = 128, kSBO = 512;   // canonical K-major layout, BF16, 32-bin tiles
+constexpr uint32_t kTileA = kM * kKT * 2;    // bytes of one piece of the spectra tile (16 KB)
+constexpr uint32_t kSBO = 1024;              // 8 rows x 128 bytes: one swizzle pattern
 constexpr long long kSpin = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Shared-memory descriptor of a K-major operand in the 128-byte swizzle: start address, leading
+// offset (unused with this swizzle: 1), stride between 8-row groups, descriptor version 1,
+// layout type 2 (SWIZZLE_128B).
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
-    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)((kSBO >> 4) & 0x3FFFu) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -105,17 +106,17 @@ __device__ __forceinline__ void arrive_tx(uint32_t mbar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// One 2D tensor copy global -> shared, completing on mbar (x = 0: the row of 128 bytes).
-__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int y, uint32_t mbar) {
+// One 3D tensor copy global -> shared (bins x, rows y, piece z), completing on mbar.
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t mbar) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"((uint64_t)map), "r"(0), "r"(y), "r"(mbar)
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(mbar)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t v[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t v[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                  : "r"(taddr));
 }
 
@@ -153,68 +154,64 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &r1, uint4 &r2
     r3 = make_uint4(w3[0], w3[1], w3[2], w3[3]);
 }
 
-// Pre-tiling of the spectra: block (kt, wb) writes the three piece tiles of walkers
-// 128 wb .. +127 and bins 32 kt .. +31; thread (r, c) splits bins 32 kt + 8 c .. +7 of walker
-// row r (zero past the last walker or bin).  A warp covers 8 rows x 4 core matrices: its
-// 16-byte stores fill 512 consecutive bytes of each piece tile.
-__global__ void __launch_bounds__(512) pretile_spectra_kernel(DevProblem P, DevState S, uint4 *At, int n_kt) {
-    const int kt = blockIdx.x, wb = blockIdx.y;
-    const int c = threadIdx.x & 3, r = threadIdx.x >> 2;
-    const int w = wb * kM + r, j0 = kt * kKT + 8 * c;
+// The three BF16 pieces of the spectra, [piece][walker row][bin] with rows of NOP bins
+// (n_omega rounded up to 64) and W_pad rows (n_walkers rounded up to 128), zero past the last
+// walker or bin: thread t splits 8 consecutive bins of one row (coalesced loads and stores).
+__global__ void presplit_spectra_kernel(DevProblem P, DevState S, uint4 *At, int n_rows, int nop) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_row = nop / 8;
+    if (t >= (size_t)n_rows * per_row) return;
+    const int w = (int)(t / per_row), j0 = (int)(t % per_row) * 8;
     float v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e)
         v[e] = (w < P.n_walkers && j0 + e < P.n_omega) ? S.b32[(size_t)w * P.n_omega + j0 + e] : 0.0f;
     uint4 r1, r2, r3;
     split8(v, r1, r2, r3);
-    const size_t tile = ((size_t)wb * n_kt + kt) * 3;           // first of the three piece tiles
-    const uint32_t off = ((uint32_t)(r >> 3) * kSBO + (uint32_t)c * kLBO + (uint32_t)(r & 7) * 16) / 16;
-    At[(tile + 0) * (kTileA / 16) + off] = r1;
-    At[(tile + 1) * (kTileA / 16) + off] = r2;
-    At[(tile + 2) * (kTileA / 16) + off] = r3;
+    const size_t plane = (size_t)n_rows * nop / 8;             // uint4 per piece
+    At[t] = r1;
+    At[plane + t] = r2;
+    At[2 * plane + t] = r3;
 }
 
-// Pre-tiling of the kernel table (once per handle): block (kt, nb) writes the piece tiles of
-// tau rows N nb .. +N-1 and bins 32 kt .. +31.
-__global__ void pretile_kernel_table(DevProblem P, uint4 *Bt, int n_kt, int N) {
-    const int kt = blockIdx.x, nb = blockIdx.y;
-    const uint32_t tileB = (uint32_t)N * kKT * 2;
-    for (int t = threadIdx.x; t < N * 4; t += blockDim.x) {
-        const int c = t & 3, r = t >> 2;
-        const int i = nb * N + r, j0 = kt * kKT + 8 * c;
-        float v[8];
+// The three BF16 pieces of the kernel table, [piece][tau row][bin] (once per handle).
+__global__ void presplit_kernel_table(DevProblem P, uint4 *Bt, int nop) {
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int per_row = nop / 8;
+    if (t >= (size_t)P.n_tau_pad * per_row) return;
+    const int i = (int)(t / per_row), j0 = (int)(t % per_row) * 8;
+    float v[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e)
-            v[e] = (i < P.n_tau && j0 + e < P.n_omega) ? P.Khat32[(size_t)(j0 + e) * P.n_tau_pad + i] : 0.0f;
-        uint4 r1, r2, r3;
-        split8(v, r1, r2, r3);
-        const size_t tile = ((size_t)nb * n_kt + kt) * 3;
-        const uint32_t off = ((uint32_t)(r >> 3) * kSBO + (uint32_t)c * kLBO + (uint32_t)(r & 7) * 16) / 16;
-        Bt[(tile + 0) * (tileB / 16) + off] = r1;
-        Bt[(tile + 1) * (tileB / 16) + off] = r2;
-        Bt[(tile + 2) * (tileB / 16) + off] = r3;
-    }
+    for (int e = 0; e < 8; ++e)
+        v[e] = (i < P.n_tau && j0 + e < P.n_omega) ? P.Khat32[(size_t)(j0 + e) * P.n_tau_pad + i] : 0.0f;
+    uint4 r1, r2, r3;
+    split8(v, r1, r2, r3);
+    const size_t plane = (size_t)P.n_tau_pad * nop / 8;
+    Bt[t] = r1;
+    Bt[plane + t] = r2;
+    Bt[2 * plane + t] = r3;
 }
 
 template <int N>
 struct TmaCfg {
     static constexpr uint32_t kTileB = N * kKT * 2;
     static constexpr uint32_t kStage = 3 * (kTileA + kTileB);
-    static constexpr uint32_t kCols = 256;                         // two buffers of (main, corr)
-    static constexpr int kPart = N / 2;                            // columns per epilogue thread
+    static constexpr int kStages = N <= 64 ? 3 : 2;                // 3 x 72 KB at N = 64, 2 x 96 KB at 128
+    static constexpr uint32_t kCols = 4 * N <= 256 ? 256 : 512;   // two buffers of (main, corr)
+    static constexpr int kPart = N / 4;                            // columns per epilogue thread
     static constexpr int kBars = 2 * kStages + 5;                 // full, empty, accfull, accempty, done
     static constexpr size_t kSmem = (size_t)kStages * kStage + 8 * kBars + 8 + 1024;
 };
 
 template <int N>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(96)
     resync_tma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, DevProblem P,
                       DevState S, int n_kt, int *status) {
     using C = TmaCfg<N>;
-    static_assert(N % 16 == 0 && N >= 16 && N <= 64, "tau columns per block");
+    static_assert(N % 32 == 0 && N >= 32 && N <= 128, "tau columns per block");
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)kStages * C::kStage);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)C::kStages * C::kStage);
     // bar[0, S) full, bar[S, 2S) empty, bar[2S, 2S + 2) accfull, bar[2S + 2, 2S + 4) accempty,
     // bar[2S + 4] done (S stages); then the tensor-memory address and the abort flag
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + C::kBars);
@@ -223,15 +220,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nb = blockIdx.x, wb = blockIdx.y;
     const uint32_t sbase = smem_u32(smem), bbase = smem_u32(bar);
     auto full = [&](int s) { return bbase + 8u * (uint32_t)s; };
-    auto empty = [&](int s) { return bbase + 8u * (uint32_t)(kStages + s); };
-    auto accfull = [&](int b) { return bbase + 8u * (uint32_t)(2 * kStages + b); };
-    auto accempty = [&](int b) { return bbase + 8u * (uint32_t)(2 * kStages + 2 + b); };
-    const uint32_t done_bar = bbase + 8u * (uint32_t)(2 * kStages + 4);
+    auto empty = [&](int s) { return bbase + 8u * (uint32_t)(C::kStages + s); };
+    auto accfull = [&](int b) { return bbase + 8u * (uint32_t)(2 * C::kStages + b); };
+    auto accempty = [&](int b) { return bbase + 8u * (uint32_t)(2 * C::kStages + 2 + b); };
+    const uint32_t done_bar = bbase + 8u * (uint32_t)(2 * C::kStages + 4);
     auto tileA = [&](int s, int q) { return sbase + (uint32_t)s * C::kStage + (uint32_t)q * kTileA; };
     auto tileB = [&](int s, int q) { return sbase + (uint32_t)s * C::kStage + 3u * kTileA + (uint32_t)q * C::kTileB; };
 
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < C::kStages; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full(s)));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty(s)));
         }
@@ -260,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---- tensor copies
             int issued = 0;
             for (int kt = 0; kt < n_kt && !*abort; ++kt) {
-                const int s = kt % kStages, u = kt / kStages;
+                const int s = kt % C::kStages, u = kt / C::kStages;
                 if (u > 0 && !wait(empty(s), (uint32_t)((u - 1) & 1), abort)) {
                     atomicExch(status, 1);
                     *abort = 1;
@@ -268,17 +265,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 arrive_tx(full(s), C::kStage);
                 for (int q = 0; q < 3; ++q) {
-                    tma_2d(tileA(s, q), &tmA, (int)((((size_t)wb * n_kt + kt) * 3 + q) * (kTileA / 128)), full(s));
-                    tma_2d(tileB(s, q), &tmB, (int)((((size_t)nb * n_kt + kt) * 3 + q) * (C::kTileB / 128)), full(s));
+                    tma_3d(tileA(s, q), &tmA, kt * kKT, wb * kM, q, full(s));
+                    tma_3d(tileB(s, q), &tmB, kt * kKT, nb * N, q, full(s));
                 }
                 issued = kt + 1;
             }
             if (*abort) {
                 // copies still landing in shared memory: wait (bounded) for the stages issued
-                for (int kt = issued > kStages ? issued - kStages : 0; kt < issued; ++kt) {
+                for (int kt = issued > C::kStages ? issued - C::kStages : 0; kt < issued; ++kt) {
                     const long long lim = kSpin;
                     for (long long it = 0; it < lim; ++it)
-                        if (try_wait(full(kt % kStages), (uint32_t)((kt / kStages) & 1))) break;
+                        if (try_wait(full(kt % C::kStages), (uint32_t)((kt / C::kStages) & 1))) break;
                 }
             }
         }
@@ -288,7 +285,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // 16-byte units), so each operand's descriptor is one base plus a constant offset.
             const uint32_t idesc = idesc_bf16(kM, N);
             const uint64_t dA = desc(tileA(0, 0)), dB = desc(tileB(0, 0));
-            constexpr uint64_t kTa = kTileA >> 4, kTb = C::kTileB >> 4, kKs = (2u * kLBO) >> 4;
+            constexpr uint64_t kTa = kTileA >> 4, kTb = C::kTileB >> 4, kKs = 32u >> 4;
             int kt = 0;
             for (int d = 0; d < n_periods && !*abort; ++d) {
                 const int b = d & 1, u = d >> 1;
@@ -300,8 +297,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t dmain = tmem + (uint32_t)(b * 2 * N), dcorr = dmain + (uint32_t)N;
                 for (int t = 0; t < kPeriodTiles && kt < n_kt; ++t, ++kt) {
-                    const int s = kt % kStages;
-                    if (!wait(full(s), (uint32_t)((kt / kStages) & 1), abort)) {
+                    const int s = kt % C::kStages;
+                    if (!wait(full(s), (uint32_t)((kt / C::kStages) & 1), abort)) {
                         atomicExch(status, 1);
                         *abort = 1;
                         break;
@@ -310,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t sa = dA + (uint64_t)((uint32_t)s * (C::kStage >> 4)),
                                    sb = dB + (uint64_t)((uint32_t)s * (C::kStage >> 4));
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {   // 16 bins = two core matrices per K step
+                    for (int ks = 0; ks < kKT / 16; ++ks) {   // 16 bins = 32 bytes of the swizzle atom
                         const uint64_t a0 = sa + ks * kKs, a1 = a0 + kTa, a2 = a0 + 2 * kTa;
                         const uint64_t b0 = sb + ks * kKs, b1 = b0 + kTb, b2 = b0 + 2 * kTb;
                         const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
@@ -332,8 +329,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (try_wait(done_bar, 0u)) break;
         }
     } else {
-        // ---- epilogue: warps 2..9; a warp may read tensor-memory lanes 32 (warp % 4) .. +31,
-        // and the two warps of each such quarter take half of the columns each
+        // ---- epilogue: warps 2..17; a warp may read tensor-memory lanes 32 (warp % 4) .. +31,
+        // and the four warps of each such quarter take a quarter of the columns each
         const int quarter = warp & 3, part = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
         float hi[C::kPart], lo[C::kPart];
@@ -357,13 +354,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t col0 = (uint32_t)(b * 2 * N + part * C::kPart);
 #pragma unroll
-            for (int c = 0; c < C::kPart; c += 8) {
-                uint32_t vm[8], vc[8];
-                tmem_ld8(tmem + lane_base + col0 + (uint32_t)c, vm);
-                tmem_ld8(tmem + lane_base + col0 + (uint32_t)N + (uint32_t)c, vc);
+            for (int c = 0; c < C::kPart; c += 4) {
+                uint32_t vm[4], vc[4];
+                tmem_ld4(tmem + lane_base + col0 + (uint32_t)c, vm);
+                tmem_ld4(tmem + lane_base + col0 + (uint32_t)N + (uint32_t)c, vc);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
+                for (int e = 0; e < 4; ++e)
                     two_sum_add(hi[c + e], lo[c + e], __uint_as_float(vm[e]) + __uint_as_float(vc[e]));
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -373,12 +370,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!*abort) {
             const int w = wb * kM + 32 * quarter + lane;
             if (w < P.n_walkers) {
+                float *Rw = S.R32 + (size_t)w * P.n_tau_pad + nb * N + part * C::kPart;
+                const double *Fw = P.Fhat64 + nb * N + part * C::kPart;
+                const int i0 = nb * N + part * C::kPart;
 #pragma unroll
                 for (int c = 0; c < C::kPart; ++c) {
-                    const int i = nb * N + part * C::kPart + c;
-                    const double model = (double)hi[c] + (double)lo[c];
-                    const double r = i < P.n_tau ? P.Fhat64[i] - model : 0.0;
-                    S.R32[(size_t)w * P.n_tau_pad + i] = (float)r;
+                    const double r = i0 + c < P.n_tau ? Fw[c] - ((double)hi[c] + (double)lo[c]) : 0.0;
+                    Rw[c] = (float)r;
                 }
             }
         }
@@ -423,66 +421,67 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// A pre-tiled buffer of `rows` rows of 128 bytes (64 BF16) as a 2D tensor; each copy moves
-// box_rows consecutive rows.
-bool encode_rows(CUtensorMap *map, void *base, size_t rows, uint32_t box_rows) {
+// A [3][rows][nop] BF16 array as a 3D tensor copied in boxes of 64 bins x box_rows rows x one
+// piece, with the 128-byte swizzle (the operand layout of the MMA's SWIZZLE_128B descriptors).
+bool encode_pieces(CUtensorMap *map, void *base, size_t rows, int nop, uint32_t box_rows) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
-    const cuuint64_t dims[2] = {64, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {128};
-    const cuuint32_t box[2] = {64, box_rows};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+    const cuuint64_t dims[3] = {(cuuint64_t)nop, (cuuint64_t)rows, 3};
+    const cuuint64_t strides[2] = {(cuuint64_t)nop * 2, (cuuint64_t)nop * 2 * rows};
+    const cuuint32_t box[3] = {(cuuint32_t)kKT, box_rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
            CUDA_SUCCESS;
 }
+
+int bins_padded(int n_omega) { return (n_omega + kKT - 1) / kKT * kKT; }
+int walkers_padded(int n_walkers) { return (n_walkers + kM - 1) / kM * kM; }
 
 }  // namespace
 
 int tma_tau_block(int n_tau_pad) {
-    for (int nc = 64; nc >= 16; nc -= 16)
+    for (int nc = 128; nc >= 32; nc -= 32)
         if (n_tau_pad % nc == 0) return nc;
     return 0;
 }
 
 size_t tma_spectra_bytes(int n_walkers, int n_omega) {
-    const size_t wb = (size_t)(n_walkers + kM - 1) / kM, kt = (size_t)(n_omega + kKT - 1) / kKT;
-    return wb * kt * 3 * kTileA;
+    return (size_t)3 * walkers_padded(n_walkers) * bins_padded(n_omega) * 2;
 }
 
-size_t tma_table_bytes(int n_tau_pad, int n_omega) {
-    const size_t kt = (size_t)(n_omega + kKT - 1) / kKT;
-    return (size_t)n_tau_pad * kKT * 2 * kt * 3;
-}
+size_t tma_table_bytes(int n_tau_pad, int n_omega) { return (size_t)3 * n_tau_pad * bins_padded(n_omega) * 2; }
 
 cudaError_t tma_plan_init(TmaPlan &T, const DevProblem &P, void *At, void *Bt, cudaStream_t st) {
     T.n = tma_tau_block(P.n_tau_pad);
     if (T.n == 0) return cudaErrorInvalidValue;
-    T.n_kt = (P.n_omega + kKT - 1) / kKT;
+    const int nop = bins_padded(P.n_omega);
+    T.n_kt = nop / kKT;
     T.n_blocks_tau = P.n_tau_pad / T.n;
-    T.n_blocks_walkers = (P.n_walkers + kM - 1) / kM;
+    T.n_blocks_walkers = walkers_padded(P.n_walkers) / kM;
     T.At = At;
     T.Bt = Bt;
-    if (((uintptr_t)At & 15) || ((uintptr_t)Bt & 15)) return cudaErrorInvalidValue;
-    const size_t rows_a = tma_spectra_bytes(P.n_walkers, P.n_omega) / 128;
-    const size_t rows_b = tma_table_bytes(P.n_tau_pad, P.n_omega) / 128;
-    if (!encode_rows(&T.map_a, At, rows_a, kTileA / 128) ||
-        !encode_rows(&T.map_b, Bt, rows_b, (uint32_t)(T.n * kKT * 2 / 128)))
+    if (((uintptr_t)At & 127) || ((uintptr_t)Bt & 127)) return cudaErrorInvalidValue;
+    if (!encode_pieces(&T.map_a, At, (size_t)walkers_padded(P.n_walkers), nop, kM) ||
+        !encode_pieces(&T.map_b, Bt, (size_t)P.n_tau_pad, nop, (uint32_t)T.n))
         return cudaErrorInvalidValue;
-    pretile_kernel_table<<<dim3(T.n_kt, T.n_blocks_tau), 256, 0, st>>>(P, (uint4 *)Bt, T.n_kt, T.n);
+    const size_t threads = (size_t)P.n_tau_pad * nop / 8;
+    presplit_kernel_table<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, (uint4 *)Bt, nop);
     return cudaGetLastError();
 }
 
 cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status,
                               cudaStream_t st) {
-    pretile_spectra_kernel<<<dim3(T.n_kt, T.n_blocks_walkers), 512, 0, st>>>(P, S, (uint4 *)T.At, T.n_kt);
+    const int nop = T.n_kt * kKT, rows = T.n_blocks_walkers * kM;
+    const size_t threads = (size_t)rows * nop / 8;
+    presplit_spectra_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, S, (uint4 *)T.At, rows, nop);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     switch (T.n) {
+        case 128: e = launch_n<128>(P, S, T, status, st); break;
+        case 96: e = launch_n<96>(P, S, T, status, st); break;
         case 64: e = launch_n<64>(P, S, T, status, st); break;
-        case 48: e = launch_n<48>(P, S, T, status, st); break;
         case 32: e = launch_n<32>(P, S, T, status, st); break;
-        case 16: e = launch_n<16>(P, S, T, status, st); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

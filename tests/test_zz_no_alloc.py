@@ -6,9 +6,10 @@ memory budget, or a service loop that must not pay for cudaMalloc / cudaFree.  F
 sail_residue_noalloc computes the residue chi2 (and the residuals) of given spectra with its
 scratch in a fixed array inside the library.  Here its output is compared, on two calls in a
 row with different sizes (so the second call runs on the array the first one filled), with
-the residual recomputation a handle runs after sail_set_state.  The two build their kernel
-tables with different exp implementations (device here, host in sail_create), so they agree
-to a relative 1e-10 rather than bit for bit.
+the residual recomputation a handle runs after sail_set_state, and with the FP64 oracle's
+residual of the same spectra (an independent implementation of the kernel table and the
+sums).  The device builds its table with its own exp, so the agreement is a relative 1e-10
+rather than bit for bit.
 """
 import ctypes
 
@@ -60,6 +61,12 @@ def test_noalloc_residue_matches_the_handle_recomputation():
         chi2_ref, R_ref = _reference(P, a)
         np.testing.assert_allclose(chi2, chi2_ref, rtol=1e-10)
         np.testing.assert_allclose(R, R_ref, rtol=1e-10, atol=1e-10 * np.abs(R_ref).max())
+        import oracle as O
+        K, Fh, _ = O.tables(P.tau, P.F, P.sigma, P.omega)
+        for w in range(W):
+            R_o, c2_o = O.residual(K, Fh, a[w])
+            assert abs(chi2[w] - c2_o) <= 1e-10 * c2_o
+            np.testing.assert_allclose(R[w], R_o, rtol=1e-10, atol=1e-10 * np.abs(R_o).max())
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch():
