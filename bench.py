@@ -34,6 +34,7 @@ NOISE = 1e-4
 WORKLOAD = (f"paper_scale_double_lorentz: N_tau={N_TAU} on [0,8], N_omega={N_OMEGA} on [0,20], "
             f"{N_WALKERS} walkers, sigma={NOISE:g}*F, FP32 moves, tensor-core (BF16 x6) resync every {RESYNC_EVERY} sweeps, "
             f"branching every {SWEEPS_PER_BLOCK} sweeps (f=1/4, t=0.1), {N_SWEEPS}-sweep schedule T 10->1e-9")
+WORKLOAD_TO_TARGET = WORKLOAD.replace("schedule T 10->1e-9", "schedule T 1e6->0.03 absolute, move scale 0.1/N_omega")
 METRIC = "walker-moves/s"
 MOVES_PER_STEP = SWEEPS_PER_BLOCK * N_OMEGA * N_WALKERS
 
@@ -49,14 +50,18 @@ TTT_INVERSIONS = 4
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
                sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0, sweep_loop: int = 0,
-               noise: float = NOISE):
+               noise: float = NOISE, schedule: str = "paper"):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(noise, n_walkers=N_WALKERS)
+    if schedule == "to_target":
+        temps = dict(T_start_abs=TTT_T_START, T_end_abs=TTT_T_END, move_scale=TTT_D_FACTOR / N_OMEGA)
+    else:
+        temps = dict(T_start=10.0, T_end=1e-9)
     prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
-                      T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=seed, timing=timing,
+                      A=P.A, B=P.B, seed=seed, timing=timing,
                       resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk,
-                      shared_bins=shared_bins, sweep_loop=sweep_loop)
+                      shared_bins=shared_bins, sweep_loop=sweep_loop, **temps)
     return P, prm
 
 
@@ -201,7 +206,7 @@ def run_gpu(args, rank, world, local_rank):
     # warm-up: W blocks on a separate handle (same configuration, other seed)
     P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
@@ -209,7 +214,7 @@ def run_gpu(args, rank, world, local_rank):
 
     P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -269,7 +274,7 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_e2e:
         P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
                               sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop)
+                              shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -300,7 +305,7 @@ def run_gpu(args, rank, world, local_rank):
         for lvl in (1e-3, 1e-5):
             P3, prm3 = params_for(seed=rank + 500, resync_kind=args.resync_kind, sweep_lanes=args.sweep_lanes,
                                   index_walk=args.index_walk, shared_bins=args.shared_bins,
-                                  sweep_loop=args.sweep_loop, noise=lvl)
+                                  sweep_loop=args.sweep_loop, noise=lvl, schedule=args.schedule)
             h3 = sail.Sail(P3.tau, P3.F, P3.sigma, P3.omega, prm3)
             h3.anneal(args.warmup)
             m0 = h3.info()["moves"]
@@ -336,7 +341,8 @@ def run_gpu(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD + (f", index walk of {args.index_walk} steps" if args.index_walk else "")
+            "config": {"workload": (WORKLOAD_TO_TARGET if args.schedule == "to_target" else WORKLOAD)
+                       + (f", index walk of {args.index_walk} steps" if args.index_walk else "")
                        + (f", bins shared by groups of {args.shared_bins} walkers" if args.shared_bins else ""), "step": f"one block: {SWEEPS_PER_BLOCK} sweeps x {N_OMEGA} moves x "
                        f"{N_WALKERS} walkers + 2 resyncs + branching", "walkers_per_gpu": N_WALKERS,
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"{world} independent inversions"},
@@ -858,6 +864,9 @@ def main():
                     help="directory for the raw nvidia-smi clock samples of the timed region (default: /tmp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-to-target", action="store_true", help="skip the time-to-target legs")
+    ap.add_argument("--schedule", default="paper", choices=["paper", "to_target"],
+                    help="temperature schedule of the timed blocks: the paper's (T 10 -> 1e-9 chi2_0, move "
+                         "scale 1/N_omega) or the to-target one (T 1e6 -> 0.03 absolute, 0.1/N_omega)")
     ap.add_argument("--ttt-inversions", type=int, default=TTT_INVERSIONS,
                     help="time to target: inversions of the workload submitted together")
     ap.add_argument("--no-noise-levels", action="store_true",
