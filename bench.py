@@ -333,6 +333,11 @@ def run_gpu(args, rank, world, local_rank):
                                        if ttt64["inversions_per_s"] > 0 else None),
             "equal_final_chi2": "both legs stop at the same target chi2 (or the same sweep budget)"}
 
+    # the uneven batch (256 inversions sharing launches) as an extra field of the same line
+    batch = None
+    if not args.no_batch:
+        batch = batch_leg(sail, torch, args.batch_size, 1, 2, args.resync_kind)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample_walkers)
@@ -368,7 +373,7 @@ def run_gpu(args, rank, world, local_rank):
             "kernel_ms": {"sweep": sweep_ms, "resync": info1["resync_ms"] - info0["resync_ms"],
                           "branch": info1["branch_ms"] - info0["branch_ms"], "total": ms},
             "e2e": e2e, "gpu_launches": own_launches, "clocks": clk, "cpu_baseline": cpu,
-            "other_noise_levels": noise_levels, "to_target": ttt,
+            "other_noise_levels": noise_levels, "to_target": ttt, "uneven_batch": batch,
             "last_block": stats[-1] if stats else None,
         }
         print(json.dumps(out), flush=True)
@@ -436,48 +441,60 @@ def cpu_baseline(n_walkers: int):
 
 
 # ---------------------------------------------------------------- uneven batch and serving
-def run_batch(args):
+def batch_leg(sail, torch, batch_size: int, steps: int, warmup: int, resync_kind: int) -> dict:
     """256 independent inversions (n_tau U{50..500}, n_omega U{200..2000}, walkers U{256..4096},
     noise log-uniform [1e-5, 1e-3], 1-4 random peaks) annealed together: one persistent sweep
-    launch per segment, tensor-core resync, branching every 100 sweeps, autotuned mapping."""
-    import torch
-    import paper_1609_07936_gb300 as sail
+    launch per class of problems and segment, tensor-core resync, branching every 100 sweeps,
+    autotuned mapping.  walker-moves/s over `steps` blocks of every inversion (CUDA events on the
+    batch's stream) after `warmup` blocks (which include the autotuner's trials)."""
     from workloads import random_batch_problem
-    sail.load()
-    probs = [random_batch_problem(i, seed=0) for i in range(args.batch_size)]
+    probs = [random_batch_problem(i, seed=0) for i in range(batch_size)]
     items = []
     for i, P in enumerate(probs):
         prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=N_SWEEPS,
                           sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
-                          T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=i, resync_kind=args.resync_kind)
+                          T_start=10.0, T_end=1e-9, A=P.A, B=P.B, seed=i, resync_kind=resync_kind)
         items.append((P.tau, P.F, P.sigma, P.omega, prm))
     t0 = time.perf_counter()
     batch = sail.Batch(items, autotune=True)
     t_create = time.perf_counter() - t0
-    batch.anneal(args.warmup)
+    batch.anneal(warmup)
     moves0 = sum(h.info()["moves"] for h in batch.handles)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = batch.stream
     e0.record(st)
-    batch.anneal(args.steps)
+    batch.anneal(steps)
     e1.record(st)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     moves = sum(h.info()["moves"] for h in batch.handles) - moves0
     per_inv = float(np.mean([N_SWEEPS * P.n_walkers * P.n_omega for P in probs]))
     value = moves / (ms * 1e-3)
-    out = {"metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"uneven batch: {len(probs)} inversions, n_tau U{{50..500}}, n_omega U{{200..2000}}, "
-                                  f"walkers U{{256..4096}} (total {sum(P.n_walkers for P in probs)}), noise log-U[1e-5,1e-3], "
-                                  f"one persistent sweep launch per {RESYNC_EVERY}-sweep segment",
-                      "step": f"one block ({SWEEPS_PER_BLOCK} sweeps) of every inversion"},
+    out = {"value": value, "unit": "walker-moves/s", "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
+           "workload": f"uneven batch: {len(probs)} inversions, n_tau U{{50..500}}, n_omega U{{200..2000}}, "
+                       f"walkers U{{256..4096}} (total {sum(P.n_walkers for P in probs)}), noise log-U[1e-5,1e-3], "
+                       f"one persistent sweep launch per class and {RESYNC_EVERY}-sweep segment",
+           "step": f"one block ({SWEEPS_PER_BLOCK} sweeps) of every inversion",
            "inversions_per_s": value / per_inv, "moves_per_inversion": per_inv,
            "tuning": batch.tuning(), "create_s": t_create}
-    print(json.dumps(out), flush=True)
     batch.close()
+    return out
+
+
+def run_batch(args):
+    """The uneven batch as its own benchmark line (see batch_leg)."""
+    import torch
+    import paper_1609_07936_gb300 as sail
+    sail.load()
+    b = batch_leg(sail, torch, args.batch_size, args.steps, args.warmup, args.resync_kind)
+    out = {"metric": METRIC, "value": b["value"], "unit": "walker-moves/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": b["workload"], "step": b["step"]},
+           "inversions_per_s": b["inversions_per_s"], "moves_per_inversion": b["moves_per_inversion"],
+           "tuning": b["tuning"], "create_s": b["create_s"]}
+    print(json.dumps(out), flush=True)
 
 
 def run_serve(args):
@@ -814,11 +831,16 @@ def run_band(args):
     results, moves, dev_ms = [], 0.0, 0.0
     for level in (0.0, 1e-5, 1e-4, 1e-2):
         P = lorentzian_band(level, seed=7)
+        if args.band_schedule == "to_target":
+            sched = dict(T_start_abs=TTT_T_START, T_end_abs=TTT_T_END, move_scale=TTT_D_FACTOR / P.n_omega,
+                         smooth_s=args.band_smooth)
+        else:
+            sched = dict(schedule_kind=sail.SCHEDULE_SELF_COOLING, adaptive_branching=True, smooth_s=1e-2,
+                         T_end_abs=0.3)
         prm = sail.Params(n_walkers=P.n_walkers, precision=sail.PREC_FP32, n_sweeps=args.band_sweeps,
                           sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
-                          schedule_kind=sail.SCHEDULE_SELF_COOLING, adaptive_branching=True, smooth_s=1e-2,
-                          T_end_abs=0.3, A=P.A, B=P.B, seed=11, resync_kind=args.resync_kind,
-                          target_chi2=1.2 * P.n_tau, timing=True, sweep_loop=args.sweep_loop)
+                          A=P.A, B=P.B, seed=11, resync_kind=args.resync_kind,
+                          target_chi2=1.2 * P.n_tau, timing=True, sweep_loop=args.sweep_loop, **sched)
         t0 = time.perf_counter()
         g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
         g.anneal()
@@ -842,8 +864,11 @@ def run_band(args):
            "steps": len(results), "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "Lorentzian band (HWHM 1 at 1 and 2, band [0.5, 2.5]), 1000 bins on [0, 3.5], "
-                                  "160 tau points at 0.05, 1500 walkers, self-cooling + adaptive branching + "
-                                  f"smoothing 1e-2, {args.band_sweeps} sweeps or chi2 <= 1.2 n_tau",
+                                  "160 tau points at 0.05, 1500 walkers, "
+                                  + ("self-cooling + adaptive branching + smoothing 1e-2"
+                                     if args.band_schedule == "protocol" else
+                                     f"geometric T 1e6 -> 0.03, move scale 0.1/N_omega, smoothing {args.band_smooth:g}")
+                                  + f", {args.band_sweeps} sweeps or chi2 <= 1.2 n_tau",
                       "step": "one inversion per noise level"},
            "band": results}
     print(json.dumps(out), flush=True)
@@ -864,6 +889,7 @@ def main():
                     help="directory for the raw nvidia-smi clock samples of the timed region (default: /tmp)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-to-target", action="store_true", help="skip the time-to-target legs")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch leg")
     ap.add_argument("--schedule", default="paper", choices=["paper", "to_target"],
                     help="temperature schedule of the timed blocks: the paper's (T 10 -> 1e-9 chi2_0, move "
                          "scale 1/N_omega) or the to-target one (T 1e6 -> 0.03 absolute, 0.1/N_omega)")
@@ -873,6 +899,11 @@ def main():
                     help="skip the timed steps at the workload's other noise levels (1e-3, 1e-5)")
     ap.add_argument("--workload", default="paper_scale", choices=["paper_scale", "batch", "serve", "band", "precision", "versus_fp64"])
     ap.add_argument("--band-sweeps", type=int, default=20000, help="band example: sweep budget per inversion")
+    ap.add_argument("--band-schedule", default="protocol", choices=["protocol", "to_target"],
+                    help="band example: the paper's protocol (self-cooling, adaptive branching, smoothing 1e-2, "
+                         "to 0.3) or the geometric to-target schedule")
+    ap.add_argument("--band-smooth", type=float, default=0.0,
+                    help="band example with the to-target schedule: smoothing strength")
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")

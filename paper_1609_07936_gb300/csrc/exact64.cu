@@ -10,6 +10,8 @@
 
 #include "moves.cuh"
 #include "philox.cuh"
+#include <cuda_bf16.h>
+
 #include "sail_internal.cuh"
 
 namespace sail {
@@ -215,7 +217,37 @@ __device__ __forceinline__ void kahan_add(float &s, float &comp, float v) {
     s = t;
 }
 
-__global__ void __launch_bounds__(256) restore_kernel(DevProblem P, DevState S) {
+// The three BF16 pieces (each the round-to-nearest BF16 of what is left) of 8 consecutive
+// spectrum values for the tensor-copy recomputation, stored as three 16-byte rows at
+// [piece][walker][bin] of At (v past the last bin is 0).
+__device__ __forceinline__ void put_pieces8(unsigned short *At, size_t plane, size_t at, const float (&v)[8]) {
+    uint32_t w1[4], w2[4], w3[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        uint32_t p1[2], p2[2], p3[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const __nv_bfloat16 b1 = __float2bfloat16_rn(v[e + h]);
+            const float r = v[e + h] - __bfloat162float(b1);
+            const __nv_bfloat16 b2 = __float2bfloat16_rn(r);
+            const __nv_bfloat16 b3 = __float2bfloat16_rn(r - __bfloat162float(b2));
+            p1[h] = __bfloat16_as_ushort(b1);
+            p2[h] = __bfloat16_as_ushort(b2);
+            p3[h] = __bfloat16_as_ushort(b3);
+        }
+        w1[e / 2] = p1[0] | (p1[1] << 16);
+        w2[e / 2] = p2[0] | (p2[1] << 16);
+        w3[e / 2] = p3[0] | (p3[1] << 16);
+    }
+    *reinterpret_cast<uint4 *>(At + at) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+    *reinterpret_cast<uint4 *>(At + plane + at) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+    *reinterpret_cast<uint4 *>(At + 2 * plane + at) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
+}
+
+// At (optional): also write the restored spectra's BF16 pieces for the tensor-copy
+// recomputation, rows of nop bins, planes of `plane` elements (the padding stays zero).
+__global__ void __launch_bounds__(256) restore_kernel(DevProblem P, DevState S, unsigned short *At, int nop,
+                                                      size_t plane) {
     const int w = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     if (w >= P.n_walkers) return;
     float *b = S.b32 + (size_t)w * P.n_omega;
@@ -233,17 +265,28 @@ __global__ void __launch_bounds__(256) restore_kernel(DevProblem P, DevState S) 
         s1 += __shfl_xor_sync(0xFFFFFFFFu, s1, o);
         s2 += __shfl_xor_sync(0xFFFFFFFFu, s2, o);
     }
-    if (!(s0 > 0.0)) return;
-    const double xmid = 0.5 * (P.x64[0] + P.x64[P.n_omega - 1]);
-    const double c = s1 / s0;                               // centre, as an offset from xmid
-    const double var = s2 / s0 - c * c;
-    const double kappa = P.A / s0;
-    double lambda = var > 0.0 ? (P.B / P.A - xmid - c) / var : 0.0;
-    if (!(fabs(lambda * (P.n_omega - 1) * P.dw) < 0.5)) lambda = 0.0;
-    const float kf = (float)kappa, lk = (float)(kappa * lambda), cf = (float)c;
-    for (int j = lane; j < P.n_omega; j += 32) {
-        const float xj = ((float)j - half) * dw;
-        b[j] = b[j] * fmaf(lk, xj - cf, kf);
+    if (s0 > 0.0) {
+        const double xmid = 0.5 * (P.x64[0] + P.x64[P.n_omega - 1]);
+        const double c = s1 / s0;                               // centre, as an offset from xmid
+        const double var = s2 / s0 - c * c;
+        const double kappa = P.A / s0;
+        double lambda = var > 0.0 ? (P.B / P.A - xmid - c) / var : 0.0;
+        if (!(fabs(lambda * (P.n_omega - 1) * P.dw) < 0.5)) lambda = 0.0;
+        const float kf = (float)kappa, lk = (float)(kappa * lambda), cf = (float)c;
+        for (int j = lane; j < P.n_omega; j += 32) {
+            const float xj = ((float)j - half) * dw;
+            b[j] = b[j] * fmaf(lk, xj - cf, kf);
+        }
+    }
+    if (!At) return;
+    // the pieces of the restored spectrum, 8 bins a lane (16-byte stores)
+    __syncwarp();
+    const size_t row = (size_t)w * nop;
+    for (int j0 = 8 * lane; j0 < P.n_omega; j0 += 256) {
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = j0 + e < P.n_omega ? b[j0 + e] : 0.0f;
+        put_pieces8(At, plane, row + j0, v);
     }
 }
 
@@ -963,8 +1006,13 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         *launches += 1;
         return cudaGetLastError();
     }
+    if (kind == 2 && !P.tma) return cudaErrorInvalidValue;
     if (restore) {
-        restore_kernel<<<(P.n_walkers * 32 + 255) / 256, 256, 0, st>>>(P, S);
+        // with the tensor-copy recomputation the restoration also writes the BF16 pieces
+        unsigned short *At = kind == 2 ? (unsigned short *)P.tma->At : nullptr;
+        const int nop = kind == 2 ? P.tma->n_kt * 64 : 0;
+        const size_t plane = kind == 2 ? (size_t)P.tma->n_blocks_walkers * 128 * nop : 0;
+        restore_kernel<<<(P.n_walkers * 32 + 255) / 256, 256, 0, st>>>(P, S, At, nop, plane);
         *launches += 1;
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -973,10 +1021,9 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
         *launches += 1;
         return launch_resync_fp64(P, S, st);
     }
-    if (kind == 2) {                  // spectra pre-tiling, tensor-copy GEMM, chi2 pass
-        if (!P.tma) return cudaErrorInvalidValue;
-        *launches += 3;
-        return launch_resync_tma(P, S, *P.tma, status, st);
+    if (kind == 2) {                  // (pieces of the spectra), tensor-copy GEMM, chi2 pass
+        *launches += restore ? 2 : 3;
+        return launch_resync_tma(P, S, *P.tma, status, !restore, st);
     }
     *launches += kind == 1 ? 2 : 1;   // tensor-core GEMM + chi2 pass, or the FP32 GEMM
     return kind == 1 ? launch_resync_tc(P, S, status, false, st) : launch_resync_fp32(P, S, st);

@@ -467,16 +467,23 @@ cudaError_t tma_plan_init(TmaPlan &T, const DevProblem &P, void *At, void *Bt, c
         return cudaErrorInvalidValue;
     const size_t threads = (size_t)P.n_tau_pad * nop / 8;
     presplit_kernel_table<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, (uint4 *)Bt, nop);
-    return cudaGetLastError();
+    // the spectra pieces' padding (rows past the last walker, bins past the last bin) stays zero:
+    // the sum-rule restoration writes only the walkers' bins
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(At, 0, tma_spectra_bytes(P.n_walkers, P.n_omega), st);
 }
 
-cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status,
+cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status, bool presplit,
                               cudaStream_t st) {
-    const int nop = T.n_kt * kKT, rows = T.n_blocks_walkers * kM;
-    const size_t threads = (size_t)rows * nop / 8;
-    presplit_spectra_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, S, (uint4 *)T.At, rows, nop);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (presplit) {
+        const int nop = T.n_kt * kKT, rows = T.n_blocks_walkers * kM;
+        const size_t threads = (size_t)rows * nop / 8;
+        presplit_spectra_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, S, (uint4 *)T.At, rows, nop);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     switch (T.n) {
         case 128: e = launch_n<128>(P, S, T, status, st); break;
         case 96: e = launch_n<96>(P, S, T, status, st); break;

@@ -129,12 +129,14 @@ cudaError_t launch_resync_tc(const DevProblem &P, const DevState &S, int *status
 // The BF16 x6 recomputation as a pipelined GEMM fed by tensor copies (resync_tma.cu): tau
 // columns per block for a padded tau count, workspace bytes of the pre-tiled spectra and
 // kernel table, the plan (tensor maps; pre-tiles the kernel table on st) and the launch
-// (pre-tiles the spectra, GEMM, chi2); status[0] <- 1 on a timed-out wait.
+// (splits the spectra unless presplit is false because the sum-rule restoration wrote the
+// pieces, GEMM, chi2); status[0] <- 1 on a timed-out wait.
 int tma_tau_block(int n_tau_pad);
 size_t tma_spectra_bytes(int n_walkers, int n_omega);
 size_t tma_table_bytes(int n_tau_pad, int n_omega);
 cudaError_t tma_plan_init(TmaPlan &T, const DevProblem &P, void *At, void *Bt, cudaStream_t st);
-cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status, cudaStream_t st);
+cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaPlan &T, int *status, bool presplit,
+                              cudaStream_t st);
 cudaError_t launch_branch(const DevProblem &P, const DevState &S, const BranchScratch &B,
                           int precision, int block_index, double fraction, double imprint_t,
                           int event, cudaStream_t st, int *launches);
