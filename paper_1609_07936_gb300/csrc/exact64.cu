@@ -1010,7 +1010,7 @@ cudaError_t launch_resync(const DevProblem &P, const DevState &S, int precision,
     if (restore) {
         // with the tensor-copy recomputation the restoration also writes the BF16 pieces
         unsigned short *At = kind == 2 ? (unsigned short *)P.tma->At : nullptr;
-        const int nop = kind == 2 ? P.tma->n_kt * 64 : 0;
+        const int nop = kind == 2 ? P.tma->nop : 0;
         const size_t plane = kind == 2 ? (size_t)P.tma->n_blocks_walkers * 128 * nop : 0;
         restore_kernel<<<(P.n_walkers * 32 + 255) / 256, 256, 0, st>>>(P, S, At, nop, plane);
         *launches += 1;

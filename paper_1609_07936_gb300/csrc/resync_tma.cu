@@ -456,6 +456,7 @@ cudaError_t tma_plan_init(TmaPlan &T, const DevProblem &P, void *At, void *Bt, c
     T.n = tma_tau_block(P.n_tau_pad);
     if (T.n == 0) return cudaErrorInvalidValue;
     const int nop = bins_padded(P.n_omega);
+    T.nop = nop;
     T.n_kt = nop / kKT;
     T.n_blocks_tau = P.n_tau_pad / T.n;
     T.n_blocks_walkers = walkers_padded(P.n_walkers) / kM;
@@ -478,7 +479,7 @@ cudaError_t launch_resync_tma(const DevProblem &P, const DevState &S, const TmaP
                               cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     if (presplit) {
-        const int nop = T.n_kt * kKT, rows = T.n_blocks_walkers * kM;
+        const int nop = T.nop, rows = T.n_blocks_walkers * kM;
         const size_t threads = (size_t)rows * nop / 8;
         presplit_spectra_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(P, S, (uint4 *)T.At, rows, nop);
         e = cudaGetLastError();

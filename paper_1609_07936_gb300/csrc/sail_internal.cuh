@@ -34,6 +34,7 @@ struct TmaPlan {
     CUtensorMap map_a, map_b;
     void *At, *Bt;
     int n, n_kt, n_blocks_tau, n_blocks_walkers;
+    int nop;               // bins of a row of the piece arrays (n_omega rounded up to 64)
 };
 
 struct DevProblem {
