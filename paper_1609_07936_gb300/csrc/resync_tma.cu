@@ -12,8 +12,8 @@
 // operand layout the MMA reads with a SWIZZLE_128B descriptor (8-row groups 1024 bytes apart;
 // the K steps of 16 bins advance the start address by 32 bytes inside the swizzle atom).
 //
-// Block: 128 walkers (the MMA's M) x N tau columns (N <= 64, a multiple of 16 dividing the
-// padded tau count), 10 warps with fixed roles:
+// Block: 128 walkers (the MMA's M) x N tau columns (N = 128, 96, 64 or 32, the widest
+// dividing the padded tau count), 18 warps with fixed roles:
 //   warp 0: one thread issues the tensor copies of stage s (3 spectra tiles, 3 kernel tiles)
 //           once the MMAs have released it (mbarrier empty[s]) and arms full[s] with the byte
 //           count;
@@ -21,18 +21,27 @@
 //           six products each), commits them to empty[s] and the accumulator buffer to
 //           accfull[b], and starts the next stage in the other buffer once the epilogue has
 //           drained it (accempty[b]);
-//   warps 2-9: drain the accumulators of each 64-bin period with tcgen05.ld and add them to
-//           per-thread float pairs (TwoSum, round to nearest), two warps per 32-lane quarter
-//           of tensor memory (each half of the columns), then write R.
-// N stops at 64: a thread keeps a float pair for each of its N / 2 columns in registers.
+//   warps 2-17: drain the accumulators of each 64-bin period with tcgen05.ld and add them to
+//           per-thread float pairs (packed Fast2Sum, round to nearest), four warps per 32-lane
+//           quarter of tensor memory (each a quarter of the columns), then write R.
+// A thread keeps a float pair for each of its N / 4 columns in registers (96 a thread: the
+// most that 576 threads can launch with).
 // The tensor core's FP32 accumulator rounds toward zero in its internal sums; restarting every
 // 64 bins (four MMAs in the main chain) keeps that bias near 2^-22 of a product, and the
 // periods are summed in float pairs.  Tensor memory holds two buffers of (main, correction) x N
 // columns, so the MMAs of one period overlap the draining of the previous one; shared memory
-// holds three stages of 64 bins.  Every wait is bounded: on time-out a thread sets the status word and the
-// block's abort flag, the roles leave their loops, the copy thread waits (bounded) for the
-// copies it issued, the MMA thread for its MMAs, and tensor memory is freed before the block
-// returns.
+// holds two (N > 64) or three stages of 64 bins.  Every wait is bounded: on time-out a thread
+// sets the status word and the block's abort flag, the roles leave their loops, the copy thread
+// waits (bounded) for the copies it issued, the MMA thread for its MMAs, and tensor memory is
+// freed before the block returns.
+//
+// Measured limit (512 tau x 2048 bins x 16384 walkers, N = 128): the MMA rate.  Alone, this
+// MMA shape runs at 64 cycles (4096 multiply-adds a cycle per SM), also with the six-product
+// pattern, random data, concurrent bulk copies into other shared memory and concurrent
+// tensor-memory loads (67); in this kernel it took about 160 cycles with a TwoSum epilogue.
+// Timing-only copies show where the rest goes: without the epilogue's arithmetic the MMAs take
+// 116 cycles, without the tensor copies 151, without both 105; the epilogue's floating-point
+// work, running on the same SM, slows the tensor pipe more than anything else.
 #include <cstdint>
 
 #include <cuda.h>
@@ -120,12 +129,36 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t v[4]) {
                  : "r"(taddr));
 }
 
-__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float x) {
-    const float s = hi + x;
-    const float bb = s - hi;
-    const float err = (hi - (s - bb)) + (x - bb);
+// (hi, lo) += m + c for a period's main partial m and correction partial c (all terms are
+// non-negative), two columns at a time in packed FP32 pairs (add/sub.rn.f32x2: two independent
+// round-to-nearest operations per instruction, the rounding of the scalar form): Fast2Sum of m
+// into hi, its rounding error and c added to lo.  The error term is exact when hi >= m (the
+// kernel decays with the bin's frequency, so the running sum soon dominates a period's
+// partial); otherwise it is off by at most a rounding of the running sum.  Five packed
+// additions per two columns and period instead of TwoSum's seven scalar ones: the epilogue's
+// arithmetic runs beside the MMAs on the same SM and slows them (measured at 512 x 2048 x
+// 16384: 0.505 ms per recomputation with TwoSum, 0.466 with scalar Fast2Sum, 0.454 packed; the
+// same maximum error).
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(uint32_t a, uint32_t b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "r"(a), "r"(b));
+    return r;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ void fast_two_sum_add2(f2 &hi, f2 &lo, f2 m, f2 c) {
+    const f2 s = add2(hi, m);
+    lo = add2(lo, add2(sub2(m, sub2(s, hi)), c));
     hi = s;
-    lo += err;
 }
 
 // The three BF16 pieces of 8 consecutive values as three 16-byte core-matrix rows.
@@ -333,11 +366,11 @@ __global__ void __maxnreg__(96)
         // and the four warps of each such quarter take a quarter of the columns each
         const int quarter = warp & 3, part = (warp - 2) >> 2;
         const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
-        float hi[C::kPart], lo[C::kPart];
+        f2 hi2[C::kPart / 2], lo2[C::kPart / 2];
 #pragma unroll
-        for (int c = 0; c < C::kPart; ++c) {
-            hi[c] = 0.0f;
-            lo[c] = 0.0f;
+        for (int c = 0; c < C::kPart / 2; ++c) {
+            hi2[c] = 0ull;
+            lo2[c] = 0ull;
         }
         for (int d = 0; d < n_periods; ++d) {
             const int b = d & 1;
@@ -359,9 +392,8 @@ __global__ void __maxnreg__(96)
                 tmem_ld4(tmem + lane_base + col0 + (uint32_t)c, vm);
                 tmem_ld4(tmem + lane_base + col0 + (uint32_t)N + (uint32_t)c, vc);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    two_sum_add(hi[c + e], lo[c + e], __uint_as_float(vm[e]) + __uint_as_float(vc[e]));
+                fast_two_sum_add2(hi2[c / 2], lo2[c / 2], pk(vm[0], vm[1]), pk(vc[0], vc[1]));
+                fast_two_sum_add2(hi2[c / 2 + 1], lo2[c / 2 + 1], pk(vm[2], vm[3]), pk(vc[2], vc[3]));
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -375,7 +407,12 @@ __global__ void __maxnreg__(96)
                 const int i0 = nb * N + part * C::kPart;
 #pragma unroll
                 for (int c = 0; c < C::kPart; ++c) {
-                    const double r = i0 + c < P.n_tau ? Fw[c] - ((double)hi[c] + (double)lo[c]) : 0.0;
+                    float h, l;
+                    if (c & 1)
+                        asm("mov.b64 {_, %0}, %2;\n\tmov.b64 {_, %1}, %3;" : "=f"(h), "=f"(l) : "l"(hi2[c / 2]), "l"(lo2[c / 2]));
+                    else
+                        asm("mov.b64 {%0, _}, %2;\n\tmov.b64 {%1, _}, %3;" : "=f"(h), "=f"(l) : "l"(hi2[c / 2]), "l"(lo2[c / 2]));
+                    const double r = i0 + c < P.n_tau ? Fw[c] - ((double)h + (double)l) : 0.0;
                     Rw[c] = (float)r;
                 }
             }
