@@ -138,7 +138,7 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t v[4]) {
 // additions per two columns and period instead of TwoSum's seven scalar ones: the epilogue's
 // arithmetic runs beside the MMAs on the same SM and slows them (measured at 512 x 2048 x
 // 16384: 0.505 ms per recomputation with TwoSum, 0.466 with scalar Fast2Sum, 0.454 packed; the
-// same maximum error).
+// same maximum error; 0.448 with a single thread polling each period's barrier).
 typedef unsigned long long f2;
 __device__ __forceinline__ f2 pk(uint32_t a, uint32_t b) {
     f2 r;
@@ -233,7 +233,7 @@ struct TmaCfg {
     static constexpr uint32_t kCols = 4 * N <= 256 ? 256 : 512;   // two buffers of (main, corr)
     static constexpr int kPart = N / 4;                            // columns per epilogue thread
     static constexpr int kBars = 2 * kStages + 5;                 // full, empty, accfull, accempty, done
-    static constexpr size_t kSmem = (size_t)kStages * kStage + 8 * kBars + 8 + 1024;
+    static constexpr size_t kSmem = (size_t)kStages * kStage + 8 * kBars + 16 + 1024;
 };
 
 template <int N>
@@ -249,6 +249,7 @@ __global__ void __maxnreg__(96)
     // bar[2S + 4] done (S stages); then the tensor-memory address and the abort flag
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bar + C::kBars);
     volatile int *abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    volatile int *epi_ok = abort + 1;                  // [2]: epilogue verdict per accumulator buffer
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nb = blockIdx.x, wb = blockIdx.y;
     const uint32_t sbase = smem_u32(smem), bbase = smem_u32(bar);
@@ -376,14 +377,20 @@ __global__ void __maxnreg__(96)
             const int b = d & 1;
             // one lane waits and the warp follows its verdict, so the warp stays converged for
             // the .sync.aligned tensor-memory loads
-            bool ok = true;
-            if (lane == 0) ok = wait(accfull(b), (uint32_t)((d >> 1) & 1), abort);
-            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
-            if (!ok) {
-                if (lane == 0) atomicExch(status, 1);
-                *abort = 1;
-                break;
+            // one thread polls the period's barrier and posts the verdict in epi_ok[b]; the 16
+            // epilogue warps meet at named barrier 1, so all leave the loop at the same period
+            // (the flag of a buffer is rewritten only after every warp has passed the next
+            // period's barrier)
+            if (warp == 2 && lane == 0) {
+                const bool ok = wait(accfull(b), (uint32_t)((d >> 1) & 1), abort);
+                if (!ok) {
+                    atomicExch(status, 1);
+                    *abort = 1;
+                }
+                epi_ok[b] = ok ? 1 : 0;
             }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+            if (!epi_ok[b]) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t col0 = (uint32_t)(b * 2 * N + part * C::kPart);
 #pragma unroll
