@@ -518,7 +518,7 @@ def run_serve(args):
         arrivals.append(t)
     free, _ = torch.cuda.mem_get_info()
     cap = int(min(150e9, free - (4 << 30)))
-    server = sail.Server(workspace_bytes=cap, max_resident=1024, max_walkers=1 << 22,
+    server = sail.Server(workspace_bytes=cap, max_resident=args.max_resident, max_walkers=1 << 22,
                          sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY)
     probs, rids = {}, []
     server.start()
@@ -528,6 +528,8 @@ def run_serve(args):
     nxt = 0
     while nxt < len(arrivals) or len(done) < len(arrivals):
         now = time.perf_counter() - t_start
+        if args.drain is not None and nxt >= len(arrivals) and now > args.duration + args.drain:
+            break                       # bounded run: stop serving the drain budget after the arrivals
         while nxt < len(arrivals) and arrivals[nxt] <= now:
             P = random_batch_problem(nxt, seed=99, max_tau=args.max_tau, max_omega=args.max_omega,
                                      max_walkers=args.max_walkers)
@@ -544,14 +546,18 @@ def run_serve(args):
         if not queue_trace or now - queue_trace[-1][0] >= 1.0:
             queue_trace.append((round(now, 1), active, queued, len(done)))
         time.sleep(0.005)
+    server.stop()                       # the worker finishes the step it is in
     wall = time.perf_counter() - t_start
-    server.stop()
-    infos = [server.request_info(r) for r in rids]
-    lat = np.array([i["t_done"] - i["t_submit"] for i in infos])
-    wait = np.array([i["t_admit"] - i["t_submit"] for i in infos])
-    conv = np.array([bool(i["converged"]) for i in infos])
+    all_infos = [server.request_info(r) for r in rids]
+    # walker-moves of every request, finished or not (the device's throughput under the load)
+    moves = sum(i["sweeps"] * probs[r].n_walkers * probs[r].n_omega for r, i in zip(rids, all_infos))
+    n_admitted = sum(1 for i in all_infos if i["t_admit"] >= 0)
+    n_unfinished = sum(1 for i in all_infos if i["state"] in (0, 1))
+    infos = [i for i in all_infos if i["state"] == 2]            # latency statistics: completed requests
+    lat = np.array([i["t_done"] - i["t_submit"] for i in infos], dtype=float)
+    wait = np.array([i["t_admit"] - i["t_submit"] for i in infos], dtype=float)
+    conv = np.array([bool(i["converged"]) for i in infos], dtype=bool)
     sweeps = np.array([i["sweeps"] for i in infos], dtype=float)
-    moves = sum(i["sweeps"] * probs[r].n_walkers * probs[r].n_omega for r, i in zip(rids, infos))
     ttt = lat[conv]
     pct = lambda x, q: float(np.percentile(x, q)) if x.size else None   # null when none converged
     out = {"metric": "inversions/s (served)", "value": len(done) / wall, "unit": "inversions/s", "n_gpus": 1,
@@ -560,9 +566,14 @@ def run_serve(args):
                                   f"sizes as the uneven batch (n_tau U{{50..{args.max_tau}}}, n_omega U{{200..{args.max_omega}}}, "
                                   f"walkers U{{256..{args.max_walkers}}}), target chi2 <= {TTT_TARGET} n_tau, budget "
                                   f"{args.serve_sweeps} sweeps, T {TTT_T_START:g} -> {TTT_T_END:g} absolute, move scale "
-                                  f"{TTT_D_FACTOR:g} / n_omega, admission cap {cap / 1e9:.0f} GB",
+                                  f"{TTT_D_FACTOR:g} / n_omega, admission cap {cap / 1e9:.0f} GB, at most "
+                                  f"{args.max_resident} resident",
                       "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6", 3: "fp64-fma"}[args.resync_kind]},
            "wall_s": wall, "walker_moves_per_s": moves / wall,
+           "submitted": len(rids), "admitted": n_admitted, "completed": len(infos),
+           "unfinished_at_stop": n_unfinished,
+           "stop": ("all requests completed" if args.drain is None or not n_unfinished else
+                    f"{args.drain:g} s after the last arrival; latency statistics over the completed requests"),
            "latency_p50_s": pct(lat, 50), "latency_p99_s": pct(lat, 99),
            "admission_wait_p50_s": pct(wait, 50), "admission_wait_p99_s": pct(wait, 99),
            "converged_fraction": float(conv.mean()) if conv.size else None,
@@ -907,6 +918,10 @@ def main():
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--max-resident", type=int, default=1024,
+                    help="serving: at most this many requests resident at once (the rest queue)")
+    ap.add_argument("--drain", type=float, default=None,
+                    help="serving: stop this many seconds after the last arrival (default: when all are done)")
     ap.add_argument("--serve-sweeps", type=int, default=20000, help="serving: sweep budget per request")
     ap.add_argument("--max-tau", type=int, default=500, help="serving: upper end of the n_tau range")
     ap.add_argument("--max-omega", type=int, default=2000, help="serving: upper end of the n_omega range")
