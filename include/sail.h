@@ -407,7 +407,7 @@ typedef struct sail_server_ctx *sail_server_t;
 typedef struct sail_request_info {
     int state;              /* 0 queued, 1 resident, 2 completed, < 0 the error that refused it */
     int converged;          /* completed: the target chi2 was reached */
-    int sweeps;             /* completed: sweeps run */
+    int sweeps;             /* sweeps run (resident: as of the last finished step) */
     int n_used;             /* completed: walkers in the average */
     long long submit_step;  /* steps begun when the request was submitted */
     long long admit_step;   /* the step that admitted it (-1 while queued) */

@@ -1817,6 +1817,12 @@ int server_step(sail_server_t s, int *completed, int max_completed, int *n_compl
         region_give(s, s->slot_off[q], s->slot_size[q]);
         s->slot_id[q] = -1;
     }
+    // the sweeps each resident request has run so far (request information between steps)
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (int q = 0; q < slots; ++q)
+            if (b.h[q]) s->results[s->slot_id[q]].info.sweeps = b.h[q]->sweeps_done;
+    }
     if (n_completed) *n_completed = nc;
     return SAIL_OK;
 }
