@@ -54,6 +54,12 @@ def test_served_results_equal_alone_runs():
         max_active = max(max_active, active)
         for rid in completed:
             done[rid] = server.result(rid)
+        # a resident request reports the sweeps it has run: one block of 20 per step since its
+        # admission (steps are numbered from 1)
+        for rid in ids:
+            inf = server.request_info(rid)
+            if inf["state"] == 1:
+                assert inf["sweeps"] == 20 * (steps + 1 - inf["admit_step"] + 1)
         steps += 1
         assert steps < 200
     assert max_active <= 3
