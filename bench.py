@@ -50,7 +50,7 @@ TTT_INVERSIONS = 4
 
 def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY, resync_kind: int = RESYNC_KIND,
                sweep_lanes: int = 0, index_walk: int = 0, shared_bins: int = 0, sweep_loop: int = 0,
-               noise: float = NOISE, schedule: str = "paper"):
+               noise: float = NOISE, schedule: str = "paper", fp64_accept: int = 0):
     import paper_1609_07936_gb300 as sail
     P = paper_scale_double_lorentz(noise, n_walkers=N_WALKERS)
     if schedule == "to_target":
@@ -61,7 +61,7 @@ def params_for(seed: int, timing: bool = True, resync_every: int = RESYNC_EVERY,
                       sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=resync_every, branching=True,
                       A=P.A, B=P.B, seed=seed, timing=timing,
                       resync_kind=resync_kind, sweep_lanes=sweep_lanes, index_walk_len=index_walk,
-                      shared_bins=shared_bins, sweep_loop=sweep_loop, **temps)
+                      shared_bins=shared_bins, sweep_loop=sweep_loop, fp64_accept=fp64_accept, **temps)
     return P, prm
 
 
@@ -206,7 +206,8 @@ def run_gpu(args, rank, world, local_rank):
     # warm-up: W blocks on a separate handle (same configuration, other seed)
     P, prm = params_for(seed=1000 + rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule,
+                        fp64_accept=args.fp64_accept)
     warm = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     warm.anneal(args.warmup)
     warm.close()
@@ -214,7 +215,8 @@ def run_gpu(args, rank, world, local_rank):
 
     P, prm = params_for(seed=rank, resync_every=args.resync_every, resync_kind=args.resync_kind,
                         sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
+                        shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule,
+                        fp64_accept=args.fp64_accept)
     g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
     st = g.stream
     info0 = g.info()
@@ -274,7 +276,8 @@ def run_gpu(args, rank, world, local_rank):
     if not args.no_e2e:
         P2, prm2 = params_for(seed=rank + 77, timing=False, resync_kind=args.resync_kind,
                               sweep_lanes=args.sweep_lanes, index_walk=args.index_walk,
-                              shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule)
+                              shared_bins=args.shared_bins, sweep_loop=args.sweep_loop, schedule=args.schedule,
+                        fp64_accept=args.fp64_accept)
         barrier()
         t0 = time.perf_counter()
         h = sail.Sail(P2.tau, P2.F, P2.sigma, P2.omega, prm2)
@@ -305,7 +308,8 @@ def run_gpu(args, rank, world, local_rank):
         for lvl in (1e-3, 1e-5):
             P3, prm3 = params_for(seed=rank + 500, resync_kind=args.resync_kind, sweep_lanes=args.sweep_lanes,
                                   index_walk=args.index_walk, shared_bins=args.shared_bins,
-                                  sweep_loop=args.sweep_loop, noise=lvl, schedule=args.schedule)
+                                  sweep_loop=args.sweep_loop, noise=lvl, schedule=args.schedule,
+                                  fp64_accept=args.fp64_accept)
             h3 = sail.Sail(P3.tau, P3.F, P3.sigma, P3.omega, prm3)
             h3.anneal(args.warmup)
             m0 = h3.info()["moves"]
@@ -325,7 +329,8 @@ def run_gpu(args, rank, world, local_rank):
     # recomputation of the residual (the same served FP32 sweep; only the recomputation differs)
     ttt = None
     if not args.no_to_target:
-        ttt = to_target(sail, torch, args.ttt_inversions, args.resync_kind, seed0=100 * rank)
+        ttt = to_target(sail, torch, args.ttt_inversions, args.resync_kind, seed0=100 * rank,
+                        fp64_accept=args.fp64_accept)
         ttt64 = to_target(sail, torch, args.ttt_inversions, 3, seed0=100 * rank)
         ttt["vs_plain_fp64_resync"] = {
             "fp64_resync": ttt64,
@@ -376,13 +381,19 @@ def run_gpu(args, rank, world, local_rank):
             "other_noise_levels": noise_levels, "to_target": ttt, "uneven_batch": batch,
             "last_block": stats[-1] if stats else None,
         }
+        if args.fp64_accept:
+            out["fp64_accept"] = {"mode": args.fp64_accept,
+                                  "rechecks": info1["fp64_rechecks"] - info0["fp64_rechecks"],
+                                  "flips": info1["fp64_flips"] - info0["fp64_flips"],
+                                  "rechecks_per_move": (info1["fp64_rechecks"] - info0["fp64_rechecks"]) /
+                                                       max(info1["moves"] - info0["moves"], 1)}
         print(json.dumps(out), flush=True)
     g.close()
     if dist is not None:
         dist.destroy_process_group()
 
 
-def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, seed0: int = 0):
+def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, seed0: int = 0, fp64_accept: int = 0):
     """n_inv inversions of the workload (4096 walkers each, seeds seed0..), one after another
     through the public API, each from its host arrays to its averaged spectrum on the host and
     stopped at chi2 of the averaged spectrum <= 1.2 N_tau (checked at every block end) or at
@@ -396,7 +407,8 @@ def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, s
         prm = sail.Params(n_walkers=N_WALKERS, precision=sail.PREC_FP32, n_sweeps=TTT_SWEEPS,
                           sweeps_per_block=SWEEPS_PER_BLOCK, resync_every=RESYNC_EVERY, branching=True,
                           T_start_abs=TTT_T_START, T_end_abs=TTT_T_END, move_scale=TTT_D_FACTOR / N_OMEGA,
-                          A=P.A, B=P.B, seed=seed0 + k, target_chi2=TTT_TARGET * N_TAU, resync_kind=resync_kind)
+                          A=P.A, B=P.B, seed=seed0 + k, target_chi2=TTT_TARGET * N_TAU, resync_kind=resync_kind,
+                          fp64_accept=fp64_accept)
         t0 = time.perf_counter()
         g = sail.Sail(P.tau, P.F, P.sigma, P.omega, prm)
         g.anneal()
@@ -404,7 +416,7 @@ def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, s
         dt = time.perf_counter() - t0
         inf = g.info()
         res.append({"converged": bool(c2 <= TTT_TARGET * N_TAU), "sweeps": inf["sweeps_done"], "chi2_of_mean": c2,
-                    "time_s": dt})
+                    "time_s": dt, "fp64_rechecks": inf["fp64_rechecks"], "fp64_flips": inf["fp64_flips"]})
         g.close()
     wall = time.perf_counter() - t_all
     t = np.array([x["time_s"] for x in res])
@@ -418,7 +430,11 @@ def to_target(sail, torch, n_inv: int, resync_kind: int, noise: float = NOISE, s
             "times_s": t.tolist(),
             "schedule": f"geometric T {TTT_T_START:g} -> {TTT_T_END:g} (absolute) over {TTT_SWEEPS} sweeps, "
                         f"move scale {TTT_D_FACTOR:g} / N_omega, branching every {SWEEPS_PER_BLOCK} sweeps",
-            "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6", 3: "fp64-fma"}[resync_kind]}
+            "resync": {0: "fp32-fma", 1: "tensor-tf32x3", 2: "tensor-bf16x6", 3: "fp64-fma"}[resync_kind],
+            **({"fp64_accept": {"mode": fp64_accept, "rechecks": sum(x["fp64_rechecks"] for x in res),
+                                "flips": sum(x["fp64_flips"] for x in res),
+                                "rechecks_per_move": sum(x["fp64_rechecks"] for x in res) / max(moves, 1)}}
+               if fp64_accept else {})}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -918,6 +934,8 @@ def main():
     ap.add_argument("--batch-size", type=int, default=256)
     ap.add_argument("--rate", type=float, default=2.0, help="serving: request arrivals per second")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: seconds of arrivals")
+    ap.add_argument("--fp64-accept", type=int, default=0, choices=[0, 1, 2],
+                    help="decisions near the acceptance threshold taken again in FP64 (1), or all (2)")
     ap.add_argument("--max-resident", type=int, default=1024,
                     help="serving: at most this many requests resident at once (the rest queue)")
     ap.add_argument("--drain", type=float, default=None,

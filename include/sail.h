@@ -154,6 +154,15 @@ typedef struct sail_params {
      * sail_walker_rows and sail_imprint_rows. */
     int walker_offset;
     int walker_total;
+    /* FP64 acceptance near the threshold (FP32 precision, uniform bins, the Metropolis test of
+     * Sec. 2.2): 1 = a decision whose FP32 Delta chi2 lies within 1e-5 S of the acceptance
+     * threshold -T ln u (or of 0), S = sum_i |d_i| (2 |R_i| + |d_i|) the magnitude of its
+     * terms, is taken again from Delta chi2 evaluated in FP64 on the same FP32-stored state
+     * (each kernel column as the exact FP64 product of its two FP32 factors, one rounding at
+     * the end); 2 = every feasible move's decision so (a test mode); 0 = off.  Counted in
+     * sail_info.fp64_rechecks and fp64_flips.  Not with index_walk_len > 0, hastings,
+     * shared_bins, batches or the server (EINVAL). */
+    int fp64_accept;
 } sail_params;
 
 /* Per-block statistics (the paper prints T, residue and acceptance per block, Sec. 4). */
@@ -184,6 +193,8 @@ typedef struct sail_info {
     long long moves;           /* walker-moves proposed so far */
     int sweep_lanes;           /* FP32 sweep: GPU lanes per walker in use (0 for FP64) */
     int reserved;
+    long long fp64_rechecks;   /* fp64_accept: decisions taken again in FP64 so far */
+    long long fp64_flips;      /* ... of which the FP64 decision differed from the FP32 one */
 } sail_info;
 
 /* Fills *p with the defaults listed above (n_walkers 1024, FP32, 20000 sweeps,

@@ -63,6 +63,7 @@ class CParams(ctypes.Structure):
         ("smooth_s", ctypes.c_double), ("index_walk_len", ctypes.c_int), ("hastings", ctypes.c_int),
         ("walk_uniform", ctypes.c_double), ("shared_bins", ctypes.c_int), ("sweep_loop", ctypes.c_int),
         ("T_start_abs", ctypes.c_double), ("walker_offset", ctypes.c_int), ("walker_total", ctypes.c_int),
+        ("fp64_accept", ctypes.c_int),
     ]
 
 
@@ -103,6 +104,7 @@ class CInfo(ctypes.Structure):
         ("branch_ms", ctypes.c_double), ("sweep_launches", ctypes.c_longlong),
         ("resync_launches", ctypes.c_longlong), ("branch_launches", ctypes.c_longlong),
         ("moves", ctypes.c_longlong), ("sweep_lanes", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("fp64_rechecks", ctypes.c_longlong), ("fp64_flips", ctypes.c_longlong),
     ]
 
 
@@ -238,6 +240,7 @@ class Params:
     T_start_abs: float = 0.0
     walker_offset: int = 0
     walker_total: int = 0
+    fp64_accept: int = 0
 
     def c(self) -> CParams:
         p = CParams()

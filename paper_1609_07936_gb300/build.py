@@ -24,6 +24,7 @@ UNITS = {
     "sweep_fp32.cu": [],
     "sweep_walk.cu": [],
     "sweep_hastings.cu": [],
+    "sweep_guard.cu": [],
     "sweep_shared.cu": [],
     "sweep_shared8.cu": [],
     "sweep_shared4.cu": [],

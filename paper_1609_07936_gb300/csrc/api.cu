@@ -70,7 +70,7 @@ size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 struct Layout {
     size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Khi32, Klo32, Tsweep, a0, R0;
     size_t status;
-    size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos;
+    size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos, guard;
     size_t acc_trace, m_trace, delta_trace;
     size_t m, zero_l, donor_l, n_pairs, delta, counters, bz, bxi, cand, cand_Z, ctl;
     size_t mean, err, R_mean, chi2_mean, n_used, cut;
@@ -120,6 +120,7 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
     L.hash = take(W * 8);
     L.n_acc = take(W * 8);
     L.n_pos = take(W * 8);
+    L.guard = take(16);
     L.max_events = p.n_sweeps / (p.sweeps_per_block > 0 ? p.sweeps_per_block : 1) + 1;
     if (p.trace) {
         L.acc_trace = take((size_t)p.n_sweeps * W * 4);
@@ -210,6 +211,9 @@ int check_params(int n_tau, int n_omega, const sail_params *p) {
         return fail(SAIL_EINVAL, "shared_bins = %d needs n_tau <= %d in FP32", p->shared_bins,
                     p->shared_bins == 8 ? 256 : 512);
     if (p->sweep_loop < 0 || p->sweep_loop > 2) return fail(SAIL_EINVAL, "sweep_loop must be 0, 1 or 2");
+    if (p->fp64_accept < 0 || p->fp64_accept > 2) return fail(SAIL_EINVAL, "fp64_accept must be 0, 1 or 2");
+    if (p->fp64_accept && (p->precision != SAIL_PREC_FP32 || p->index_walk_len > 0 || p->hastings || p->shared_bins > 1))
+        return fail(SAIL_EINVAL, "fp64_accept needs FP32 precision, uniform bins, the Metropolis test and own bins");
     if (p->n_walkers > 1 && p->branching && p->n_walkers > kMaxWalkers)
         return fail(SAIL_EINVAL, "branching supports at most %d walkers", kMaxWalkers);
     return SAIL_OK;
@@ -535,6 +539,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.hastings = p->hastings;
     P.shared_bins = p->shared_bins > 1 ? p->shared_bins : 0;
     P.walker_base = p->walker_offset;
+    P.fp64_accept = p->fp64_accept;
     {
         // the look-ahead loop pays where several warps share each scheduler (4096 walkers on
         // 152 SMs: +12%); with few walkers per SM its longer chain per move costs more (1500:
@@ -557,6 +562,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     S.hash = (unsigned long long *)(ws + L.hash);
     S.n_acc = (unsigned long long *)(ws + L.n_acc);
     S.n_pos = (unsigned long long *)(ws + L.n_pos);
+    S.guard = (unsigned long long *)(ws + L.guard);
     S.acc_trace = p->trace ? (int *)(ws + L.acc_trace) : nullptr;
     BranchScratch &Bs = h->Bs;
     Bs.m = (int *)(ws + L.m);
@@ -590,6 +596,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     if (e == cudaSuccess) e = up(L.Khi32, Khi.data(), Khi.size() * 4);
     if (e == cudaSuccess) e = up(L.Klo32, Klo.data(), Klo.size() * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.status, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.guard, 0, 16, st);
     if (e == cudaSuccess) e = up(L.Tsweep, T.data(), T.size() * 8);
     if (e == cudaSuccess) e = up(L.a0, a0.data(), NO * 8);
     if (e == cudaSuccess) e = up(L.R0, R0.data(), PAD * 8);
@@ -649,6 +656,13 @@ int sail_get_info(sail_t h, sail_info *info) {
     info->branch_launches = h->n_kind[kBranch];
     info->moves = h->moves;
     info->sweep_lanes = h->prm.precision == SAIL_PREC_FP32 ? h->P.lanes : 0;
+    if (h->prm.fp64_accept) {
+        unsigned long long g[2] = {0, 0};
+        SAIL_CUDA(cudaMemcpyAsync(g, h->ws + h->L.guard, 16, cudaMemcpyDeviceToHost, h->stream), "D2H");
+        SAIL_CUDA(cudaStreamSynchronize(h->stream), "info sync");
+        info->fp64_rechecks = (long long)g[0];
+        info->fp64_flips = (long long)g[1];
+    }
     return SAIL_OK;
 }
 
@@ -1015,6 +1029,7 @@ std::vector<CkptRegion> ckpt_regions(const sail_ctx *h) {
     r.push_back({L.hash, W * 8});
     r.push_back({L.n_acc, W * 8});
     r.push_back({L.n_pos, W * 8});
+    r.push_back({L.guard, 16});
     r.push_back({L.Tsweep, (size_t)h->prm.n_sweeps * 8});
     if (h->prm.trace) {
         r.push_back({L.acc_trace, (size_t)h->prm.n_sweeps * W * 4});
@@ -1298,6 +1313,7 @@ int check_batch(int n, const sail_problem *probs) {
         const sail_params &p = probs[k].params;
         if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "problem %d: batches run FP32 precision", k);
         if (p.shared_bins > 1) return fail(SAIL_EINVAL, "problem %d: batches do not run shared bins", k);
+        if (p.fp64_accept) return fail(SAIL_EINVAL, "problem %d: batches do not run fp64_accept", k);
         if (p.sweeps_per_block != probs[0].params.sweeps_per_block || p.resync_every != probs[0].params.resync_every)
             return fail(SAIL_EINVAL, "problem %d: sweeps_per_block and resync_every must match problem 0", k);
         const int rc = check_params(probs[k].n_tau, probs[k].n_omega, &p);
@@ -1917,6 +1933,7 @@ int sail_server_submit(sail_server_t s, const sail_problem *req, int *id) {
     const sail_params &p = req->params;
     if (p.precision != SAIL_PREC_FP32) return fail(SAIL_EINVAL, "served inversions run FP32 precision");
     if (p.shared_bins > 1) return fail(SAIL_EINVAL, "served inversions do not run shared bins");
+    if (p.fp64_accept) return fail(SAIL_EINVAL, "served inversions do not run fp64_accept");
     if (p.sweeps_per_block != s->sweeps_per_block || p.resync_every != s->resync_every)
         return fail(SAIL_EINVAL, "request periods differ from the server's");
     size_t bytes = 0;

@@ -65,6 +65,7 @@ struct DevProblem {
     const double *Tsweep;
     const TmaPlan *tma;    // host pointer (launchers only): the BF16 tensor-copy recomputation, or null
     int walker_base;       // population index of walker 0: the walker word of every random counter
+    int fp64_accept;       // FP32: 1 = decisions near the threshold taken again in FP64, 2 = all of them
 };
 
 struct DevState {
@@ -79,6 +80,7 @@ struct DevState {
     unsigned long long *n_acc;
     unsigned long long *n_pos;
     int *acc_trace;        // [n_sweeps][n_walkers] or null
+    unsigned long long *guard;   // [2]: decisions taken again in FP64, and how many of them changed
 };
 
 struct BranchScratch {
@@ -114,6 +116,10 @@ cudaError_t launch_sweep_walk(const DevProblem &P, const DevState &S, int sweep_
 // The FP32 sweep of a problem with shared bins (P.shared_bins = 2, 4 or 8), plain or Hastings.
 cudaError_t launch_sweep_shared(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                                 cudaStream_t st);
+// The FP32 sweep whose decisions near the acceptance threshold are taken again in FP64
+// (P.fp64_accept, uniform bins, Metropolis test).
+cudaError_t launch_sweep_guard(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
+                               cudaStream_t st);
 // The FP32 sweep with the Metropolis-Hastings acceptance (P.hastings, uniform bins).
 cudaError_t launch_sweep_hastings(const DevProblem &P, const DevState &S, int sweep_begin, int sweep_end,
                                   cudaStream_t st);

@@ -123,6 +123,7 @@ cudaError_t launch_sweep_fp32(const DevProblem &P, const DevState &S, int n0, in
     if (P.shared_bins > 1) return launch_sweep_shared(P, S, n0, n1, st);
     if (P.walk_len > 0) return launch_sweep_walk(P, S, n0, n1, st);
     if (P.hastings) return launch_sweep_hastings(P, S, n0, n1, st);
+    if (P.fp64_accept) return launch_sweep_guard(P, S, n0, n1, st);
     return launch_sweep_w<kPlain>(P, S, n0, n1, st);
 }
 

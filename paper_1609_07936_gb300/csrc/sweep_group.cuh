@@ -42,6 +42,8 @@ constexpr int kThreads = 512;          // at most 16 warps per round
 constexpr int kPlain = 0;              // uniform bins, Metropolis test (the paper's)
 constexpr int kWalk = 1;               // bins from the index walk (Sec. 2.3)
 constexpr int kHastings = 2;           // uniform bins, Metropolis-Hastings test with the Jacobian
+constexpr int kGuard = 3;              // uniform bins, Metropolis test, decisions near the threshold
+                                       // taken again in FP64
 
 // (hi, lo) <- (hi, lo) * r with the product's rounding error carried in lo.
 __device__ __forceinline__ void pair_scale(float &hi, float &lo, float r) {
@@ -240,6 +242,90 @@ __device__ __forceinline__ float delta_sum(const f2 (&d)[C][H], const f2 (&R)[C]
     return pp.x + pp.y;
 }
 
+// The same sum with the magnitude of its terms, S = sum_i |d_i| |2 R_i + d_i| (the lane's parts):
+// the Delta chi2 part is formed by the same operations as delta_sum, so it rounds the same.
+__device__ __forceinline__ f2 abs2(f2 v) {
+    f2 r;
+    asm("and.b64 %0, %1, 0x7FFFFFFF7FFFFFFF;" : "=l"(r) : "l"(v));
+    return r;
+}
+template <int C, int H>
+__device__ __forceinline__ void delta_sum_mag(const f2 (&d)[C][H], const f2 (&R)[C][H], f2 two, float &D, float &S) {
+    f2 part0 = 0ull, part1 = 0ull, mag = 0ull;
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const f2 t = fma2(two, R[c][h], d[c][h]);
+            if ((c * H + h) & 1)
+                part1 = fma2(d[c][h], t, part1);
+            else
+                part0 = fma2(d[c][h], t, part0);
+            mag = fma2(abs2(d[c][h]), abs2(t), mag);
+        }
+    const float2 pp = up(add2(part0, part1)), mm = up(mag);
+    D = pp.x + pp.y;
+    S = mm.x + mm.y;
+}
+
+// Delta chi2 of move m in FP64 on the walker's FP32 state (Sec. 2.2): the lane's elements of
+// sum_i d_i (2 R_i + d_i), d_i = eps M_i - delta_p Khat_ip - delta_s Khat_is, each kernel column
+// element the exact FP64 product of its two FP32 factors, summed in FP64 over the walker's G
+// lanes.  Every lane of the warp calls it (the butterfly is warp-wide).
+template <int G, int C>
+__device__ __forceinline__ double delta_chi2_fp64(const f2 (&R)[C][32 / G / 2], const f2 (&M)[C][32 / G / 2],
+                                                  uint32_t qhi, uint32_t qlo, int PAD, const MoveDraw &m) {
+    constexpr int H = 32 / G / 2;
+    const RowAddr a = row_addr(m.ps, qhi, qlo, PAD);
+    const double eps = (double)m.eps, dp = (double)m.dp, ds = (double)m.ds;
+    double part = 0.0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        f2 hp[H], lp[H], hs[H], ls[H];
+        ld_chunk(a.hp + 128u * c, a.lp + 128u * c, a.hs + 128u * c, a.ls + 128u * c, hp, lp, hs, ls);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            const float2 Hp = up(hp[h]), Lp = up(lp[h]), Hs = up(hs[h]), Ls = up(ls[h]);
+            const float2 r = up(R[c][h]), mm = up(M[c][h]);
+            const double kp0 = (double)Hp.x * (double)Lp.x, ks0 = (double)Hs.x * (double)Ls.x;
+            const double kp1 = (double)Hp.y * (double)Lp.y, ks1 = (double)Hs.y * (double)Ls.y;
+            const double d0 = eps * (double)mm.x - dp * kp0 - ds * ks0;
+            const double d1 = eps * (double)mm.y - dp * kp1 - ds * ks1;
+            part += d0 * (2.0 * (double)r.x + d0);
+            part += d1 * (2.0 * (double)r.y + d1);
+        }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, G);
+    return part;
+}
+
+// The Metropolis decision of a feasible move with the FP64 guard (kGuard): the FP32 decision
+// stands unless its Delta chi2 D lies within 1e-5 S of the threshold or of 0 (or every decision
+// is to be checked, fp64_accept = 2); then Delta chi2 is evaluated in FP64 on the same state and
+// decides, and D takes its value.  n_re and n_flip count the decisions taken again and those
+// that changed.  Warp-uniform entry (every lane calls it).
+template <int G, int C>
+__device__ __forceinline__ bool guarded_accept(bool live, float &D, float S, float thr, int mode,
+                                               const f2 (&R)[C][32 / G / 2], const f2 (&M)[C][32 / G / 2],
+                                               uint32_t qhi, uint32_t qlo, int PAD, const MoveDraw &m,
+                                               unsigned &n_re, unsigned &n_flip) {
+    bool acc = live && (D <= 0.0f || D < thr);
+    const float band = 1e-5f * S;
+    const bool near = live && (mode == 2 || fabsf(D - thr) <= band || fabsf(D) <= band);
+    if (__any_sync(kFull, near)) {
+        const double D64 = delta_chi2_fp64<G, C>(R, M, qhi, qlo, PAD, m);
+        if (near) {
+            const bool acc64 = D64 <= 0.0 || D64 < (double)thr;
+            n_re += 1;
+            n_flip += acc64 != acc;
+            acc = acc64;
+            D = (float)D64;
+        }
+    }
+    return acc;
+}
+
 // Sweeps [n0, n1) for the 32 / G walkers of group grp of one problem on one warp, G lanes per
 // walker.  Lane l of a walker's G lanes holds R_i and M_i = Fhat_i - R_i for
 // i = 32 c + E l .. 32 c + E l + E - 1 (E = 32 / G floats of every 32-tau chunk c) and reads the
@@ -324,6 +410,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     double chi2 = S.chi2[wr];
     int accp = S.acc_prev[wr];
     unsigned long long nacc = 0, npos = 0;
+    unsigned n_re = 0, n_flip = 0;     // kGuard: decisions taken again in FP64, and changed
     const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
 
     for (int n = n0; n < n1; ++n) {
@@ -423,9 +510,20 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             if constexpr (!BAHEAD) nxt = take_move(mine, (mv + 1) & (G - 1), G);
             if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
             // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
-            const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
-            // the Hastings threshold may be negative: then D <= 0 does not pass by itself
-            if (ok && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr))) {
+            float D;
+            bool acc_k;
+            if constexpr (MODE == kGuard) {
+                float Dp, Sp;
+                delta_sum_mag<C, H>(d, R, two, Dp, Sp);
+                D = group_sum<G>(Dp);
+                acc_k = guarded_accept<G, C>(ok, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M, qhi, qlo, PAD, cur,
+                                             n_re, n_flip);
+            } else {
+                D = group_sum<G>(delta_sum<C, H>(d, R, two));
+                // the Hastings threshold may be negative: then D <= 0 does not pass by itself
+                acc_k = ok && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr));
+            }
+            if (acc_k) {
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
 #pragma unroll
@@ -488,6 +586,10 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
         S.acc_prev[w] = accp;
         S.n_acc[w] += nacc;
         S.n_pos[w] += npos;
+        if constexpr (MODE == kGuard) {
+            if (n_re) atomicAdd(&S.guard[0], (unsigned long long)n_re);
+            if (n_flip) atomicAdd(&S.guard[1], (unsigned long long)n_flip);
+        }
     }
 }
 
@@ -565,6 +667,7 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
     double chi2 = S.chi2[wr];
     int accp = S.acc_prev[wr];
     unsigned nacc = 0, npos = 0;       // this launch's accepted and positivity-rejected moves
+    unsigned n_re = 0, n_flip = 0;     // kGuard: decisions taken again in FP64, and changed
     const f2 two = pk(2.0f, 2.0f), minus_one = pk(-1.0f, -1.0f);
 
     // the walker's sweep (the same in all G lanes of its group)
@@ -728,8 +831,18 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
         if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, take_bit(tr < 0 ? 0 : tr));
         // move icur: delta chi2 = sum d (2 R + d) and the Metropolis test (the Hastings
         // threshold may be negative: then D <= 0 does not pass by itself)
-        const float D = group_sum<G>(delta_sum<C, H>(d, R, two));
-        const bool accepted = live && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr));
+        float D;
+        bool accepted;
+        if constexpr (MODE == kGuard) {
+            float Dp, Sp;
+            delta_sum_mag<C, H>(d, R, two, Dp, Sp);
+            D = group_sum<G>(Dp);
+            accepted = guarded_accept<G, C>(live, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M, qhi, qlo, PAD, cur,
+                                            n_re, n_flip);
+        } else {
+            D = group_sum<G>(delta_sum<C, H>(d, R, two));
+            accepted = live && (MODE == kHastings ? D < cur.thr : (D <= 0.0f || D < cur.thr));
+        }
         if (accepted) {
 #pragma unroll
             for (int c = 0; c < C; ++c) {
@@ -786,6 +899,10 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
         S.acc_prev[w] = accp;
         S.n_acc[w] += nacc;
         S.n_pos[w] += npos;
+        if constexpr (MODE == kGuard) {
+            if (n_re) atomicAdd(&S.guard[0], (unsigned long long)n_re);
+            if (n_flip) atomicAdd(&S.guard[1], (unsigned long long)n_flip);
+        }
     }
 }
 
@@ -807,11 +924,14 @@ __device__ __forceinline__ void run_walkers(const DevProblem &P, const DevState 
 // chunks, or 9 (the first count without prefetched columns): 128 registers a thread; 12 warps
 // otherwise (168 registers: the residual arrays grow with the chunks); 8 warps with 8 lanes per
 // walker (whose 4 walkers a warp hold twice the residual elements per lane).
-template <int G, int C>
-constexpr int sweep_threads() { return G == 8 ? 256 : ((C <= 4 || C == 9) ? kThreads : 384); }
+// The guarded variant past 8 chunks gets 8 warps (255 registers a thread) for its FP64 check.
+template <int G, int C, int MODE = kPlain>
+constexpr int sweep_threads() {
+    return G == 8 ? 256 : (MODE == kGuard && C > 8) ? 256 : ((C <= 4 || C == 9) ? kThreads : 384);
+}
 
 template <int G, int C, int MODE, bool AHEAD>
-__global__ void __launch_bounds__(sweep_threads<G, C>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
+__global__ void __launch_bounds__(sweep_threads<G, C, MODE>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom Gm) {
     extern __shared__ float4 smem4[];
     float *sm = reinterpret_cast<float *>(smem4);
@@ -856,7 +976,7 @@ cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cud
     Gm.groups_total = (P.n_walkers + WPW - 1) / WPW;
     const int ctas = Gm.groups_total < sms ? Gm.groups_total : sms;
     Gm.groups_per_cta = (Gm.groups_total + ctas - 1) / ctas;
-    const int max_warps = sweep_threads<G, C>() / 32;
+    const int max_warps = sweep_threads<G, C, MODE>() / 32;
     Gm.rounds = (Gm.groups_per_cta + max_warps - 1) / max_warps;
     Gm.warps = (Gm.groups_per_cta + Gm.rounds - 1) / Gm.rounds;
     const size_t tb = table_bytes(P);

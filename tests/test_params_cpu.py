@@ -20,6 +20,7 @@ BAD = [
     ("adaptive_branching", 2, "adaptive_branching"), ("cool_begin", math.nan, "cool_begin"),
     ("smooth_s", 0.5, "smooth_s"), ("index_walk_len", 8, "index_walk_len"), ("walk_uniform", 1.5, "walk_uniform"),
     ("hastings", 2, "hastings"), ("shared_bins", 3, "shared_bins"), ("sweep_loop", 3, "sweep_loop"),
+    ("fp64_accept", 3, "fp64_accept"),
 ]
 
 
@@ -43,7 +44,8 @@ def test_bad_value_is_refused(field, value, word):
     assert rc == _capi.SAIL_EINVAL and word in msg, (rc, msg)
 
 
-@pytest.mark.parametrize("case", ["lanes8_wide", "hastings_walk", "shared_walk", "shared8_wide", "shared4_wide"])
+@pytest.mark.parametrize("case", ["lanes8_wide", "hastings_walk", "shared_walk", "shared8_wide", "shared4_wide",
+                                  "fp64_accept_fp64", "fp64_accept_walk", "fp64_accept_hastings", "fp64_accept_shared"])
 def test_combinations_are_refused(case):
     prm = sail.Params(B=1.0)
     n_tau = 200
@@ -57,6 +59,16 @@ def test_combinations_are_refused(case):
         prm.shared_bins, n_tau = 8, 300
     elif case == "shared4_wide":
         prm.shared_bins, n_tau = 4, 513
+    elif case.startswith("fp64_accept"):
+        prm.fp64_accept = 1
+        if case.endswith("fp64"):
+            prm.precision = sail.PREC_FP64
+        elif case.endswith("walk"):
+            prm.index_walk_len = 2
+        elif case.endswith("hastings"):
+            prm.hastings = True
+        else:
+            prm.shared_bins = 4
     rc, msg = _size(n_tau, 1000, prm)
     assert rc == _capi.SAIL_EINVAL and msg, (rc, msg)
 
@@ -90,5 +102,7 @@ def test_batch_checks():
     assert rc == _capi.SAIL_EINVAL and "match" in msg
     rc, msg, _ = _batch_size([ok, sail.Params(n_walkers=256, B=1.0, shared_bins=4)])
     assert rc == _capi.SAIL_EINVAL and "shared bins" in msg
+    rc, msg, _ = _batch_size([ok, sail.Params(n_walkers=256, B=1.0, fp64_accept=1)])
+    assert rc == _capi.SAIL_EINVAL and "fp64_accept" in msg
     rc, msg, _ = _batch_size([])
     assert rc == _capi.SAIL_EINVAL
