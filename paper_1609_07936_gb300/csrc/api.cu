@@ -243,6 +243,8 @@ struct sail_ctx {
     std::vector<double> chi2_host;
     TmaPlan tma;             // resync kind 2: tensor maps of the pre-tiled operands
     int *status;             // device status word: nonzero after a timed-out device wait
+    bool ahead_auto;         // FP32 sweep_loop 0 with enough walkers: the loop follows the rejections
+    double pos_frac_last = -1.0;   // positivity-rejected share of the last block's proposals
     bool converged;          // chi2 of the averaged spectrum reached target_chi2
     double chi2_of_mean;
     // optional per-kernel timing: event pairs recorded around launches, read at block ends
@@ -256,6 +258,11 @@ struct sail_ctx {
 namespace {
 
 enum { kSweep = 0, kResync = 1, kBranch = 2 };
+
+// Positivity-rejected share of a block's proposals from which the automatic move loop takes the
+// look-ahead loop for the next block (measured on the paper-scale problem: look-ahead +12% at
+// 40% rejections, one move at a time 6% faster at 22-27%).
+constexpr double kAheadMinPos = 0.30;
 
 // A named NVTX range around the host calls that enqueue one phase of the schedule (sweep,
 // residual recomputation, branching, batched sweep segment): a profiler attached to the process
@@ -548,6 +555,7 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         P.ahead = p->sweep_loop == 2 ? 1 : p->sweep_loop == 1 ? 0 : (p->n_walkers >= 16 * sms ? 1 : 0);
+        h->ahead_auto = p->sweep_loop == 0 && P.ahead == 1;
     }
     h->status = (int *)(ws + L.status);
     P.Tsweep = (const double *)(ws + L.Tsweep);
@@ -863,6 +871,10 @@ int block_finish(sail_ctx *h, const BlockPending &b, sail_block_stats *out) {
         s.branch_delta = b.delta;
         s.branch_zeros = b.zeros;
     }
+    {
+        const double proposed = (double)(b.block_end - b.n_begin) * p.n_walkers * h->n_omega;
+        h->pos_frac_last = (double)(b.bc.pos - h->pos_seen) / proposed;
+    }
     h->acc_seen = b.bc.acc;
     h->pos_seen = b.bc.pos;
     h->blocks_done += 1;
@@ -887,6 +899,10 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
     int done = 0;
     cudaStream_t st = h->stream;
     while (done < max_blocks && handle_active(h)) {
+        // automatic move loop: the look-ahead loop pays for its proposal bookkeeping by
+        // skipping positivity-rejected moves, so it runs while the last block rejected at least
+        // kAheadMinPos of its proposals (both loops give the same chain bit for bit)
+        if (h->ahead_auto && h->pos_frac_last >= 0.0) h->P.ahead = h->pos_frac_last >= kAheadMinPos ? 1 : 0;
         BlockPending b{};
         b.n_begin = h->sweeps_done;
         b.block_end = block_end_of(h);
