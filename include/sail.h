@@ -194,7 +194,7 @@ typedef struct sail_info {
     long long sweep_launches, resync_launches, branch_launches;
     long long moves;           /* walker-moves proposed so far */
     int sweep_lanes;           /* FP32 sweep: GPU lanes per walker in use (0 for FP64) */
-    int reserved;
+    int sweep_ahead;           /* FP32 sweep: 1 if the next block runs the look-ahead move loop */
     long long fp64_rechecks;   /* fp64_accept: decisions taken again in FP64 so far */
     long long fp64_flips;      /* ... of which the FP64 decision differed from the FP32 one */
 } sail_info;

@@ -103,7 +103,7 @@ class CInfo(ctypes.Structure):
         ("workspace_bytes", ctypes.c_size_t), ("sweep_ms", ctypes.c_double), ("resync_ms", ctypes.c_double),
         ("branch_ms", ctypes.c_double), ("sweep_launches", ctypes.c_longlong),
         ("resync_launches", ctypes.c_longlong), ("branch_launches", ctypes.c_longlong),
-        ("moves", ctypes.c_longlong), ("sweep_lanes", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("moves", ctypes.c_longlong), ("sweep_lanes", ctypes.c_int), ("sweep_ahead", ctypes.c_int),
         ("fp64_rechecks", ctypes.c_longlong), ("fp64_flips", ctypes.c_longlong),
     ]
 

@@ -264,6 +264,14 @@ enum { kSweep = 0, kResync = 1, kBranch = 2 };
 // 40% rejections, one move at a time 6% faster at 22-27%).
 constexpr double kAheadMinPos = 0.30;
 
+// The move loop of the next block: the automatic choice follows the last block's positivity
+// rejections (see sail_anneal); explicit choices and walker counts below the threshold keep the
+// create-time choice.
+int sweep_ahead_next(const sail_ctx *h) {
+    if (h->ahead_auto && h->pos_frac_last >= 0.0) return h->pos_frac_last >= kAheadMinPos ? 1 : 0;
+    return h->P.ahead;
+}
+
 // A named NVTX range around the host calls that enqueue one phase of the schedule (sweep,
 // residual recomputation, branching, batched sweep segment): a profiler attached to the process
 // shows the phases on the host timeline next to their kernels; without one it costs a branch.
@@ -664,6 +672,7 @@ int sail_get_info(sail_t h, sail_info *info) {
     info->branch_launches = h->n_kind[kBranch];
     info->moves = h->moves;
     info->sweep_lanes = h->prm.precision == SAIL_PREC_FP32 ? h->P.lanes : 0;
+    info->sweep_ahead = h->prm.precision == SAIL_PREC_FP32 ? sweep_ahead_next(h) : 0;
     if (h->prm.fp64_accept) {
         unsigned long long g[2] = {0, 0};
         SAIL_CUDA(cudaMemcpyAsync(g, h->ws + h->L.guard, 16, cudaMemcpyDeviceToHost, h->stream), "D2H");
@@ -902,7 +911,7 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
         // automatic move loop: the look-ahead loop pays for its proposal bookkeeping by
         // skipping positivity-rejected moves, so it runs while the last block rejected at least
         // kAheadMinPos of its proposals (both loops give the same chain bit for bit)
-        if (h->ahead_auto && h->pos_frac_last >= 0.0) h->P.ahead = h->pos_frac_last >= kAheadMinPos ? 1 : 0;
+        h->P.ahead = sweep_ahead_next(h);
         BlockPending b{};
         b.n_begin = h->sweeps_done;
         b.block_end = block_end_of(h);

@@ -154,3 +154,35 @@ def test_spectra_in_global_memory_leave_the_same_bits(W):
     assert out[0][4].sum() > 0 and (out[0][4] < 1024).any()
     for x, y in zip(out[0], out[1]):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("schedule", ["paper", "to_target"])
+def test_automatic_loop_follows_the_rejections_with_the_same_chain(schedule):
+    """With sweep_loop = 0 and enough walkers for the look-ahead loop (16 a SM), the next
+    block runs the look-ahead loop while the last block rejected at least 30% of its proposals
+    for positivity (the paper's schedule, ~40%) and the one-move loop below (the to-target
+    schedule, ~25%); either way the states equal those of the explicit loops bit for bit."""
+    from workloads import paper_scale_double_lorentz
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    W = 16 * sms
+    P = paper_scale_double_lorentz(1e-4, n_walkers=W)
+    temps = (dict(T_start=10.0, T_end=1e-9) if schedule == "paper"
+             else dict(T_start_abs=1e6, T_end_abs=0.03, move_scale=0.1 / P.n_omega))
+    out = {}
+    for loop in (0, 1):
+        g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                      sail.Params(n_walkers=W, precision=sail.PREC_FP32, n_sweeps=20000, sweeps_per_block=20,
+                                  resync_every=10, branching=True, A=P.A, B=P.B, seed=8, sweep_loop=loop,
+                                  resync_kind=sail.RESYNC_TENSOR_BF16, **temps))
+        first = g.info()["sweep_ahead"]
+        stats = g.anneal(2)
+        out[loop] = (first, g.info()["sweep_ahead"], stats[-1]["positivity_rejected"], g.state())
+        g.close()
+    first, nxt, pos, _ = out[0]
+    assert first == 1                                   # create-time choice: enough walkers
+    assert nxt == (1 if pos >= 0.30 else 0)
+    assert (pos >= 0.30) == (schedule == "paper")
+    assert out[1][1] == 0                               # explicit one-move loop
+    for x, y in zip(out[0][3], out[1][3]):
+        np.testing.assert_array_equal(x, y)
