@@ -186,3 +186,28 @@ def test_automatic_loop_follows_the_rejections_with_the_same_chain(schedule):
     assert out[1][1] == 0                               # explicit one-move loop
     for x, y in zip(out[0][3], out[1][3]):
         np.testing.assert_array_equal(x, y)
+
+
+def test_bench_configuration_samples_take_the_oracle_decisions():
+    """The bench's launch configuration at full size — 4096 walkers on the paper grid (the
+    look-ahead loop, 8 lanes a walker, 7 warps a SM, spectra staged in shared memory, the
+    tensor-core recomputation) — for 2 sweeps at T = chi2_0 / 10 without branching: the walkers
+    0-63 and 4032-4095, run by the oracle as shards of the same population (their own random
+    counters), accept exactly the oracle's number of moves in both sweeps for at least 90% of
+    them."""
+    from workloads import paper_scale_double_lorentz
+    P = paper_scale_double_lorentz(1e-4, n_walkers=4096)
+    kw = dict(n_sweeps=2, sweeps_per_block=2, resync_every=2, branching=False, T_start=0.1, T_end=0.1, seed=47)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=4096, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True,
+                              resync_kind=sail.RESYNC_TENSOR_BF16, **kw))
+    assert g.info()["sweep_lanes"] == 8 and g.info()["sweep_ahead"] == 1
+    g.anneal()
+    acc_g = g.trace()[0]
+    g.close()
+    for lo in (0, 4032):
+        an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(walker_base=lo, **kw))
+        acc_o, _, _ = an.run(trace=True)
+        same = np.all(acc_g[:, lo:lo + 64] == acc_o, axis=0)
+        assert same.mean() >= 0.9, (lo, same.mean())
+        assert 0 < acc_o.mean() < P.n_omega

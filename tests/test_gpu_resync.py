@@ -85,3 +85,30 @@ def test_fp64_resync_of_fp32_state():
     _check(paper_scale_double_lorentz(1e-4, n_walkers=300), 300, 3, 1, rel=1e-12)
     _check(tiny_double_lorentz(), 70, 3, 2, rel=1e-12)
     _check(precision_random_peaks(3, n_walkers=130), 130, 3, 3, rel=1e-12)
+
+
+def test_bf16x6_resync_at_full_size_on_sampled_walkers():
+    """512 tau x 2048 bins x 16384 walkers, the precision workload's size and launch
+    configuration (128-column tiles, 128 walker blocks): the residuals and chi2 of 65 sampled
+    walkers (every 256th and the last) against the FP64 oracle, within the bound of the other
+    cases."""
+    P = precision_random_peaks(3, n_walkers=16384)
+    W = 16384
+    rng = np.random.default_rng(9)
+    K, Fh, _ = O.tables(P.tau, P.F, P.sigma, P.omega)
+    a0, _ = O.initial_spectrum(P.omega, P.A, P.B)
+    a = a0[None, :] * rng.uniform(0.2, 1.8, (W, P.n_omega))
+    a[rng.random((W, P.n_omega)) < 0.1] = 0.0
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=W, precision=sail.PREC_FP32, n_sweeps=10, A=P.A, B=P.B,
+                              resync_kind=sail.RESYNC_TENSOR_BF16))
+    g.set_state(a)
+    a32, R, chi2, _, _ = g.state()
+    g.close()
+    for w in list(range(0, W, 256)) + [W - 1]:
+        model = K @ a32[w]
+        R_ref = Fh - model
+        tol = 2e-6 * model + 6e-8 * np.abs(R_ref) + 1e-6
+        assert np.all(np.abs(R[w] - R_ref) <= tol), (w, np.max(np.abs(R[w] - R_ref) / tol))
+        c2 = np.sum(R_ref ** 2)
+        assert abs(chi2[w] - c2) <= 2 * np.sum(np.abs(R_ref) * tol) + 1e-9 * c2
