@@ -375,12 +375,10 @@ __global__ void __maxnreg__(96)
         }
         for (int d = 0; d < n_periods; ++d) {
             const int b = d & 1;
-            // one lane waits and the warp follows its verdict, so the warp stays converged for
-            // the .sync.aligned tensor-memory loads
             // one thread polls the period's barrier and posts the verdict in epi_ok[b]; the 16
-            // epilogue warps meet at named barrier 1, so all leave the loop at the same period
-            // (the flag of a buffer is rewritten only after every warp has passed the next
-            // period's barrier)
+            // epilogue warps meet at named barrier 1 (each converged for the .sync.aligned
+            // tensor-memory loads), so all leave the loop at the same period (the flag of a
+            // buffer is rewritten only after every warp has passed the next period's barrier)
             if (warp == 2 && lane == 0) {
                 const bool ok = wait(accfull(b), (uint32_t)((d >> 1) & 1), abort);
                 if (!ok) {
