@@ -68,7 +68,7 @@ constexpr double kFp32TermMax = 1e15;
 size_t align_up(size_t v) { return (v + 255) & ~size_t(255); }
 
 struct Layout {
-    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, Khi32, Klo32, Tsweep, a0, R0;
+    size_t Khat64, Khat32, Fhat64, Fhat32, x64, beta32, rgap32, Qhi32, Qlo32, x4_32, mrho32, Khi32, Klo32, Tsweep, a0, R0;
     size_t status;
     size_t a64, b32, g2, R64, R32, chi2, acc_prev, hash, n_acc, n_pos, guard;
     size_t acc_trace, m_trace, delta_trace;
@@ -153,6 +153,8 @@ Layout make_layout(int n_tau, int n_omega, const sail_params &p) {
     L.pr_eps = take((size_t)kProbeMax * 8);
     L.pr_delta = take((size_t)kProbeMax * 8);
     L.pr_ok = take((size_t)kProbeMax * 4);
+    L.x4_32 = take(NO * 16);
+    L.mrho32 = take(PAD * 4);
     L.total = off;
     return L;
 }
@@ -382,6 +384,15 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         if (!(sigma[i] > 0) || !std::isfinite(sigma[i])) return fail(SAIL_EINVAL, "sigma[%d] must be finite and > 0", i);
         if (!std::isfinite(F[i])) return fail(SAIL_EINVAL, "F[%d] is not finite", i);
     }
+    // a uniform tau grid (tau_i = tau_0 + i dtau) lets the 8-lane sweep form its kernel columns
+    // from one factor value per four tau points (Eq. efficient-correlation-model along tau)
+    const double dtau = n_tau > 1 ? (tau[n_tau - 1] - tau[0]) / (double)(n_tau - 1) : 0.0;
+    bool uniform_tau = true;
+    for (int i = 0; i < n_tau; ++i)
+        if (!(std::fabs(tau[i] - (tau[0] + (double)i * dtau)) <= 1e-12 * std::max(1.0, std::fabs(tau[n_tau - 1]))))
+            uniform_tau = false;
+    if (p->precision == SAIL_PREC_FP32 && p->sweep_lanes == 8 && !uniform_tau)
+        return fail(SAIL_EINVAL, "sweep_lanes = 8 needs a uniform tau grid (tau_i = tau_0 + i dtau)");
     double A = p->A;
     const double B = p->B;
     if (std::isnan(A)) {
@@ -398,17 +409,26 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
 
     const int PAD = (n_tau + 31) / 32 * 32;
     const size_t NO = (size_t)n_omega;
+    // lanes per walker of the FP32 sweep: 8 (the quad-compact column tables) on a uniform tau
+    // grid of at most 256 points whose tables fit in shared memory, else 16
+    int lanes = p->sweep_lanes;
     if (p->precision == SAIL_PREC_FP32) {
         DevProblem probe{};
         probe.n_omega = n_omega;
         probe.n_tau_pad = PAD;
         int dev = 0, smem_max = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess &&
-            sweep_fp32_table_bytes(probe) > (size_t)smem_max)
+        const bool got = cudaGetDevice(&dev) == cudaSuccess &&
+                         cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess;
+        if (lanes == 0) {
+            probe.lanes = 8;
+            lanes = (PAD <= 256 && uniform_tau && (!got || sweep_fp32_table_bytes(probe) <= (size_t)smem_max)) ? 8 : 16;
+        }
+        probe.lanes = lanes;
+        if (got && sweep_fp32_table_bytes(probe) > (size_t)smem_max)
             return fail(SAIL_EINVAL, "FP32 sweep tables need %zu bytes of shared memory, the device has %d",
                         sweep_fp32_table_bytes(probe), smem_max);
     }
+    if (lanes == 0) lanes = PAD <= 256 && uniform_tau ? 8 : 16;
     // ---- weighted bin-integrated kernel, Eq. (correlation-model): column-major [j][i]
     std::vector<double> K64(NO * PAD, 0.0), F64(PAD, 0.0);
     std::vector<float> K32(NO * PAD, 0.0f), F32(PAD, 0.0f), beta(NO);
@@ -443,6 +463,15 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     for (int l = 0; l < 32; ++l)
         for (int i = 0; i < n_tau; ++i) Qlo[(size_t)l * PAD + i] = (float)std::exp(-(double)l * dw * tau[i]);
     for (int k = 1; k < n_omega; ++k) rgap[k] = (float)(1.0 / ((double)k * dw));
+    // uniform tau: Khat_{i0+e,j} = Khat_{i0,j} rho_{i0+e} X_j^e with i0 a multiple of 4,
+    // X_j = e^{-j dw dtau} and rho_i = Khat_{i,0} / Khat_{i0,0} (the bin integral's factor over
+    // sigma); the tables hold X_j^e in FP64 rounded once, and -rho
+    std::vector<float> x4(NO * 4, 0.0f), mrho(PAD, 0.0f);
+    if (uniform_tau) {
+        for (int j = 0; j < n_omega; ++j)
+            for (int e = 0; e < 4; ++e) x4[(size_t)j * 4 + e] = (float)std::exp(-(double)j * dw * (double)e * dtau);
+        for (int i = 0; i < n_tau; ++i) mrho[i] = (float)(-(K64[i] / K64[i & ~3]));
+    }
     // tensor-core resync tables, K-major [i][j]: Khi = Khat cut to TF32, Klo = the remainder
     const int NOP = (n_omega + 31) / 32 * 32;
     std::vector<float> Khi((size_t)PAD * NOP, 0.0f), Klo((size_t)PAD * NOP, 0.0f);
@@ -544,11 +573,13 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     P.rgap32 = (const float *)(ws + L.rgap32);
     P.Qhi32 = (const float *)(ws + L.Qhi32);
     P.Qlo32 = (const float *)(ws + L.Qlo32);
+    P.x4_32 = (const float *)(ws + L.x4_32);
+    P.mrho32 = (const float *)(ws + L.mrho32);
     P.Khi32 = (const float *)(ws + L.Khi32);
     P.Klo32 = (const float *)(ws + L.Klo32);
     P.n_omega_pad = NOP;
     P.wait_test = p->wait_test;
-    P.lanes = p->sweep_lanes != 0 ? p->sweep_lanes : (PAD <= 256 ? 8 : 16);
+    P.lanes = lanes;
     P.walk_len = p->index_walk_len;
     P.walk_rho = p->walk_uniform;
     P.hastings = p->hastings;
@@ -609,6 +640,8 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
     if (e == cudaSuccess) e = up(L.rgap32, rgap.data(), NO * 4);
     if (e == cudaSuccess) e = up(L.Qhi32, Qhi.data(), Qhi.size() * 4);
     if (e == cudaSuccess) e = up(L.Qlo32, Qlo.data(), Qlo.size() * 4);
+    if (e == cudaSuccess) e = up(L.x4_32, x4.data(), x4.size() * 4);
+    if (e == cudaSuccess) e = up(L.mrho32, mrho.data(), mrho.size() * 4);
     if (e == cudaSuccess) e = up(L.Khi32, Khi.data(), Khi.size() * 4);
     if (e == cudaSuccess) e = up(L.Klo32, Klo.data(), Klo.size() * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(ws + L.status, 0, 4, st);

@@ -7,6 +7,8 @@
 //   rgap32           [n_omega]             1 / (k dw), k = 0..n_omega-1 (k = 0 unused)
 //   Qhi32            [ceil(n_omega/32)][n_tau_pad]  Khat_{i,32h}
 //   Qlo32            [32][n_tau_pad]        q_i^l = e^{-l dw tau_i}; Khat_{i,32h+l} = Qhi[h][i] Qlo[l][i]
+//   x4_32            [n_omega][4]           (1, X_j, X_j^2, X_j^3), X_j = e^{-j dw dtau} (uniform tau only)
+//   mrho32           [n_tau_pad]            -Khat_{i,0} / Khat_{4 floor(i/4),0}, zero past n_tau (uniform tau)
 //   Tsweep           [n_sweeps]            absolute temperature of each sweep
 //   a64  (FP64)      [n_walkers][n_omega]  spectra
 //   b32  (FP32)      [n_walkers][n_omega]  spectra / common scale g
@@ -56,7 +58,8 @@ struct DevProblem {
     int n_omega_pad;       // n_omega rounded up to 32
     int tc_cols;           // tau columns per tensor-core resync block (0: the widest that fits)
     int wait_test;         // test hook: the tensor-core resync withholds its first commit
-    int lanes;             // FP32 sweep: lanes per walker (8: 4 walkers per warp, n_tau <= 256; 16: 2)
+    int lanes;             // FP32 sweep: lanes per walker (8: 4 walkers per warp, n_tau <= 256 on a uniform
+                           // tau grid, columns from quad-compact tables; 16: 2, full factor rows)
     int walk_len;          // steps of the index walk (0: uniform bins)
     int hastings;          // Metropolis-Hastings acceptance with the move's Jacobian
     double walk_rho;       // probability that an index skips its walk
@@ -66,6 +69,8 @@ struct DevProblem {
     const TmaPlan *tma;    // host pointer (launchers only): the BF16 tensor-copy recomputation, or null
     int walker_base;       // population index of walker 0: the walker word of every random counter
     int fp64_accept;       // FP32: 1 = decisions near the threshold taken again in FP64, 2 = all of them
+    const float *x4_32;    // uniform tau grid: per-bin powers of X_j (8-lane sweep's columns)
+    const float *mrho32;   // uniform tau grid: minus the ratio of Khat_{i,0} to its quad's first
 };
 
 struct DevState {

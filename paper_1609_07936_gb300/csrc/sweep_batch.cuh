@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(sweep_threads<G, G == 8 ? 8 : 16>()) sweep_bat
         const BatchItem I = items[it];
         const BatchProblem &BP = probs[I.prob];
         if (I.prob != s_loaded) {
-            load_tables(BP.P, sm);
+            load_tables_g<G == 8>(BP.P, sm);
             __syncthreads();
             if (threadIdx.x == 0) s_loaded = I.prob;
         }

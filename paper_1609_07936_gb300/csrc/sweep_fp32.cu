@@ -50,9 +50,20 @@ __global__ void probe_kernel(DevProblem P, DevState S, int precision, int n, con
     for (int i = lane; i < PAD; i += 32) {
         const float R = S.R32[(size_t)w * PAD + i];
         const float M = P.Fhat32[i] - R;
-        const float Kp = P.Qhi32[(p >> 5) * PAD + i] * P.Qlo32[(p & 31) * PAD + i];
-        const float Ks = P.Qhi32[(s >> 5) * PAD + i] * P.Qlo32[(s & 31) * PAD + i];
-        const float d = fmaf(-ds, Ks, fmaf(-dp, Kp, eps * M));
+        float d;
+        if (P.lanes == 8) {
+            // the 8-lane sweep's columns (uniform tau): quad-start factors, X^e and -rho_e, in
+            // the sweep's order of operations
+            const int i0 = i & ~3, e = i & 3;
+            const float u = (P.Qhi32[(p >> 5) * PAD + i0] * P.Qlo32[(p & 31) * PAD + i0]) * dp;
+            const float v = (P.Qhi32[(s >> 5) * PAD + i0] * P.Qlo32[(s & 31) * PAD + i0]) * ds;
+            const float T = fmaf(v, P.x4_32[4 * s + e], u * P.x4_32[4 * p + e]);
+            d = fmaf(eps, M, P.mrho32[i] * T);
+        } else {
+            const float Kp = P.Qhi32[(p >> 5) * PAD + i] * P.Qlo32[(p & 31) * PAD + i];
+            const float Ks = P.Qhi32[(s >> 5) * PAD + i] * P.Qlo32[(s & 31) * PAD + i];
+            d = fmaf(-ds, Ks, fmaf(-dp, Kp, eps * M));
+        }
         part = fmaf(d, fmaf(2.0f, R, d), part);
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
@@ -107,7 +118,12 @@ cudaError_t launch_smem_probe(int reps, void *sink, cudaStream_t st, double *byt
     return cudaGetLastError();
 }
 
-size_t sweep_fp32_table_bytes(const DevProblem &P) { return table_bytes(P); }
+// the larger of the layouts a problem's sweeps may load: its lanes' tables, and the full rows of
+// the shared-bin sweep
+size_t sweep_fp32_table_bytes(const DevProblem &P) {
+    const size_t g = table_bytes_g(P.lanes == 8, P), full = table_bytes(P);
+    return g > full ? g : full;
+}
 
 cudaError_t launch_read_probe(const void *buf, size_t bytes, int reps, void *sink, cudaStream_t st) {
     int dev = 0, sms = 0;

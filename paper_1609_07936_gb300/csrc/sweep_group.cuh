@@ -91,6 +91,83 @@ __device__ void load_tables(const DevProblem &P, float *sm) {
     }
 }
 
+// Shared-memory layout of the sweep tables (float offsets).
+//
+// Full rows (16 lanes per walker, the look-ahead loop and the shared-bin kernels): the factor
+// rows Qhi [NH][PAD] and Qlo [32][PAD].
+//
+// Quad-compact (the one-move loop with 8 lanes per walker, uniform tau grid, tau_i = tau_0 +
+// i dtau).  Lane l of a walker
+// holds the four consecutive points i0 + e (e < 4, i0 = 32 c + 4 l) of every chunk c, and along
+// a uniform grid e^{-j dw tau_{i0+e}} = e^{-j dw tau_i0} X_j^e with X_j = e^{-j dw dtau}; so
+//     Khat_{i0+e,j} = Qhi[j/32][i0] Qlo[j%32][i0] * X_j^e * rho_{i0+e},
+// rho_i the ratio of Khat_{i,0} to Khat_{i0,0} (Eq. efficient-correlation-model applied along
+// tau as well as omega).  A move then reads one factor value of each of its four rows per lane
+// and chunk (4 bytes, not 16), the per-bin powers (1, X, X^2, X^3) once per column, and the lane's
+// -rho quad once per chunk.  The compact rows keep the quad starts only (k = 8 c + l, pitch a
+// multiple of 32 floats) and come in four copies, copy s offset by 8 s banks, so that the four
+// walkers of a warp (walker s of the warp reads copy s) read four random rows in one
+// conflict-free shared-memory access.  Measured: the one-move loop, which loads columns for
+// every proposal, gains (uneven batch +8%, to-target anneals +2.5%); the look-ahead loop, which
+// loads them for feasible moves only and waits on its chain rather than on shared memory, loses
+// 2% to the extra instructions per chunk, and keeps the full rows.
+struct TabLayout {
+    int hi, lo, rho, x4, beta, rgap, total;
+    int pitch;            // floats per row
+    int cs_hi, cs_lo;     // floats per copy (quad-compact)
+};
+__host__ __device__ __forceinline__ TabLayout tab_layout(bool compact, int NO, int PAD) {
+    const int NH = (NO + 31) >> 5;
+    TabLayout T{};
+    if (compact) {
+        T.pitch = (8 * (PAD / 32) + 31) / 32 * 32;
+        T.cs_hi = NH * T.pitch + 8;
+        T.cs_lo = 32 * T.pitch + 8;
+        T.hi = 0;
+        T.lo = 4 * T.cs_hi;
+        T.rho = T.lo + 4 * T.cs_lo;
+        T.x4 = T.rho + PAD;
+        T.beta = T.x4 + 4 * NO;
+    } else {
+        T.pitch = PAD;
+        T.hi = 0;
+        T.lo = NH * PAD;
+        T.rho = T.x4 = 0;
+        T.beta = T.lo + 32 * PAD;
+    }
+    T.rgap = T.beta + NO;
+    T.total = T.rgap + NO;
+    return T;
+}
+
+// Loads a problem's tables in the full-row or the quad-compact layout.
+template <bool CT>
+__device__ void load_tables_g(const DevProblem &P, float *sm) {
+    if constexpr (!CT) {
+        load_tables(P, sm);
+    } else {
+        const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
+        const TabLayout T = tab_layout(true, NO, PAD);
+        const int used = 8 * (PAD / 32);           // quad starts per row
+        for (int q = threadIdx.x; q < 4 * NH * T.pitch; q += blockDim.x) {
+            const int cp = q / (NH * T.pitch), r = q % (NH * T.pitch), h = r / T.pitch, k = r % T.pitch;
+            sm[T.hi + cp * T.cs_hi + r] = k < used ? P.Qhi32[(size_t)h * PAD + 4 * k] : 0.0f;
+        }
+        for (int q = threadIdx.x; q < 4 * 32 * T.pitch; q += blockDim.x) {
+            const int cp = q / (32 * T.pitch), r = q % (32 * T.pitch), l = r / T.pitch, k = r % T.pitch;
+            sm[T.lo + cp * T.cs_lo + r] = k < used ? P.Qlo32[(size_t)l * PAD + 4 * k] : 0.0f;
+        }
+        for (int q = threadIdx.x; q < PAD; q += blockDim.x) sm[T.rho + q] = P.mrho32[q];
+        const float4 *x4 = reinterpret_cast<const float4 *>(P.x4_32);
+        float4 *s4 = reinterpret_cast<float4 *>(sm + T.x4);
+        for (int q = threadIdx.x; q < NO; q += blockDim.x) {
+            s4[q] = x4[q];
+            sm[T.beta + q] = P.beta32[q];
+            sm[T.rgap + q] = P.rgap32[q];
+        }
+    }
+}
+
 // Packed pairs of floats: Blackwell executes mul/fma.rn.f32x2 as one instruction for two
 // independent round-to-nearest operations, so each element pair of the move costs half the
 // instructions of two scalar streams and rounds exactly as they would.
@@ -208,8 +285,47 @@ __device__ __forceinline__ RowAddr row_addr(int ps, uint32_t qhi, uint32_t qlo, 
     return a;
 }
 
-// dpart = -delta_p Khat_p - delta_s Khat_s over the lane's elements, the columns formed from
-// the factor rows (Eq. efficient-correlation-model).
+// A lane's view of the sweep tables (shared-window addresses): its piece of chunk 0 of row 0
+// of the hi and lo tables (quad-compact, CT: in its walker's copy), its -rho quad of chunk 0
+// and the per-bin powers (CT), and the row pitch in floats.
+struct ColTab {
+    uint32_t hi, lo, rho, x4;
+    int pitch;
+};
+template <int G, bool CT>
+__device__ __forceinline__ ColTab col_tab(const TabLayout &T, const float *sm, int gl, int sub) {
+    static_assert(!CT || G == 8, "the quad-compact tables serve 8 lanes per walker");
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(sm);
+    ColTab t;
+    t.pitch = T.pitch;
+    if constexpr (CT) {
+        t.hi = base + 4u * (uint32_t)(T.hi + sub * T.cs_hi + gl);
+        t.lo = base + 4u * (uint32_t)(T.lo + sub * T.cs_lo + gl);
+        t.rho = base + 4u * (uint32_t)(T.rho + 4 * gl);
+        t.x4 = base + 4u * (uint32_t)T.x4;
+    } else {
+        t.hi = base + 4u * (uint32_t)(T.hi + (32 / G) * gl);
+        t.lo = base + 4u * (uint32_t)(T.lo + (32 / G) * gl);
+        t.rho = t.x4 = 0u;
+    }
+    return t;
+}
+
+__device__ __forceinline__ float lds1(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float4 lds4(uint32_t a) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
+    return v;
+}
+
+// dpart = -delta_p Khat_p - delta_s Khat_s over the lane's elements.  Full rows: each column
+// element the product of its two factor rows (Eq. efficient-correlation-model).  Quad-compact
+// (CT): per chunk u = delta_p Qhi Qlo at the lane's quad start of p (v likewise for s), then
+// element e of the quad is -rho_e (u X_p^e + v X_s^e).
 template <int G, int C>
 __device__ __forceinline__ void columns(f2 (&dpart)[C][32 / G / 2], uint32_t qhi, uint32_t qlo, int PAD,
                                         const MoveDraw &m) {
@@ -222,6 +338,29 @@ __device__ __forceinline__ void columns(f2 (&dpart)[C][32 / G / 2], uint32_t qhi
         ld_chunk(a.hp + 128u * c, a.lp + 128u * c, a.hs + 128u * c, a.ls + 128u * c, hp, lp, hs, ls);
 #pragma unroll
         for (int h = 0; h < H; ++h) dpart[c][h] = fma2(mds, mul2(hs[h], ls[h]), mul2(mdp, mul2(hp[h], lp[h])));
+    }
+}
+template <int G, int C, bool CT>
+__device__ __forceinline__ void columns_tab(f2 (&dpart)[C][32 / G / 2], const ColTab &t, const MoveDraw &m) {
+    if constexpr (CT) {
+        const int p = m.ps & 0xFFFF, s = m.ps >> 16;
+        const uint32_t hp = t.hi + 4u * (uint32_t)((p >> 5) * t.pitch), lp = t.lo + 4u * (uint32_t)((p & 31) * t.pitch);
+        const uint32_t hs = t.hi + 4u * (uint32_t)((s >> 5) * t.pitch), ls = t.lo + 4u * (uint32_t)((s & 31) * t.pitch);
+        const float4 xp = lds4(t.x4 + 16u * (uint32_t)p), xs = lds4(t.x4 + 16u * (uint32_t)s);
+        const f2 xp01 = pk(xp.x, xp.y), xp23 = pk(xp.z, xp.w), xs01 = pk(xs.x, xs.y), xs23 = pk(xs.z, xs.w);
+        const f2 dps = pk(m.dp, m.ds);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const float vhp = lds1(hp + 32u * c), vlp = lds1(lp + 32u * c);
+            const float vhs = lds1(hs + 32u * c), vls = lds1(ls + 32u * c);
+            const float4 mr = lds4(t.rho + 128u * c);
+            const float2 uv = up(mul2(mul2(pk(vhp, vhs), pk(vlp, vls)), dps));
+            const f2 u2 = pk(uv.x, uv.x), v2 = pk(uv.y, uv.y);
+            dpart[c][0] = mul2(pk(mr.x, mr.y), fma2(v2, xs01, mul2(u2, xp01)));
+            dpart[c][1] = mul2(pk(mr.z, mr.w), fma2(v2, xs23, mul2(u2, xp23)));
+        }
+    } else {
+        columns<G, C>(dpart, t.hi, t.lo, t.pitch, m);
     }
 }
 
@@ -270,15 +409,42 @@ __device__ __forceinline__ void delta_sum_mag(const f2 (&d)[C][H], const f2 (&R)
 
 // Delta chi2 of move m in FP64 on the walker's FP32 state (Sec. 2.2): the lane's elements of
 // sum_i d_i (2 R_i + d_i), d_i = eps M_i - delta_p Khat_ip - delta_s Khat_is, each kernel column
-// element the exact FP64 product of its two FP32 factors, summed in FP64 over the walker's G
+// element the FP64 product of its FP32 factors (full rows: the two factor rows, exact;
+// quad-compact: the two quad-start factors, X^e and rho_e), summed in FP64 over the walker's G
 // lanes.  Every lane of the warp calls it (the butterfly is warp-wide).
-template <int G, int C>
+template <int G, int C, bool CT>
 __device__ __forceinline__ double delta_chi2_fp64(const f2 (&R)[C][32 / G / 2], const f2 (&M)[C][32 / G / 2],
-                                                  uint32_t qhi, uint32_t qlo, int PAD, const MoveDraw &m) {
+                                                  const ColTab &t, const MoveDraw &m) {
     constexpr int H = 32 / G / 2;
-    const RowAddr a = row_addr(m.ps, qhi, qlo, PAD);
     const double eps = (double)m.eps, dp = (double)m.dp, ds = (double)m.ds;
     double part = 0.0;
+    if constexpr (CT) {
+        const int p = m.ps & 0xFFFF, s = m.ps >> 16;
+        const uint32_t hp = t.hi + 4u * (uint32_t)((p >> 5) * t.pitch), lp = t.lo + 4u * (uint32_t)((p & 31) * t.pitch);
+        const uint32_t hs = t.hi + 4u * (uint32_t)((s >> 5) * t.pitch), ls = t.lo + 4u * (uint32_t)((s & 31) * t.pitch);
+        const float4 xp4 = lds4(t.x4 + 16u * (uint32_t)p), xs4 = lds4(t.x4 + 16u * (uint32_t)s);
+        const double xp[4] = {xp4.x, xp4.y, xp4.z, xp4.w}, xs[4] = {xs4.x, xs4.y, xs4.z, xs4.w};
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const double bp = (double)lds1(hp + 32u * c) * (double)lds1(lp + 32u * c);
+            const double bs = (double)lds1(hs + 32u * c) * (double)lds1(ls + 32u * c);
+            const float4 mr4 = lds4(t.rho + 128u * c);
+            const double rho[4] = {-(double)mr4.x, -(double)mr4.y, -(double)mr4.z, -(double)mr4.w};
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const float2 r = up(R[c][h]), mm = up(M[c][h]);
+                const int e = 2 * h;
+                const double d0 = eps * (double)mm.x - dp * (bp * xp[e] * rho[e]) - ds * (bs * xs[e] * rho[e]);
+                const double d1 = eps * (double)mm.y - dp * (bp * xp[e + 1] * rho[e + 1]) - ds * (bs * xs[e + 1] * rho[e + 1]);
+                part += d0 * (2.0 * (double)r.x + d0);
+                part += d1 * (2.0 * (double)r.y + d1);
+            }
+        }
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, G);
+        return part;
+    }
+    const RowAddr a = row_addr(m.ps, t.hi, t.lo, t.pitch);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
         f2 hp[H], lp[H], hs[H], ls[H];
@@ -305,16 +471,16 @@ __device__ __forceinline__ double delta_chi2_fp64(const f2 (&R)[C][32 / G / 2], 
 // is to be checked, fp64_accept = 2); then Delta chi2 is evaluated in FP64 on the same state and
 // decides, and D takes its value.  n_re and n_flip count the decisions taken again and those
 // that changed.  Warp-uniform entry (every lane calls it).
-template <int G, int C>
+template <int G, int C, bool CT>
 __device__ __forceinline__ bool guarded_accept(bool live, float &D, float S, float thr, int mode,
                                                const f2 (&R)[C][32 / G / 2], const f2 (&M)[C][32 / G / 2],
-                                               uint32_t qhi, uint32_t qlo, int PAD, const MoveDraw &m,
+                                               const ColTab &tab, const MoveDraw &m,
                                                unsigned &n_re, unsigned &n_flip) {
     bool acc = live && (D <= 0.0f || D < thr);
     const float band = 1e-5f * S;
     const bool near = live && (mode == 2 || fabsf(D - thr) <= band || fabsf(D) <= band);
     if (__any_sync(kFull, near)) {
-        const double D64 = delta_chi2_fp64<G, C>(R, M, qhi, qlo, PAD, m);
+        const double D64 = delta_chi2_fp64<G, C, CT>(R, M, tab, m);
         if (near) {
             const bool acc64 = D64 <= 0.0 || D64 < (double)thr;
             n_re += 1;
@@ -360,14 +526,13 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
     constexpr bool WALK = MODE == kWalk;
     constexpr bool PIPE = C <= 8 && !WALK;
     constexpr bool BAHEAD = BA && !WALK;   // b read one move ahead (above)
-    const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
-    const float *sQhi = sm;
-    const float *sQlo = sQhi + (size_t)NH * PAD;
-    const float *sBeta = sQlo + (size_t)32 * PAD;
-    const float *sRgap = sBeta + NO;
+    const int NO = P.n_omega, PAD = P.n_tau_pad;
+    constexpr bool CT = G == 8;       // quad-compact tables with 8 lanes per walker
+    const TabLayout TL = tab_layout(CT, NO, PAD);
+    const float *sBeta = sm + TL.beta;
+    const float *sRgap = sm + TL.rgap;
     const int lane = threadIdx.x & 31, gl = lane & (G - 1), sub = lane / G;
-    const uint32_t qhi = (uint32_t)__cvta_generic_to_shared(sQhi) + 4u * E * gl;
-    const uint32_t qlo = (uint32_t)__cvta_generic_to_shared(sQlo) + 4u * E * gl;
+    const ColTab tab = col_tab<G, CT>(TL, sm, gl, sub);
     const uint2 key = philox_key(P.seed);
     const double dmove = P.move_scale > 0.0 ? P.move_scale : 1.0 / NO;
     const float rho = (float)P.walk_rho;
@@ -421,7 +586,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
         MoveDraw mine = draw_move<MODE>(gl, n, wr + P.walker_base, key, NO, yd, T, sBeta, sRgap);
         MoveDraw cur = take_move(mine, 0, G);
         f2 dcur[PIPE ? C : 1][H];
-        if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, cur);
+        if constexpr (PIPE) columns_tab<G, C, CT>(dcur, tab, cur);
         // b at the current move's bins, read one move ahead (BAHEAD, see below)
         float bpc = 0.0f, bsc = 0.0f;
         if constexpr (BAHEAD) {
@@ -499,7 +664,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
 #pragma unroll
                     for (int h = 0; h < H; ++h) d[c][h] = fma2(e2, M[c][h], dcur[c][h]);
             } else {
-                columns<G, C>(d, qhi, qlo, PAD, cur);
+                columns_tab<G, C, CT>(d, tab, cur);
 #pragma unroll
                 for (int c = 0; c < C; ++c)
 #pragma unroll
@@ -508,7 +673,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
             // move k+1: its words (unless taken above) and (pipelined) its columns, into dcur,
             // now free; neither depends on move k's outcome
             if constexpr (!BAHEAD) nxt = take_move(mine, (mv + 1) & (G - 1), G);
-            if constexpr (PIPE) columns<G, C>(dcur, qhi, qlo, PAD, nxt);
+            if constexpr (PIPE) columns_tab<G, C, CT>(dcur, tab, nxt);
             // move k: delta chi2 = sum d (2 R + d) and the Metropolis test
             float D;
             bool acc_k;
@@ -516,7 +681,7 @@ __device__ __forceinline__ void run_group(const DevProblem &P, const DevState &S
                 float Dp, Sp;
                 delta_sum_mag<C, H>(d, R, two, Dp, Sp);
                 D = group_sum<G>(Dp);
-                acc_k = guarded_accept<G, C>(ok, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M, qhi, qlo, PAD, cur,
+                acc_k = guarded_accept<G, C, CT>(ok, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M, tab, cur,
                                              n_re, n_flip);
             } else {
                 D = group_sum<G>(delta_sum<C, H>(d, R, two));
@@ -619,6 +784,7 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
     constexpr int H = E / 2;           // float pairs of a chunk per lane
     constexpr int WPW = 32 / G;        // walkers per warp
     constexpr bool PIPE = C <= 8;      // registers for the prefetched columns (see run_group)
+    // full factor rows (see TabLayout)
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
     const float *sQhi = sm;
     const float *sQlo = sQhi + (size_t)NH * PAD;
@@ -837,7 +1003,8 @@ __device__ __forceinline__ void run_group_ahead(const DevProblem &P, const DevSt
             float Dp, Sp;
             delta_sum_mag<C, H>(d, R, two, Dp, Sp);
             D = group_sum<G>(Dp);
-            accepted = guarded_accept<G, C>(live, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M, qhi, qlo, PAD, cur,
+            accepted = guarded_accept<G, C, false>(live, D, group_sum<G>(Sp), cur.thr, P.fp64_accept, R, M,
+                                                   ColTab{qhi, qlo, 0u, 0u, PAD}, cur,
                                             n_re, n_flip);
         } else {
             D = group_sum<G>(delta_sum<C, H>(d, R, two));
@@ -930,6 +1097,13 @@ constexpr int sweep_threads() {
     return G == 8 ? 256 : (MODE == kGuard && C > 8) ? 256 : ((C <= 4 || C == 9) ? kThreads : 384);
 }
 
+// The table layout a kernel variant loads: quad-compact where its 8-lane walkers run the
+// one-move loop (see TabLayout).
+template <int G, int C, int MODE, bool AHEAD>
+__host__ __device__ constexpr bool sweep_compact() {
+    return G == 8 && !(MODE != kWalk && C <= 8 && AHEAD);
+}
+
 template <int G, int C, int MODE, bool AHEAD>
 __global__ void __launch_bounds__(sweep_threads<G, C, MODE>()) sweep_fp32_kernel(DevProblem P, DevState S, int n0, int n1,
                                                               SweepGeom Gm) {
@@ -937,8 +1111,10 @@ __global__ void __launch_bounds__(sweep_threads<G, C, MODE>()) sweep_fp32_kernel
     float *sm = reinterpret_cast<float *>(smem4);
     constexpr int WPW = 32 / G;
     const int NO = P.n_omega, PAD = P.n_tau_pad, NH = (NO + 31) >> 5;
-    float *sB = sm + (size_t)(NH + 32) * PAD + 2 * NO;   // staged spectra [WPW * groups_per_cta][NO]
-    load_tables(P, sm);
+    constexpr bool CT = sweep_compact<G, C, MODE, AHEAD>();
+    // staged spectra [WPW * groups_per_cta][NO], after the tables
+    float *sB = CT ? sm + tab_layout(true, NO, PAD).total : sm + (size_t)(NH + 32) * PAD + 2 * NO;
+    load_tables_g<CT>(P, sm);
     const int grp_lo = blockIdx.x * Gm.groups_per_cta;
     const int grp_hi = min(grp_lo + Gm.groups_per_cta, Gm.groups_total);
     const int walker_lo = WPW * grp_lo;
@@ -960,9 +1136,13 @@ __global__ void __launch_bounds__(sweep_threads<G, C, MODE>()) sweep_fp32_kernel
     }
 }
 
+// Bytes of the full-row tables and of the tables of either layout.
 size_t table_bytes(const DevProblem &P) {
     const size_t NH = (size_t)(P.n_omega + 31) / 32;
     return (NH + 32) * (size_t)P.n_tau_pad * 4 + 2 * (size_t)P.n_omega * 4;
+}
+size_t table_bytes_g(bool compact, const DevProblem &P) {
+    return (size_t)tab_layout(compact, P.n_omega, P.n_tau_pad).total * 4;
 }
 
 template <int G, int C, int MODE, bool AHEAD>
@@ -979,7 +1159,7 @@ cudaError_t launch_c(const DevProblem &P, const DevState &S, int n0, int n1, cud
     const int max_warps = sweep_threads<G, C, MODE>() / 32;
     Gm.rounds = (Gm.groups_per_cta + max_warps - 1) / max_warps;
     Gm.warps = (Gm.groups_per_cta + Gm.rounds - 1) / Gm.rounds;
-    const size_t tb = table_bytes(P);
+    const size_t tb = table_bytes_g(sweep_compact<G, C, MODE, AHEAD>(), P);
     const size_t staged = (size_t)WPW * Gm.groups_per_cta * P.n_omega * 4;
     if (tb > (size_t)smem_max) return cudaErrorInvalidValue;
     Gm.stage_b = tb + staged <= (size_t)smem_max;

@@ -107,3 +107,21 @@ def test_create_refuses_bad_inputs_before_touching_the_device():
     rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
                        ctypes.c_void_p(256), 16, None)
     assert rc == _capi.SAIL_ENOMEM
+
+
+def test_eight_lanes_need_a_uniform_tau_grid():
+    """The 8-lane FP32 sweep forms its kernel columns along a uniform tau grid; asked for on an
+    uneven grid, create refuses before touching the device."""
+    L = sail.load()
+    import numpy as np
+    tau = np.array([0.0, 0.1, 0.3, 0.6])
+    F = np.ones(4)
+    sig = np.ones(4)
+    om = (np.arange(8) + 0.5) * 0.5
+    p = sail.Params(n_walkers=2, B=1.0, A=1.0, precision=sail.PREC_FP32, sweep_lanes=8).c()
+    h = ctypes.c_void_p()
+    dp = ctypes.POINTER(ctypes.c_double)
+    ptr = lambda a: a.ctypes.data_as(dp)
+    rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
+                       ctypes.c_void_p(256), 1 << 40, None)
+    assert rc == _capi.SAIL_EINVAL and b"uniform tau" in L.sail_last_error()

@@ -88,6 +88,31 @@ def test_fp32_wide_tau_takes_the_oracle_decisions(W, n_tau):
     g.close()
 
 
+def test_uneven_tau_grid_runs_on_sixteen_lanes():
+    """The 8-lane sweep forms its columns along a uniform tau grid; an uneven grid of 40 points
+    (tau_i = 3 (i / 39)^1.5) takes the 16-lane sweep with full factor rows, which still takes
+    the oracle's decisions, and an explicit request for 8 lanes is refused."""
+    tau = 3.0 * (np.arange(40, dtype=np.float64) / 39) ** 1.5
+    peaks = [Peak("lorentz", 2.0, 0.4, 0.6), Peak("gauss", 5.0, 0.8, 0.4)]
+    P = make_problem("uneven_tau", tau, 37, 10.0, peaks, 1e-4, 3, 64)
+    kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=47)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(**kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True,
+                              resync_kind=sail.RESYNC_FP32, **kw))
+    assert g.info()["sweep_lanes"] == 16
+    g.anneal()
+    acc_g, _, _ = g.trace()
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    assert acc_o.sum() > 0 and (acc_o < 37).any()
+    g.close()
+    with pytest.raises(sail.SailError, match="uniform tau"):
+        sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, sweep_lanes=8, **kw))
+
+
 @pytest.mark.parametrize("hastings", [False, True])
 def test_lookahead_and_one_move_loops_are_the_same_chain(hastings):
     """Paper-scale grid (200 tau, 1000 bins), 512 walkers, two blocks of 50 sweeps with branching
