@@ -116,7 +116,11 @@ def test_uneven_tau_grid_runs_on_sixteen_lanes():
 @pytest.mark.parametrize("hastings", [False, True])
 def test_lookahead_and_one_move_loops_are_the_same_chain(hastings):
     """Paper-scale grid (200 tau, 1000 bins), 512 walkers, two blocks of 50 sweeps with branching
-    and tensor-core recomputation: both FP32 move loops end in the same bits."""
+    and tensor-core recomputation: both FP32 move loops end in the same bits.  They draw the same
+    proposals and take the same decisions; the one-move loop forms its columns from the
+    quad-compact tables (FP32 values that differ from the full rows' in the last bits), so the
+    states agree bit for bit while no delta chi2 falls within rounding of its threshold, and the
+    residuals are recomputed at the block ends."""
     from workloads import paper_scale_double_lorentz
     P = paper_scale_double_lorentz(1e-4, n_walkers=512)
     out = []
