@@ -87,9 +87,12 @@ typedef struct sail_params {
     int wait_test;          /* test hook, 0 in use: 1 makes the tensor-core resync withhold its
                                first commit so its bounded wait runs out (sail_anneal then
                                returns SAIL_ETIMEOUT) */
-    int sweep_lanes;        /* FP32 moves: GPU lanes per walker, 0 = choose (8 when n_tau <= 256,
-                               else 16), 8 (n_tau <= 256 only) or 16.  The choice sets the order
-                               of the FP32 delta-chi2 sum, so trajectories depend on it */
+    int sweep_lanes;        /* FP32 moves: GPU lanes per walker, 0 = choose (8 when n_tau <= 256
+                               on a uniform tau grid, tau_i = tau_0 + i dtau, else 16), 8 (n_tau
+                               <= 256 on a uniform grid only: sail_create returns SAIL_EINVAL
+                               otherwise; its one-move loop forms the kernel columns from
+                               tables of every fourth tau point) or 16.  The choice sets the
+                               order of the FP32 delta-chi2 sum, so trajectories depend on it */
     /* The paper's protocol against the sawtooth instability (Sec. self-cooling, Sec. 2.5,
      * Sec. smoothing).  All three act at the end of every full block of k sweeps, in this
      * order: block statistics (acceptance; mean and smallest residue after the block's
