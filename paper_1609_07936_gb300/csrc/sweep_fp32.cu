@@ -7,7 +7,9 @@ namespace sail {
 namespace {
 
 // The proposal probe: one warp per proposal, the FP32 arithmetic of the sweep (or FP64 for a
-// validation handle) on the stored state, no state change.
+// validation handle) on the stored state, no state change.  With 8 lanes per walker the column
+// elements are formed as the one-move loop forms them (quad-compact tables); the look-ahead
+// loop's full factor rows give the same values to within the last bits.
 __global__ void probe_kernel(DevProblem P, DevState S, int precision, int n, const int *walker,
                              const int *pp, const int *ss, const double *epsv, double *delta, int *ok) {
     const int lane = threadIdx.x & 31;

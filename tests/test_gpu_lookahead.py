@@ -88,6 +88,31 @@ def test_fp32_wide_tau_takes_the_oracle_decisions(W, n_tau):
     g.close()
 
 
+@pytest.mark.parametrize("n_tau", [5, 37, 230])
+def test_quad_compact_columns_at_ragged_and_widest_tau(n_tau):
+    """The one-move loop with 8 lanes per walker forms its columns from tables of every fourth
+    tau point: 5 and 37 points end in a partial quad (rho zero past n_tau), 230 points are the
+    widest 8-lane layout (8 chunks, rows of 64 floats).  The walkers take the oracle's decisions
+    and keep the sum rules."""
+    P = _problem(21, n_tau=n_tau)
+    kw = dict(n_sweeps=6, sweeps_per_block=6, resync_every=3, branching=False, T_start=0.5, T_end=0.5, seed=53)
+    an = O.Anneal(P.tau, P.F, P.sigma, P.omega, P.A, P.B, 64, O.Schedule(**kw))
+    acc_o, _, _ = an.run(trace=True)
+    g = sail.Sail(P.tau, P.F, P.sigma, P.omega,
+                  sail.Params(n_walkers=64, precision=sail.PREC_FP32, A=P.A, B=P.B, trace=True, sweep_loop=1,
+                              resync_kind=sail.RESYNC_FP32, **kw))
+    assert g.info()["sweep_lanes"] == 8
+    g.anneal()
+    acc_g, _, _ = g.trace()
+    same = np.all(acc_g == acc_o, axis=0)
+    assert same.mean() >= 0.9, same.mean()
+    assert acc_o.sum() > 0 and (acc_o < 21).any()
+    a = g.state()[0]
+    np.testing.assert_allclose(a.sum(1), P.A, rtol=2e-6)
+    np.testing.assert_allclose(a @ P.omega, P.B, rtol=2e-6)
+    g.close()
+
+
 def test_uneven_tau_grid_runs_on_sixteen_lanes():
     """The 8-lane sweep forms its columns along a uniform tau grid; an uneven grid of 40 points
     (tau_i = 3 (i / 39)^1.5) takes the 16-lane sweep with full factor rows, which still takes
