@@ -18,18 +18,23 @@
 //           once the MMAs have released it (mbarrier empty[s]) and arms full[s] with the byte
 //           count;
 //   warp 1: one thread waits full[s], issues the stage's 24 MMAs (four K steps of 16 bins,
-//           six products each), commits them to empty[s] and the accumulator buffer to
+//           six products each), commits them to empty[s] and the main accumulator buffer to
 //           accfull[b], and starts the next stage in the other buffer once the epilogue has
 //           drained it (accempty[b]);
-//   warps 2-17: drain the accumulators of each 64-bin period with tcgen05.ld and add them to
+//   warps 2-17: drain the main accumulator of each 64-bin period with tcgen05.ld and add it to
 //           per-thread float pairs (packed Fast2Sum, round to nearest), four warps per 32-lane
-//           quarter of tensor memory (each a quarter of the columns), then write R.
+//           quarter of tensor memory (each a quarter of the columns); after the last period add
+//           the correction accumulator once, then write R.
 // A thread keeps a float pair for each of its N / 4 columns in registers (96 a thread: the
 // most that 576 threads can launch with).
-// The tensor core's FP32 accumulator rounds toward zero in its internal sums; restarting every
-// 64 bins (four MMAs in the main chain) keeps that bias near 2^-22 of a product, and the
-// periods are summed in float pairs.  Tensor memory holds two buffers of (main, correction) x N
-// columns, so the MMAs of one period overlap the draining of the previous one; shared memory
+// The tensor core's FP32 accumulator rounds toward zero in its internal sums; restarting the
+// main chain every 64 bins (four MMAs) keeps that bias near 2^-22 of a product, and the periods
+// are summed in float pairs.  The correction products are about 2^-8 of the main ones, so their
+// one accumulator runs over all bins (the bias, ~2^-24 per addition of a sum 2^-8 of the model,
+// stays near 1e-7 of the model at 2048 bins): the epilogue drains half the columns per period
+// (measured 0.448 -> 0.440 ms per call at 512 x 2048 x 16384, the same maximum error).  Tensor
+// memory holds two buffers of N main columns and one region of N correction columns, so the
+// MMAs of one period overlap the draining of the previous one; shared memory
 // holds two (N > 64) or three stages of 64 bins.  Every wait is bounded: on time-out a thread
 // sets the status word and the block's abort flag, the roles leave their loops, the copy thread
 // waits (bounded) for the copies it issued, the MMA thread for its MMAs, and tensor memory is
@@ -154,6 +159,11 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
     f2 d;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
+}
+__device__ __forceinline__ void fast_two_sum_add1(f2 &hi, f2 &lo, f2 m) {
+    const f2 s = add2(hi, m);
+    lo = add2(lo, sub2(m, sub2(s, hi)));
+    hi = s;
 }
 __device__ __forceinline__ void fast_two_sum_add2(f2 &hi, f2 &lo, f2 m, f2 c) {
     const f2 s = add2(hi, m);
@@ -329,7 +339,7 @@ __global__ void __maxnreg__(96)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t dmain = tmem + (uint32_t)(b * 2 * N), dcorr = dmain + (uint32_t)N;
+                const uint32_t dmain = tmem + (uint32_t)(b * N), dcorr = tmem + (uint32_t)(2 * N);
                 for (int t = 0; t < kPeriodTiles && kt < n_kt; ++t, ++kt) {
                     const int s = kt % C::kStages;
                     if (!wait(full(s), (uint32_t)((kt / C::kStages) & 1), abort)) {
@@ -345,8 +355,9 @@ __global__ void __maxnreg__(96)
                         const uint64_t a0 = sa + ks * kKs, a1 = a0 + kTa, a2 = a0 + 2 * kTa;
                         const uint64_t b0 = sb + ks * kKs, b1 = b0 + kTb, b2 = b0 + 2 * kTb;
                         const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t acc_c = (d > 0 || t > 0 || ks > 0) ? 1u : 0u;
                         mma_bf16(dmain, a0, b0, idesc, acc);
-                        mma_bf16(dcorr, a0, b1, idesc, acc);
+                        mma_bf16(dcorr, a0, b1, idesc, acc_c);
                         mma_bf16(dcorr, a1, b0, idesc, 1u);
                         mma_bf16(dcorr, a0, b2, idesc, 1u);
                         mma_bf16(dcorr, a1, b1, idesc, 1u);
@@ -390,21 +401,37 @@ __global__ void __maxnreg__(96)
             asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
             if (!epi_ok[b]) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t col0 = (uint32_t)(b * 2 * N + part * C::kPart);
+            const uint32_t col0 = (uint32_t)(b * N + part * C::kPart);
 #pragma unroll
-            for (int c = 0; c < C::kPart; c += 4) {
-                uint32_t vm[4], vc[4];
-                tmem_ld4(tmem + lane_base + col0 + (uint32_t)c, vm);
-                tmem_ld4(tmem + lane_base + col0 + (uint32_t)N + (uint32_t)c, vc);
+            for (int c = 0; c < C::kPart; c += 8) {
+                uint32_t v0[4], v1[4];
+                tmem_ld4(tmem + lane_base + col0 + (uint32_t)c, v0);
+                tmem_ld4(tmem + lane_base + col0 + (uint32_t)(c + 4), v1);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                fast_two_sum_add2(hi2[c / 2], lo2[c / 2], pk(vm[0], vm[1]), pk(vc[0], vc[1]));
-                fast_two_sum_add2(hi2[c / 2 + 1], lo2[c / 2 + 1], pk(vm[2], vm[3]), pk(vc[2], vc[3]));
+                fast_two_sum_add1(hi2[c / 2], lo2[c / 2], pk(v0[0], v0[1]));
+                fast_two_sum_add1(hi2[c / 2 + 1], lo2[c / 2 + 1], pk(v0[2], v0[3]));
+                fast_two_sum_add1(hi2[c / 2 + 2], lo2[c / 2 + 2], pk(v1[0], v1[1]));
+                fast_two_sum_add1(hi2[c / 2 + 3], lo2[c / 2 + 3], pk(v1[2], v1[3]));
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
             if (lane == 0) arrive(accempty(b));
         }
         if (!*abort) {
+            // the correction accumulator, complete with the last period's commit, added once
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t colc = (uint32_t)(2 * N + part * C::kPart);
+#pragma unroll
+            for (int c = 0; c < C::kPart; c += 8) {
+                uint32_t v0[4], v1[4];
+                tmem_ld4(tmem + lane_base + colc + (uint32_t)c, v0);
+                tmem_ld4(tmem + lane_base + colc + (uint32_t)(c + 4), v1);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                lo2[c / 2] = add2(lo2[c / 2], pk(v0[0], v0[1]));
+                lo2[c / 2 + 1] = add2(lo2[c / 2 + 1], pk(v0[2], v0[3]));
+                lo2[c / 2 + 2] = add2(lo2[c / 2 + 2], pk(v1[0], v1[1]));
+                lo2[c / 2 + 3] = add2(lo2[c / 2 + 3], pk(v1[2], v1[3]));
+            }
             const int w = wb * kM + 32 * quarter + lane;
             if (w < P.n_walkers) {
                 float *Rw = S.R32 + (size_t)w * P.n_tau_pad + nb * N + part * C::kPart;
