@@ -27,6 +27,33 @@ def test_kernel_is_the_bin_integral():
     np.testing.assert_array_equal(Fh, 1.0 / sigma)
 
 
+@pytest.mark.parametrize("tau0", [0.0, 0.3])
+def test_kernel_factors_along_tau_in_quads(tau0):
+    """The factorisation the 8-lane FP32 sweep builds its quad-compact column tables on: on a
+    uniform grid tau_i = tau_0 + i dtau, with i0 = 4 floor(i / 4) and e = i - i0,
+    Khat_{i,j} = Khat_{i0,j} (Khat_{i,0} / Khat_{i0,0}) e^{-j dw e dtau} (Eq. efficient-
+    correlation-model read along tau), checked on the oracle's FP64 table with sigma varying
+    along tau.  On an uneven grid it fails by far more than rounding, which is why the 8-lane
+    sweep refuses one."""
+    n_tau, n_omega, dtau = 37, 50, 8.0 / 199
+    tau = tau0 + dtau * np.arange(n_tau, dtype=np.float64)
+    omega = (np.arange(n_omega) + 0.5) * (20.0 / n_omega)
+    sigma = 1e-4 * np.exp(-1.3 * tau) + 1e-9
+    K, _, dw = O.tables(tau, np.ones_like(tau), sigma, omega)
+    j = np.arange(n_omega)
+    for i in range(n_tau):
+        i0, e = i & ~3, i & 3
+        pred = K[i0] * (K[i, 0] / K[i0, 0]) * np.exp(-j * dw * e * dtau)
+        np.testing.assert_allclose(K[i], pred, rtol=1e-12, atol=0)
+    uneven = tau0 + 8.0 * (np.arange(n_tau, dtype=np.float64) / (n_tau - 1)) ** 1.5
+    Ku, _, _ = O.tables(uneven, np.ones_like(uneven), np.ones_like(uneven), omega)
+    d = uneven[1] - uneven[0]
+    pred = Ku[0] * (Ku[1, 0] / Ku[0, 0]) * np.exp(-j * dw * d)
+    np.testing.assert_allclose(Ku[1], pred, rtol=1e-12)        # one step defines dtau
+    pred3 = Ku[0] * (Ku[3, 0] / Ku[0, 0]) * np.exp(-j * dw * 3 * d)
+    assert np.max(np.abs(Ku[3] / pred3 - 1.0)) > 1e-3
+
+
 def test_kernel_matches_efficient_form():
     """Eq. (efficient-correlation-model): F(tau_i) = c_i sum_j a_j (e^{-dw dtau})^{ij} with
     c_0 = dw/2pi and c_i = (1 - e^{-i dw dtau}) / (2 pi i dtau) on a uniform tau grid."""
