@@ -384,10 +384,11 @@ int sail_create(sail_t *out, const double *tau, const double *F, const double *s
         if (!(sigma[i] > 0) || !std::isfinite(sigma[i])) return fail(SAIL_EINVAL, "sigma[%d] must be finite and > 0", i);
         if (!std::isfinite(F[i])) return fail(SAIL_EINVAL, "F[%d] is not finite", i);
     }
-    // a uniform tau grid (tau_i = tau_0 + i dtau) lets the 8-lane sweep form its kernel columns
-    // from one factor value per four tau points (Eq. efficient-correlation-model along tau)
+    // a uniform tau grid (tau_i = tau_0 + i dtau, dtau >= 0) lets the 8-lane sweep form its
+    // kernel columns from one factor value per four tau points (Eq. efficient-correlation-model
+    // along tau); a decreasing grid is not taken (its powers e^{-j dw e dtau} would grow with j)
     const double dtau = n_tau > 1 ? (tau[n_tau - 1] - tau[0]) / (double)(n_tau - 1) : 0.0;
-    bool uniform_tau = true;
+    bool uniform_tau = dtau >= 0.0;
     for (int i = 0; i < n_tau; ++i)
         if (!(std::fabs(tau[i] - (tau[0] + (double)i * dtau)) <= 1e-12 * std::max(1.0, std::fabs(tau[n_tau - 1]))))
             uniform_tau = false;

@@ -125,3 +125,8 @@ def test_eight_lanes_need_a_uniform_tau_grid():
     rc = L.sail_create(ctypes.byref(h), ptr(tau), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
                        ctypes.c_void_p(256), 1 << 40, None)
     assert rc == _capi.SAIL_EINVAL and b"uniform tau" in L.sail_last_error()
+    # an evenly spaced but decreasing grid is not taken either
+    down = np.array([0.6, 0.4, 0.2, 0.0])
+    rc = L.sail_create(ctypes.byref(h), ptr(down), ptr(F), ptr(sig), 4, ptr(om), 8, ctypes.byref(p),
+                       ctypes.c_void_p(256), 1 << 40, None)
+    assert rc == _capi.SAIL_EINVAL and b"uniform tau" in L.sail_last_error()
