@@ -54,6 +54,35 @@ def test_kernel_factors_along_tau_in_quads(tau0):
     assert np.max(np.abs(Ku[3] / pred3 - 1.0)) > 1e-3
 
 
+def test_fp32_column_forms_stay_within_a_few_ulp():
+    """The FP32 sweeps form a kernel column element from FP32 factors, each rounded once from
+    FP64: full rows as Qhi[j/32][i] * Qlo[j%32][i]; the quad-compact tables (uniform tau) as
+    ((Qhi[j/32][i0] * Qlo[j%32][i0]) * X_j^e) * rho_i.  Emulated in float32 with those operation
+    orders on the paper-scale grid, the full rows stay within 2 float32 ulp of the oracle's FP64
+    table and the compact form (seven roundings) within 5, wherever the element is a normal
+    float32: the two forms differ in the last bits only."""
+    from workloads import paper_scale_double_lorentz
+    P = paper_scale_double_lorentz(1e-4, n_walkers=1)
+    K, _, dw = O.tables(P.tau, P.F, P.sigma, P.omega)         # [n_tau, n_omega], FP64
+    n_tau, n_omega = K.shape
+    dtau = P.tau[1] - P.tau[0]
+    i = np.arange(n_tau)[:, None]
+    j = np.arange(n_omega)[None, :]
+    qhi = K[:, (j[0] // 32) * 32].astype(np.float32)          # Khat_{i, 32 h}
+    qlo = np.exp(-(j % 32) * dw * P.tau[:, None]).astype(np.float32)
+    full = qhi * qlo
+    i0 = (i // 4) * 4
+    e = i - i0
+    x = np.exp(-j * dw * e * dtau).astype(np.float32)
+    rho = (K[:, :1] / K[i0[:, 0], :1]).astype(np.float32)
+    compact = ((qhi[i0[:, 0], :] * qlo[i0[:, 0], :]) * x) * rho
+    normal = K > np.finfo(np.float32).tiny * 2 ** 8
+    ulp = np.spacing(K.astype(np.float32)).astype(np.float64)
+    for form, bound in ((full, 2), (compact, 5)):
+        err = np.abs(form.astype(np.float64) - K)
+        assert np.all(err[normal] <= bound * ulp[normal])
+
+
 def test_kernel_matches_efficient_form():
     """Eq. (efficient-correlation-model): F(tau_i) = c_i sum_j a_j (e^{-dw dtau})^{ij} with
     c_0 = dw/2pi and c_i = (1 - e^{-i dw dtau}) / (2 pi i dtau) on a uniform tau grid."""
