@@ -142,7 +142,9 @@ typedef struct sail_params {
     int sweep_loop;         /* FP32 move loop for n_tau <= 256 (uniform bins, own bins): 1 = one move
                                at a time; 2 = look-ahead (each walker keeps its next 16 proposals
                                drawn and spends columns and reduction on feasible ones only; the
-                               same chain bit for bit); 0 = choose: look-ahead when the problem has
+                               same draws and decisions, and with 8 lanes per walker on a uniform
+                               tau grid the one-move loop's column values differ from the
+                               look-ahead's in the last bits); 0 = choose: look-ahead when the problem has
                                at least 16 walkers per SM (measured faster there, slower with fewer)
                                and the last block rejected at least 30% of its proposals for
                                positivity (measured +12% at 40%, -6% at 22-27%) */

@@ -944,7 +944,8 @@ int sail_anneal(sail_t h, int max_blocks, sail_block_stats *stats, int *n_done) 
     while (done < max_blocks && handle_active(h)) {
         // automatic move loop: the look-ahead loop pays for its proposal bookkeeping by
         // skipping positivity-rejected moves, so it runs while the last block rejected at least
-        // kAheadMinPos of its proposals (both loops give the same chain bit for bit)
+        // kAheadMinPos of its proposals (both loops draw the same proposals and take the same
+        // decisions)
         h->P.ahead = sweep_ahead_next(h);
         BlockPending b{};
         b.n_begin = h->sweeps_done;

@@ -3,7 +3,9 @@
 // probes; sweep_walk.cu and sweep_hastings.cu: the kernels with an index walk and with the
 // Hastings acceptance; sweep_batch8.cu and sweep_batch16.cu: batched kernels).  Two move loops:
 // run_group takes one move at a time; run_group_ahead looks ahead over drawn proposals and
-// spends the kernel columns on feasible moves only (the same chain bit for bit).
+// spends the kernel columns on feasible moves only (the same draws and decisions; on a uniform
+// tau grid with 8 lanes per walker the one-move loop forms its columns from the quad-compact
+// tables, whose FP32 values differ from the full rows' in the last bits).
 //
 // Kernel columns from two small tables.  Eq. (efficient-correlation-model) writes the bin
 // kernel as c_i q_i^j with q_i = e^{-dw tau_i}; so with j = 32 h + l,
